@@ -1,0 +1,137 @@
+"""Iterated extended Kalman smoother (Algorithm 2, Section 3.2), run sequentially.
+
+Test infrastructure only.  The parallel solver computes the same numbers as the sequential
+IEKS (Section 4.1); this is that sequential IEKS, in float64 and original coordinates:
+
+    mu0 <- exact initial state (Eq. mu0), Sigma0 = 0
+    eta_n <- mu0 for n = 0..N                        (constant initial trajectory)
+    repeat
+        H_n, d_n <- first-order Taylor linearisation at eta_n, n = 1..N
+                    H_n = E1 - F_y(E0 eta_n) E0,  d_n = f(E0 eta_n) - F_y(E0 eta_n) E0 eta_n
+        (m^s, P^s) <- square-root Kalman filter + RTS smoother in the linearised model
+        delta <- max over n and state components of |m^s_n - eta_n|
+        eta <- m^s
+    until delta < atol or max_iter iterations
+
+Then the quasi-maximum-likelihood diffusion sigma^2 (Section 2.4; formula not printed in the
+paper, read as the prediction-error estimate (1 / (N d)) sum_n r_n^T S_n^-1 r_n of the final
+filter pass with sigma = 1, r_n = H_n m-_n - d_n) rescales the square-root covariances by
+sigma-hat; the means do not depend on sigma.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+from . import odes
+from .filtering import rts_smoother, sequential_filter
+from .linalg import solve_lower
+from .prior import iwp_transition, projection
+from .taylor import initial_state
+
+
+def linearize(kind, params, eta_n, t, q, d):
+    """H_n, d_n of Eq. linearized-observation-model."""
+    E0 = projection(0, q, d)
+    E1 = projection(1, q, d)
+    y = E0 @ eta_n
+    F = odes.jac(kind, params, y, t)
+    fy = odes.f(kind, params, y, t)
+    return E1 - F @ E0, fy - F @ y
+
+
+def linearize_all(problem, traj):
+    d, q = problem.d, problem.q
+    ts = problem.t0 + problem.h * np.arange(problem.N + 1)
+    Hs = [None]
+    ds = [None]
+    for n in range(1, problem.N + 1):
+        H, dv = linearize(problem.kind, problem.params, traj[n], ts[n], q, d)
+        Hs.append(H)
+        ds.append(dv)
+    return Hs, ds
+
+
+def prior_factors(problem):
+    Phi, Q = iwp_transition(problem.q, problem.h, problem.d)
+    sQ = np.linalg.cholesky(Q)
+    return Phi, Q, sQ
+
+
+def linear_smoother(problem, traj, mu0, Phi, sQ, want_cov=True):
+    """One linearise + filter + smoother pass (Alg. 1 in the linearised model)."""
+    D = problem.D
+    Hs, ds = linearize_all(problem, traj)
+    mf, sPf, sS, res = sequential_filter(mu0, np.zeros((D, D)), Phi, sQ, Hs, ds)
+    ms, sPs = rts_smoother(mf, sPf, Phi, sQ)
+    return dict(Hs=Hs, ds=ds, mf=mf, sPf=sPf, sS=sS, res=res, ms=ms, sPs=sPs)
+
+
+def sigma2_hat(sS, res, N, d):
+    """(1 / (N d)) sum_{n=1..N} || sqrtS_n^-1 r_n ||^2."""
+    tot = 0.0
+    for n in range(1, N + 1):
+        z = solve_lower(sS[n], res[n])
+        tot += float(z @ z)
+    return tot / (N * d)
+
+
+def objective(traj, Phi, sQ):
+    """V(eta_0:N) = 1/2 sum_n || eta_n - Phi eta_{n-1} ||^2_{Q^-1}  (Eq. objective-value)."""
+    tot = 0.0
+    for n in range(1, traj.shape[0]):
+        z = solve_lower(sQ, traj[n] - Phi @ traj[n - 1])
+        tot += float(z @ z)
+    return 0.5 * tot
+
+
+@dataclasses.dataclass
+class IEKSResult:
+    means: np.ndarray            # (N+1, D) smoothing means of the final iteration
+    sqrtcovs: np.ndarray         # (N+1, D, D) calibrated square-root covariances
+    sigma2: float                # quasi-MLE diffusion
+    iterations: int
+    deltas: List[float]          # max |change| per iteration
+    iterates: Optional[List[np.ndarray]] = None   # means after each iteration (if recorded)
+    mu0: Optional[np.ndarray] = None
+    last_pass: Optional[dict] = None
+
+
+def ieks(problem, atol: float = 1e-10, max_iter: int = 20, fixed_iters: Optional[int] = None,
+         calibrate: bool = True, record_iterates: bool = False, init: str = "mu0",
+         want_cov: bool = True) -> IEKSResult:
+    """Algorithm 2.  ``fixed_iters`` runs exactly that many iterations (no stopping rule);
+    ``init='y0'`` starts from eta_n = [y0, 0, ..., 0] instead of mu0 (Section 3.2.2 notes that
+    only E0 eta matters for the linearisation)."""
+    d, q, N, D = problem.d, problem.q, problem.N, problem.D
+    Phi, Q, sQ = prior_factors(problem)
+    mu0 = initial_state(problem.kind, problem.params, problem.y0, q)
+    if init == "mu0":
+        start = mu0
+    else:
+        start = np.zeros(D)
+        start[0::q + 1] = problem.y0
+    traj = np.tile(start, (N + 1, 1))
+    deltas = []
+    iterates = [] if record_iterates else None
+    k = 0
+    last = None
+    limit = fixed_iters if fixed_iters is not None else max_iter
+    while k < limit:
+        last = linear_smoother(problem, traj, mu0, Phi, sQ)
+        new = last["ms"]
+        delta = float(np.max(np.abs(new - traj)))
+        deltas.append(delta)
+        traj = new
+        k += 1
+        if record_iterates:
+            iterates.append(new.copy())
+        if fixed_iters is None and delta < atol:
+            break
+    s2 = sigma2_hat(last["sS"], last["res"], N, d) if calibrate else 1.0
+    scale = np.sqrt(s2)
+    return IEKSResult(means=traj, sqrtcovs=last["sPs"] * scale if want_cov else None,
+                      sigma2=s2, iterations=k, deltas=deltas, iterates=iterates, mu0=mu0,
+                      last_pass=last)

@@ -1,0 +1,123 @@
+"""Pins of the oracle's iterated extended Kalman smoother (Algorithm 2) and calibration.
+
+* Affine ODEs (Section 3.1): the IEKS is exact inference, so one iteration must equal dense
+  Gaussian conditioning of the joint prior on the observations, the second iteration must not
+  move, and the quasi-MLE diffusion must equal the exact maximum-likelihood value.
+* Logistic ODE of Section 4.1 (rate 1): the converged MAP approaches the analytic solution at
+  least at the polynomial rate h^q as the grid is refined (Section 3.2.2, convergence of the
+  MAP estimate).
+* Every iterate satisfies the linearised constraint H_n m^s_n = d_n (noiseless observation);
+  at convergence E1 m_n = f(E0 m_n) on the grid.
+* Starting from [y0, 0, ..., 0] instead of mu0 gives the same iterates (only E0 eta matters for
+  the linearisation, Section 3.2.2).
+* The sequential EKS is exact on affine problems (local linearisation is exact there).
+* The objective value (Eq. objective-value) is minimised by the posterior mean under the
+  constraints: perturbations that keep the constraints only increase it.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import eks, gp, ieks
+from oracle.odes import f as ode_f
+from oracle.prior import projection
+
+AFFINE_CASES = [
+    W.affine([[-1.0]], [0.0], [1.0], t1=1.5, N=7, q=1),
+    W.affine([[-1.0]], [1.0], [0.2], t1=2.0, N=6, q=2),
+    W.affine([[0.0, 1.0], [-1.0, 0.0]], [0.0, 0.0], [1.0, 0.0], t1=3.0, N=5, q=2),
+    W.affine([[0.3, -0.5], [0.8, -0.2]], [0.1, -0.4], [0.5, 1.0], t1=1.0, N=4, q=3),
+]
+
+
+@pytest.mark.parametrize("problem", AFFINE_CASES)
+def test_affine_one_iteration_is_exact_posterior(problem):
+    r = ieks.ieks(problem, fixed_iters=2)
+    means, covs, s2 = gp.dense_posterior(problem)
+    it1 = ieks.ieks(problem, fixed_iters=1)
+    np.testing.assert_allclose(it1.means, means, atol=1e-10, rtol=1e-9)
+    assert r.deltas[1] < 1e-12 * max(1.0, np.max(np.abs(means)))
+    assert r.sigma2 == pytest.approx(s2, rel=1e-9)
+    got = np.einsum("nij,nkj->nik", r.sqrtcovs, r.sqrtcovs)
+    np.testing.assert_allclose(got, covs * s2, atol=1e-10 * max(1.0, np.max(np.abs(covs * s2))))
+
+
+def test_logistic_converges_at_polynomial_rate():
+    errs = {}
+    for q in (1, 2):
+        Ns = (512, 1024, 2048) if q == 1 else (64, 128, 256)
+        e = []
+        for N in Ns:
+            p = W.logistic_paper(N=N, q=q)
+            r = ieks.ieks(p)
+            t = np.linspace(p.t0, p.t1, N + 1)
+            exact = 1.0 / (1.0 + (1.0 / 0.01 - 1.0) * np.exp(-t))
+            e.append(np.max(np.abs(r.means[:, 0] - exact)))
+        slope = np.polyfit(np.log([p.t1 / N for N in Ns]), np.log(e), 1)[0]
+        errs[q] = (e, slope)
+        assert slope >= q - 0.3, (q, e, slope)
+    # observed on the grid: order q + 1 for these problems
+    assert errs[2][1] > 2.5
+
+
+@pytest.mark.parametrize("problem", [W.logistic(N=96, q=2), W.fitzhugh_nagumo(N=64, q=2),
+                                     W.van_der_pol(N=60, q=3)], ids=lambda p: p.name)
+def test_constraint_identity_every_iteration(problem):
+    r = ieks.ieks(problem, fixed_iters=3, record_iterates=True)
+    traj_prev = np.tile(r.mu0, (problem.N + 1, 1))
+    for new in r.iterates:
+        Hs, ds = ieks.linearize_all(problem, traj_prev)
+        for n in range(1, problem.N + 1):
+            res = Hs[n] @ new[n] - ds[n]
+            assert np.max(np.abs(res)) <= 1e-9 * max(1.0, np.max(np.abs(new[n])))
+        traj_prev = new
+
+
+def test_converged_mean_solves_ode_on_grid():
+    p = W.logistic_paper(N=256, q=2)
+    r = ieks.ieks(p)
+    assert r.deltas[-1] < 1e-10
+    E0, E1 = projection(0, p.q, p.d), projection(1, p.q, p.d)
+    for n in range(p.N + 1):
+        y = E0 @ r.means[n]
+        assert np.max(np.abs(E1 @ r.means[n] - ode_f(p.kind, p.params, y))) < 1e-8
+
+
+def test_init_with_y0_only_gives_same_iterates():
+    p = W.van_der_pol(N=40, q=2)
+    a = ieks.ieks(p, fixed_iters=4, record_iterates=True)
+    b = ieks.ieks(p, fixed_iters=4, record_iterates=True, init="y0")
+    for x, y in zip(a.iterates, b.iterates):
+        np.testing.assert_allclose(x, y, atol=1e-12, rtol=1e-12)
+
+
+@pytest.mark.parametrize("problem", AFFINE_CASES[:3])
+def test_eks_exact_on_affine(problem):
+    ms, sPs, s2 = eks.eks(problem)
+    means, covs, s2ref = gp.dense_posterior(problem)
+    np.testing.assert_allclose(ms, means, atol=1e-10)
+    assert s2 == pytest.approx(s2ref, rel=1e-9)
+
+
+def test_posterior_mean_minimises_objective_under_constraints():
+    p = AFFINE_CASES[2]
+    r = ieks.ieks(p, fixed_iters=1)
+    Phi, Q, sQ = ieks.prior_factors(p)
+    V0 = ieks.objective(r.means, Phi, sQ)
+    # a trajectory propagated exactly by Phi has zero cost
+    traj = np.zeros_like(r.means)
+    traj[0] = r.mu0
+    for n in range(1, p.N + 1):
+        traj[n] = Phi @ traj[n - 1]
+    assert ieks.objective(traj, Phi, sQ) == pytest.approx(0.0, abs=1e-20)
+    # feasible perturbations (kept in the null space of H_n, x_0 fixed) increase V
+    H = projection(1, p.q, p.d) - p.params[:4].reshape(2, 2) @ projection(0, p.q, p.d)
+    _, _, Vt = np.linalg.svd(H)
+    null = Vt[H.shape[0]:]
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        pert = np.zeros_like(r.means)
+        for n in range(1, p.N + 1):
+            pert[n] = null.T @ rng.standard_normal(null.shape[0])
+        for eps in (1e-3, -1e-3):
+            assert ieks.objective(r.means + eps * pert, Phi, sQ) > V0
