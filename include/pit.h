@@ -1,0 +1,234 @@
+/*
+ * pit.h -- C ABI of the GB300 parallel-in-time probabilistic ODE solver.
+ *
+ * Bosch, Corenflos, Yaghoobi, Tronarp, Hennig, Saerkkae: "Parallel-in-Time Probabilistic
+ * Numerical ODE Solvers" (JMLR 25, 2024).  The solver computes the probabilistic numerical
+ * solution p(y(t_n) | y(0) = y0, {y'(t_m) = f(y(t_m), t_m)}) (Section 2, Eq. pnsol) of an
+ * initial value problem y' = f(y, t), y(t0) = y0 (Eq. ivp) on a uniform grid, by the iterated
+ * extended Kalman smoother of Algorithm 2 (ParaIEKS), whose linear smoothing step is the
+ * time-parallel square-root Rauch-Tung-Striebel smoother of Algorithm 1 (ParaRTS).
+ *
+ * Conventions (all entry points):
+ *  - Plain pointers and sizes only.  "host" pointers are CPU memory, "device" pointers are
+ *    CUDA global memory of the current device.  The caller owns every buffer; the library
+ *    never frees caller memory and never allocates device memory on the calls below: scratch
+ *    space is a caller-provided device workspace whose size the *_workspace_size functions
+ *    return.  A workspace that is too small gives PIT_ENOMEM.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Device
+ *    work is enqueued on it.  Unless stated otherwise a call returns once its work is
+ *    enqueued; pit_solve synchronises the stream (see there).
+ *  - Matrices are row-major.  A state vector of an ODE of dimension d under an IWP(q) prior
+ *    has D = d (q+1) entries ordered dimension-major, derivative-minor: entry k (q+1) + i is
+ *    the i-th derivative of component k (E_i = I_d (x) e_i, Section 2.1).
+ *  - Square-root factors are D x D matrices S with S S^T the covariance (left square roots,
+ *    Section 3.1.2); narrower factors are zero-padded to D columns.
+ *  - Floating point arithmetic on the device is in the dtype the call names (PIT_F32 or
+ *    PIT_F64); device buffers have that element type.  Prior construction, the initial state
+ *    and the diffusion sum are always computed in FP64.
+ *  - Errors: a non-zero pit_status; pit_last_error() gives a one-line, thread-local detail.
+ *    Invalid arguments are rejected on the host before any device work (PIT_EINVAL).  No C++
+ *    exception crosses the ABI.
+ */
+#ifndef PIT_H_
+#define PIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PIT_OK = 0,
+  PIT_EINVAL = 1,       /* invalid argument (checked on the host)                        */
+  PIT_ENOMEM = 2,       /* workspace smaller than the *_workspace_size value              */
+  PIT_ECUDA = 3,        /* a CUDA runtime call failed                                     */
+  PIT_ENOCONV = 4,      /* stopping rule not met within max_iter (outputs hold last iterate)*/
+  PIT_ETIMEOUT = 5,     /* a bounded device-side wait expired                             */
+  PIT_ENONFINITE = 6,   /* a non-finite value appeared in the device computation          */
+  PIT_EINTERNAL = 7,    /* internal consistency check failed                             */
+  PIT_EUNSUPPORTED = 8  /* valid request outside the compiled kernel set (e.g. d, q)      */
+} pit_status;
+
+typedef enum { PIT_F32 = 0, PIT_F64 = 1 } pit_dtype;
+
+/* ODE families with device-side vector fields and Jacobians.  Parameter layouts:
+ *   PIT_ODE_LOGISTIC         d=1  params = [r]               y' = r y (1 - y)            (Eq. logistic)
+ *   PIT_ODE_FITZHUGH_NAGUMO  d=2  params = [a, b, c]         v' = c (v - v^3/3 + w), w' = -(v - a + b w)/c
+ *   PIT_ODE_LOTKA_VOLTERRA   d=2  params = [al, be, ga, de]  x' = al x - be x y, y' = de x y - ga y
+ *   PIT_ODE_LORENZ96         d>=4 params = [F]               x_i' = (x_{i+1} - x_{i-2}) x_{i-1} - x_i + F
+ *   PIT_ODE_AFFINE           d    params = [L (d*d), c (d)]  y' = L y + c                (Eq. affine-ivp)
+ *   PIT_ODE_RIGID_BODY       d=3  params = []                y' = (-2 y2 y3, 1.25 y1 y3, -0.5 y1 y2)
+ *   PIT_ODE_VAN_DER_POL      d=2  params = [mu]              y1' = y2, y2' = mu ((1 - y1^2) y2 - y1)
+ */
+typedef enum {
+  PIT_ODE_LOGISTIC = 0,
+  PIT_ODE_FITZHUGH_NAGUMO = 1,
+  PIT_ODE_LOTKA_VOLTERRA = 2,
+  PIT_ODE_LORENZ96 = 3,
+  PIT_ODE_AFFINE = 4,
+  PIT_ODE_RIGID_BODY = 5,
+  PIT_ODE_VAN_DER_POL = 6
+} pit_ode_kind;
+
+/* An initial value problem's vector field (Eq. ivp).  `params` is host memory, FP64. */
+typedef struct {
+  int32_t kind;          /* pit_ode_kind */
+  int32_t d;             /* ODE dimension */
+  const double* params;  /* host, n_params values (layout above) */
+  int32_t n_params;
+} pit_ode;
+
+/* Uniform grid t_n = t0 + n (t1 - t0) / N, n = 0..N (N >= 1 steps, N observations). */
+typedef struct {
+  double t0;
+  double t1;
+  int64_t N;
+} pit_grid;
+
+/* Solver options.  pit_opts_default() fills the defaults given in brackets. */
+typedef struct {
+  int32_t max_iter;     /* [20]  iteration cap (>= 1)                                        */
+  int32_t fixed_iters;  /* [0]   > 0: run exactly this many iterations, ignore the stop rule  */
+  double atol_delta;    /* [1e-10] stop when max_n,k |y_n,k(new) - y_n,k(old)| <=            */
+  double rtol_delta;    /* [0]     atol + rtol * max_n,k |y_n,k(new)|, y = E0 mean, original  */
+                        /*         coordinates (the change in the solution estimate, Sec. 3.2.2)*/
+  int32_t dtype;        /* [PIT_F64] device arithmetic and output element type              */
+  int32_t calibrate;    /* [1]   quasi-MLE diffusion (Section 2.4) rescales the covariances */
+  int32_t want_cov;     /* [1]   write square-root covariances (needs `sqrtcov`)            */
+  int32_t chain_len;    /* [0]   time steps per sequential chain inside the scans, 0 = auto  */
+} pit_opts;
+
+/* Per-solve report, written by pit_solve (host memory). */
+typedef struct {
+  int32_t iterations;   /* IEKS iterations performed (Algorithm 2 loop trips)               */
+  int32_t converged;    /* 1 if the stopping rule was met (or fixed_iters was requested)    */
+  double last_delta;    /* max |change of E0 mean| in the last iteration                    */
+  double sigma2;        /* quasi-MLE diffusion sigma^2 (1 when calibrate == 0)              */
+  int64_t kernel_launches; /* CUDA kernels this call launched                               */
+} pit_solve_info;
+
+/* ---- library ------------------------------------------------------------------------- */
+
+/* Version string, e.g. "pit 0.1 sm_103a". */
+const char* pit_version(void);
+/* Static description of a status code. */
+const char* pit_status_string(int32_t status);
+/* Thread-local detail of the last error on this thread ("" if none). */
+const char* pit_last_error(void);
+/* Total CUDA kernels launched by this process through the library (monotone counter). */
+int64_t pit_launch_count(void);
+/* Fill `opts` with the defaults documented in pit_opts. */
+void pit_opts_default(pit_opts* opts);
+
+/* ---- prior and initial state (host, FP64) --------------------------------------------- */
+
+/* IWP(q) prior of one ODE dimension (Section 2.1) and its preconditioned form (Section 2.4,
+ * "preconditioned state transitions").  Outputs (host, each may be NULL):
+ *   Phi, Q        (q+1) x (q+1)  closed-form transition and process-noise covariance, sigma = 1:
+ *                                [Phi]_ij = h^(j-i)/(j-i)! (j >= i), [Q]_ij = h^(2q+1-i-j) /
+ *                                ((2q+1-i-j) (q-i)! (q-j)!)
+ *   Phibar        (q+1) x (q+1)  binom(q-i, j-i) (j >= i): step-size free transition
+ *   sqrtQbar      (q+1) x (q+1)  lower Cholesky factor of Qbar_ij = 1/(2q+1-i-j)
+ *   Tdiag         (q+1)          diagonal of T(h) = sqrt(h) diag(h^(q-i)/(q-i)!), so that
+ *                                Phi = T Phibar T^-1 and Q = T Qbar T
+ * The full D x D matrices are I_d (x) these blocks.  Errors: PIT_EINVAL if q < 1, q > 8 or
+ * h is not a positive finite number. */
+int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
+                  double* Tdiag);
+
+/* Exact initial state mu0 = [y0, y'(t0), ..., y^(q)(t0)] (Eq. mu0) by Taylor-mode recursion on
+ * the family's polynomial vector field.  y0: host, d values; mu0: host, D = d (q+1) values in
+ * the state layout above.  Errors: PIT_EINVAL for an unknown family, a bad d or n_params, or a
+ * non-finite y0. */
+int32_t pit_init_state(const pit_ode* ode, int32_t q, const double* y0, double* mu0);
+
+/* ---- device building blocks -------------------------------------------------------------- */
+
+/* First-order Taylor linearisation of the information operator at all grid points at once
+ * (Section 3.2.1, Eq. linearized-observation-model):
+ *   H_n = E1 - F_y(E0 traj_n, t_n) E0,   d_n = f(E0 traj_n, t_n) - F_y(E0 traj_n, t_n) E0 traj_n
+ * for n = 1..N.  traj: device, (N+1) x D, original coordinates (row n = linearisation point at
+ * t_n; row 0 is not read).  H: device, N x d x D (row n-1 holds H_n); dvec: device, N x d.
+ * Asynchronous.  Errors: PIT_EINVAL for bad sizes/pointers, PIT_EUNSUPPORTED if d > 16. */
+int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
+                      const void* traj, void* H, void* dvec, void* stream);
+
+/* Bytes of device workspace pit_filter_scan needs for N elements of dimension D. */
+int32_t pit_filter_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, size_t* bytes);
+
+/* Inclusive time-parallel scan of square-root filtering elements with the associative
+ * operator of Eq. sqrt-associative-filtering (Section 3.1.2):
+ *   a_1, ..., a_N  ->  a_1 (x)_f a_2 (x)_f ... (x)_f a_n,  n = 1..N  (in place).
+ * Element n is (A_n, b_n, C_n = sqrt(C_n), eta_n, J_n = sqrt(J_n)); device arrays
+ * A, C, J: N x D x D, b, eta: N x D, all of `dtype`.  For elements built as in Eq.
+ * sqrt-filtering-elements the outputs b, C are the filtering means and square-root
+ * covariances m^f_n, sqrt(P^f_n).  Output factors C, J are lower-triangular; they are
+ * square roots of the same matrices as the paper's but their column signs are not fixed.
+ * Asynchronous.  Errors: PIT_EINVAL (N < 1, D < 1, null pointer), PIT_EUNSUPPORTED (D not
+ * compiled: 1..16), PIT_ENOMEM (workspace too small). */
+int32_t pit_filter_scan(int64_t N, int32_t D, int32_t dtype, void* A, void* b, void* C,
+                        void* eta, void* J, void* workspace, size_t ws_bytes, void* stream);
+
+/* Bytes of device workspace pit_smooth_scan needs. */
+int32_t pit_smooth_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, int32_t want_L,
+                                       size_t* bytes);
+
+/* Reverse inclusive time-parallel scan of square-root smoothing elements with the operator of
+ * Eq. sqrt-associative-smoothing (Section 3.1.3):
+ *   b_n (x)_s b_{n+1} (x)_s ... (x)_s b_{N-1},  n = 0..N-1  (in place; N elements here).
+ * Element n is (E_n, g_n, L_n = sqrt(L_n)); device arrays E, L: N x D x D, g: N x D.  For
+ * smoothing elements built as in Eq. sqrt-smoothing-elements the outputs g, L are the
+ * smoothing means and square-root covariances.  want_L = 0 skips the covariance part (L may be
+ * NULL).  Asynchronous.  Errors as pit_filter_scan. */
+int32_t pit_smooth_scan(int64_t N, int32_t D, int32_t dtype, void* E, void* g, void* L,
+                        int32_t want_L, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- the solver (Algorithm 2) ------------------------------------------------------------ */
+
+/* Bytes of device workspace pit_solve needs for this problem. */
+int32_t pit_solve_workspace_size(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                                 const pit_opts* opts, size_t* bytes);
+
+/* ParaIEKS (Algorithm 2): exact initial state (Eq. mu0), constant initial trajectory
+ * eta_n = mu0 (or `init_traj`), then repeat { linearise at all n (Section 3.2.1); time-parallel
+ * square-root filter and smoother (Algorithm 1) } until the stopping rule of pit_opts holds or
+ * max_iter iterations ran.  The quasi-MLE diffusion sigma^2 = (1/(N d)) sum_n ||sqrtS_n^-1 r_n||^2
+ * of the final iteration's filter pass (Section 2.4) rescales the covariances when calibrate
+ * is set; means do not depend on sigma.
+ *   ode, grid, q, y0   problem (host); y0 has d values; 1 <= q <= 3 for the compiled kernels
+ *   opts               host, NULL = defaults
+ *   init_traj          optional device (N+1) x D warm-start trajectory in original
+ *                      coordinates, of `dtype`; NULL = Algorithm 2's constant guess
+ *   mean               device, (N+1) x D, `dtype`: smoothing means E[Y(t_n)], original coords
+ *   sqrtcov            device, (N+1) x D x D, `dtype` (or NULL when want_cov = 0): square-root
+ *                      covariances (calibrated), original coordinates
+ *   info               host, may be NULL
+ *   workspace          device, >= pit_solve_workspace_size bytes, 256-byte aligned
+ * Work runs on `stream`; the call synchronises the stream once per iteration to read the
+ * convergence scalar (once at the end with fixed_iters) and returns when the outputs are
+ * complete.  Errors: PIT_EINVAL, PIT_EUNSUPPORTED (family/d/q without compiled kernels),
+ * PIT_ENOMEM, PIT_ECUDA, PIT_ENONFINITE; PIT_ENOCONV when max_iter ran out (outputs hold the
+ * last iterate). */
+int32_t pit_solve(const pit_ode* ode, const pit_grid* grid, int32_t q, const double* y0,
+                  const pit_opts* opts, const void* init_traj, void* mean, void* sqrtcov,
+                  pit_solve_info* info, void* workspace, size_t ws_bytes, void* stream);
+
+/* Sequential extended Kalman smoother with local linearisation at the predicted mean (the
+ * established sequential solver the paper compares against, Sections 2.3 and 4.3): one
+ * forward filter pass and one backward RTS pass, strictly in time order, one thread group on
+ * the GPU.  Same arguments and outputs as pit_solve (no iteration; opts->max_iter and the stop
+ * rule are ignored); workspace size from pit_eks_workspace_size. */
+int32_t pit_eks_workspace_size(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                               const pit_opts* opts, size_t* bytes);
+int32_t pit_eks_sequential(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                           const double* y0, const pit_opts* opts, void* mean, void* sqrtcov,
+                           pit_solve_info* info, void* workspace, size_t ws_bytes,
+                           void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIT_H_ */

@@ -1,0 +1,313 @@
+"""Python binding of the GB300 parallel-in-time probabilistic ODE solver (libpit.so).
+
+Argument marshalling only: every step of the solver runs in the CUDA library behind the C ABI
+of include/pit.h.  PyTorch provides device memory and streams.  Function names mirror the C
+entry points (pit_solve, pit_filter_scan, ...).  If libpit.so is missing this module raises on
+first use -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpit.so")
+
+PIT_F32, PIT_F64 = 0, 1
+
+STATUS = {0: "PIT_OK", 1: "PIT_EINVAL", 2: "PIT_ENOMEM", 3: "PIT_ECUDA", 4: "PIT_ENOCONV",
+          5: "PIT_ETIMEOUT", 6: "PIT_ENONFINITE", 7: "PIT_EINTERNAL", 8: "PIT_EUNSUPPORTED"}
+
+
+class PitError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Ode(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("d", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("n_params", ctypes.c_int32)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double), ("t1", ctypes.c_double), ("N", ctypes.c_int64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
+                ("atol_delta", ctypes.c_double), ("rtol_delta", ctypes.c_double),
+                ("dtype", ctypes.c_int32), ("calibrate", ctypes.c_int32),
+                ("want_cov", ctypes.c_int32), ("chain_len", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+# exported symbols and their signatures (declared in include/pit.h)
+_P, _I32, _I64, _SZ, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "pit_version": (ctypes.c_char_p, []),
+    "pit_status_string": (ctypes.c_char_p, [_I32]),
+    "pit_last_error": (ctypes.c_char_p, []),
+    "pit_launch_count": (_I64, []),
+    "pit_opts_default": (None, [ctypes.POINTER(_Opts)]),
+    "pit_prior": (_I32, [_I32, _D, _DP, _DP, _DP, _DP, _DP]),
+    "pit_init_state": (_I32, [ctypes.POINTER(_Ode), _I32, _DP, _DP]),
+    "pit_linearize": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _I32, _P, _P, _P, _P]),
+    "pit_filter_scan_workspace_size": (_I32, [_I64, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "pit_filter_scan": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "pit_smooth_scan_workspace_size": (_I32, [_I64, _I32, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "pit_smooth_scan": (_I32, [_I64, _I32, _I32, _P, _P, _P, _I32, _P, _SZ, _P]),
+    "pit_solve_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
+                                        ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
+    "pit_solve": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
+                         ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P, _SZ, _P]),
+    "pit_eks_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
+                                      ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
+    "pit_eks_sequential": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
+                                  ctypes.POINTER(_Opts), _P, _P, ctypes.POINTER(_Info), _P, _SZ,
+                                  _P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libpit.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_2310_01145_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise PitError(st, f"{what}: {load().pit_last_error().decode()}")
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dtype_code(dtype) -> int:
+    import torch
+    if dtype in (torch.float64, "f64", "float64", PIT_F64):
+        return PIT_F64
+    if dtype in (torch.float32, "f32", "float32", PIT_F32):
+        return PIT_F32
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _torch_dtype(code: int):
+    import torch
+    return torch.float64 if code == PIT_F64 else torch.float32
+
+
+@dataclasses.dataclass
+class Ode:
+    """Vector field description (see pit_ode_kind in pit.h)."""
+    kind: int
+    d: int
+    params: np.ndarray
+
+    def c(self):
+        self._p = np.ascontiguousarray(self.params, dtype=np.float64)
+        return _Ode(self.kind, self.d,
+                    self._p.ctypes.data_as(_DP) if self._p.size else ctypes.cast(None, _DP),
+                    int(self._p.size))
+
+
+def ode_from_problem(problem) -> Ode:
+    return Ode(problem.kind, problem.d, np.asarray(problem.params, dtype=np.float64))
+
+
+def pit_opts_default() -> _Opts:
+    o = _Opts()
+    load().pit_opts_default(ctypes.byref(o))
+    return o
+
+
+def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
+              calibrate=True, want_cov=True, chain_len=0) -> _Opts:
+    o = pit_opts_default()
+    o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
+    o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
+    o.dtype = _dtype_code(dtype)
+    o.calibrate, o.want_cov, o.chain_len = int(bool(calibrate)), int(bool(want_cov)), int(chain_len)
+    return o
+
+
+def pit_version() -> str:
+    return load().pit_version().decode()
+
+
+def pit_launch_count() -> int:
+    return int(load().pit_launch_count())
+
+
+def pit_prior(q: int, h: float):
+    """Host FP64 prior blocks: dict of Phi, Q, Phibar, sqrtQbar ((q+1)^2) and Tdiag (q+1)."""
+    K = q + 1
+    out = {k: np.zeros((K, K)) for k in ("Phi", "Q", "Phibar", "sqrtQbar")}
+    out["Tdiag"] = np.zeros(K)
+    _check(load().pit_prior(q, h, _dptr(out["Phi"]), _dptr(out["Q"]), _dptr(out["Phibar"]),
+                            _dptr(out["sqrtQbar"]), _dptr(out["Tdiag"])), "pit_prior")
+    return out
+
+
+def pit_init_state(ode: Ode, q: int, y0) -> np.ndarray:
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    mu0 = np.zeros(ode.d * (q + 1))
+    c = ode.c()
+    _check(load().pit_init_state(ctypes.byref(c), q, _dptr(y), _dptr(mu0)), "pit_init_state")
+    return mu0
+
+
+def pit_linearize(ode: Ode, t0: float, t1: float, N: int, q: int, traj, stream=None):
+    """H (N, d, D) and dvec (N, d) at the device trajectory traj ((N+1, D))."""
+    import torch
+    code = _dtype_code(traj.dtype)
+    D = ode.d * (q + 1)
+    H = torch.empty((N, ode.d, D), dtype=traj.dtype, device=traj.device)
+    dv = torch.empty((N, ode.d), dtype=traj.dtype, device=traj.device)
+    c, gr = ode.c(), _Grid(t0, t1, N)
+    _check(load().pit_linearize(ctypes.byref(c), ctypes.byref(gr), q, code, _tptr(traj.contiguous()),
+                                _tptr(H), _tptr(dv), _stream_ptr(stream)), "pit_linearize")
+    return H, dv
+
+
+def _workspace(nbytes: int, device):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def pit_filter_scan(A, b, C, eta, J, stream=None):
+    """In-place inclusive scan of filtering elements (tensors on one CUDA device)."""
+    N, D = b.shape
+    code = _dtype_code(b.dtype)
+    sz = ctypes.c_size_t(0)
+    _check(load().pit_filter_scan_workspace_size(N, D, code, ctypes.byref(sz)),
+           "pit_filter_scan_workspace_size")
+    ws = _workspace(sz.value, b.device)
+    for t in (A, b, C, eta, J):
+        assert t.is_contiguous() and t.dtype == b.dtype
+    _check(load().pit_filter_scan(N, D, code, _tptr(A), _tptr(b), _tptr(C), _tptr(eta), _tptr(J),
+                                  _tptr(ws), ws.numel(), _stream_ptr(stream)), "pit_filter_scan")
+    return A, b, C, eta, J
+
+
+def pit_smooth_scan(E, g, L=None, stream=None):
+    """In-place reverse inclusive scan of smoothing elements."""
+    N, D = g.shape
+    code = _dtype_code(g.dtype)
+    want_L = 1 if L is not None else 0
+    sz = ctypes.c_size_t(0)
+    _check(load().pit_smooth_scan_workspace_size(N, D, code, want_L, ctypes.byref(sz)),
+           "pit_smooth_scan_workspace_size")
+    ws = _workspace(sz.value, g.device)
+    _check(load().pit_smooth_scan(N, D, code, _tptr(E), _tptr(g), _tptr(L), want_L, _tptr(ws),
+                                  ws.numel(), _stream_ptr(stream)), "pit_smooth_scan")
+    return E, g, L
+
+
+@dataclasses.dataclass
+class SolveResult:
+    mean: "object"          # torch tensor (N+1, D)
+    sqrtcov: "object"       # torch tensor (N+1, D, D) or None
+    iterations: int
+    converged: bool
+    last_delta: float
+    sigma2: float
+    kernel_launches: int
+    status: int
+
+
+def _solve_like(fn_ws, fn_run, ode: Ode, y0, t0, t1, N, q, opts: _Opts, init_traj=None,
+                device=None, stream=None, workspace=None, out=None, allow_noconv=True,
+                is_eks=False):
+    import torch
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    c, gr = ode.c(), _Grid(float(t0), float(t1), int(N))
+    sz = ctypes.c_size_t(0)
+    _check(fn_ws(ctypes.byref(c), ctypes.byref(gr), int(q), ctypes.byref(opts), ctypes.byref(sz)),
+           "workspace_size")
+    if workspace is None or workspace.numel() < sz.value:
+        workspace = _workspace(sz.value, device)
+    tdt = _torch_dtype(opts.dtype)
+    D = ode.d * (q + 1)
+    if out is None:
+        mean = torch.empty((N + 1, D), dtype=tdt, device=device)
+        cov = torch.empty((N + 1, D, D), dtype=tdt, device=device) if opts.want_cov else None
+    else:
+        mean, cov = out
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    info = _Info()
+    if is_eks:
+        st = fn_run(ctypes.byref(c), ctypes.byref(gr), int(q), _dptr(y), ctypes.byref(opts),
+                    _tptr(mean), _tptr(cov), ctypes.byref(info), _tptr(workspace),
+                    workspace.numel(), _stream_ptr(stream))
+    else:
+        st = fn_run(ctypes.byref(c), ctypes.byref(gr), int(q), _dptr(y), ctypes.byref(opts),
+                    _tptr(init_traj), _tptr(mean), _tptr(cov), ctypes.byref(info),
+                    _tptr(workspace), workspace.numel(), _stream_ptr(stream))
+    if not (st == 0 or (st == 4 and allow_noconv)):
+        _check(st, "pit_solve")
+    return SolveResult(mean, cov, info.iterations, bool(info.converged), info.last_delta,
+                       info.sigma2, int(info.kernel_launches), int(st))
+
+
+def pit_solve(ode: Ode, y0, t0: float, t1: float, N: int, q: int, opts: Optional[_Opts] = None,
+              init_traj=None, device=None, stream=None, workspace=None, out=None,
+              allow_noconv=True) -> SolveResult:
+    """ParaIEKS (Algorithm 2) through the C ABI; outputs are torch tensors on `device`."""
+    lib = load()
+    return _solve_like(lib.pit_solve_workspace_size, lib.pit_solve, ode, y0, t0, t1, N, q,
+                       opts or make_opts(), init_traj, device, stream, workspace, out,
+                       allow_noconv)
+
+
+def pit_eks_sequential(ode: Ode, y0, t0: float, t1: float, N: int, q: int,
+                       opts: Optional[_Opts] = None, device=None, stream=None,
+                       workspace=None, out=None) -> SolveResult:
+    """Sequential EKS with local linearisation (GPU baseline) through the C ABI."""
+    lib = load()
+    return _solve_like(lib.pit_eks_workspace_size, lib.pit_eks_sequential, ode, y0, t0, t1, N,
+                       q, opts or make_opts(), None, device, stream, workspace, out, True,
+                       is_eks=True)
+
+
+def solve_problem(problem, **kw) -> SolveResult:
+    """Convenience wrapper for a workloads.Problem."""
+    opts = kw.pop("opts", None) or make_opts(**{k: kw.pop(k) for k in list(kw)
+                                                if k in ("dtype", "max_iter", "fixed_iters",
+                                                         "atol_delta", "rtol_delta", "calibrate",
+                                                         "want_cov", "chain_len")})
+    return pit_solve(ode_from_problem(problem), problem.y0, problem.t0, problem.t1, problem.N,
+                     problem.q, opts, **kw)

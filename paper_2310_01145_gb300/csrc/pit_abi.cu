@@ -1,0 +1,559 @@
+// C ABI of the solver (declared in include/pit.h): validation, host FP64 prior and initial
+// state, dispatch to the per-configuration kernel sets, pit_linearize.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "pit_internal.h"
+#include "pit_ode.cuh"
+
+namespace pit {
+
+// ---- error state and accounting ----------------------------------------------------------
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const std::string& msg) { g_err = msg; }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---- registry -------------------------------------------------------------------------------
+struct Registry {
+  std::mutex mu;
+  std::map<int, SolveFn> solvers;  // key dtype*10000 + d*100 + q
+  std::map<int, ScanFn> fscans;    // key dtype*100 + D
+  std::map<int, ScanFn> sscans;
+};
+static Registry& registry() {
+  static Registry r;
+  return r;
+}
+Registrar::Registrar(int dtype, int d, int q, SolveFn fn) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.solvers[dtype * 10000 + d * 100 + q] = fn;
+}
+ScanRegistrar::ScanRegistrar(int dtype, int D, ScanFn f, ScanFn s) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.fscans[dtype * 100 + D] = f;
+  r.sscans[dtype * 100 + D] = s;
+}
+SolveFn find_solver(int dtype, int d, int q) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.solvers.find(dtype * 10000 + d * 100 + q);
+  return it == r.solvers.end() ? nullptr : it->second;
+}
+ScanFn find_filter_scan(int dtype, int D) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.fscans.find(dtype * 100 + D);
+  return it == r.fscans.end() ? nullptr : it->second;
+}
+ScanFn find_smooth_scan(int dtype, int D) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.sscans.find(dtype * 100 + D);
+  return it == r.sscans.end() ? nullptr : it->second;
+}
+
+// ---- host FP64 prior (Section 2.1) and preconditioner (Section 2.4) -----------------------
+static double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+static double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  return factorial(n) / (factorial(k) * factorial(n - k));
+}
+
+int prior_blocks(int q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
+                 double* Tdiag) {
+  if (q < 1 || q > 8 || !(h > 0.0) || !std::isfinite(h)) return PIT_EINVAL;
+  const int K = q + 1;
+  double Qb[81];
+  for (int i = 0; i < K; ++i) {
+    for (int j = 0; j < K; ++j) {
+      const int p = 2 * q + 1 - i - j;
+      if (Phi) Phi[i * K + j] = (j >= i) ? std::pow(h, j - i) / factorial(j - i) : 0.0;
+      if (Q) Q[i * K + j] = std::pow(h, p) / (p * factorial(q - i) * factorial(q - j));
+      if (Phibar) Phibar[i * K + j] = (j >= i) ? binom(q - i, j - i) : 0.0;
+      Qb[i * K + j] = 1.0 / p;
+    }
+    if (Tdiag) Tdiag[i] = std::sqrt(h) * std::pow(h, q - i) / factorial(q - i);
+  }
+  if (sqrtQbar) {
+    // Cholesky factor of the (well-conditioned for q <= 8) matrix Qbar, lower-triangular
+    for (int i = 0; i < K * K; ++i) sqrtQbar[i] = 0.0;
+    for (int j = 0; j < K; ++j) {
+      double s = Qb[j * K + j];
+      for (int k = 0; k < j; ++k) s -= sqrtQbar[j * K + k] * sqrtQbar[j * K + k];
+      if (!(s > 0.0)) return PIT_EINTERNAL;
+      const double djj = std::sqrt(s);
+      sqrtQbar[j * K + j] = djj;
+      for (int i = j + 1; i < K; ++i) {
+        double t = Qb[i * K + j];
+        for (int k = 0; k < j; ++k) t -= sqrtQbar[i * K + k] * sqrtQbar[j * K + k];
+        sqrtQbar[i * K + j] = t / djj;
+      }
+    }
+  }
+  return PIT_OK;
+}
+
+// ---- exact initial state by Taylor-series recursion (Eq. mu0) ------------------------------
+namespace {
+constexpr int kMaxOrd = 10;
+struct Ser {
+  double c[kMaxOrd];
+};
+Ser s_const(double v) {
+  Ser s{};
+  s.c[0] = v;
+  return s;
+}
+Ser s_add(const Ser& a, const Ser& b) {
+  Ser s;
+  for (int k = 0; k < kMaxOrd; ++k) s.c[k] = a.c[k] + b.c[k];
+  return s;
+}
+Ser s_sub(const Ser& a, const Ser& b) {
+  Ser s;
+  for (int k = 0; k < kMaxOrd; ++k) s.c[k] = a.c[k] - b.c[k];
+  return s;
+}
+Ser s_scale(const Ser& a, double f) {
+  Ser s;
+  for (int k = 0; k < kMaxOrd; ++k) s.c[k] = a.c[k] * f;
+  return s;
+}
+Ser s_mul(const Ser& a, const Ser& b) {
+  Ser s{};
+  for (int k = 0; k < kMaxOrd; ++k)
+    for (int j = 0; j <= k; ++j) s.c[k] += a.c[j] * b.c[k - j];
+  return s;
+}
+// f applied to series y[0..d-1]
+void f_series(const Problem& pb, const Ser* y, Ser* out) {
+  const double* p = pb.params;
+  switch (pb.kind) {
+    case PIT_ODE_LOGISTIC:
+      out[0] = s_scale(s_mul(y[0], s_sub(s_const(1.0), y[0])), p[0]);
+      break;
+    case PIT_ODE_FITZHUGH_NAGUMO: {
+      const double a = p[0], b = p[1], c = p[2];
+      Ser v3 = s_mul(s_mul(y[0], y[0]), y[0]);
+      out[0] = s_scale(s_add(s_sub(y[0], s_scale(v3, 1.0 / 3.0)), y[1]), c);
+      out[1] = s_scale(s_add(s_sub(y[0], s_const(a)), s_scale(y[1], b)), -1.0 / c);
+      break;
+    }
+    case PIT_ODE_LOTKA_VOLTERRA: {
+      Ser xy = s_mul(y[0], y[1]);
+      out[0] = s_sub(s_scale(y[0], p[0]), s_scale(xy, p[1]));
+      out[1] = s_sub(s_scale(xy, p[3]), s_scale(y[1], p[2]));
+      break;
+    }
+    case PIT_ODE_VAN_DER_POL: {
+      Ser one_m = s_sub(s_const(1.0), s_mul(y[0], y[0]));
+      out[0] = y[1];
+      out[1] = s_scale(s_sub(s_mul(one_m, y[1]), y[0]), p[0]);
+      break;
+    }
+    case PIT_ODE_RIGID_BODY:
+      out[0] = s_scale(s_mul(y[1], y[2]), -2.0);
+      out[1] = s_scale(s_mul(y[0], y[2]), 1.25);
+      out[2] = s_scale(s_mul(y[0], y[1]), -0.5);
+      break;
+    case PIT_ODE_AFFINE: {
+      const int d = pb.d;
+      for (int i = 0; i < d; ++i) {
+        Ser acc = s_const(p[d * d + i]);
+        for (int j = 0; j < d; ++j) acc = s_add(acc, s_scale(y[j], p[i * d + j]));
+        out[i] = acc;
+      }
+      break;
+    }
+    case PIT_ODE_LORENZ96: {
+      const int d = pb.d;
+      for (int i = 0; i < d; ++i) {
+        Ser t = s_mul(s_sub(y[(i + 1) % d], y[(i - 2 + d) % d]), y[(i - 1 + d) % d]);
+        out[i] = s_add(s_sub(t, y[i]), s_const(p[0]));
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+}  // namespace
+
+int taylor_init(const Problem& pb, double* mu0) {
+  const int d = pb.d, q = pb.q;
+  if (q + 1 > kMaxOrd || d > 16) return PIT_EINVAL;
+  Ser y[16], fy[16];
+  for (int i = 0; i < d; ++i) y[i] = s_const(pb.y0[i]);
+  for (int k = 0; k < q; ++k) {
+    f_series(pb, y, fy);
+    for (int i = 0; i < d; ++i) y[i].c[k + 1] = fy[i].c[k] / (k + 1);
+  }
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k <= q; ++k) mu0[i * (q + 1) + k] = factorial(k) * y[i].c[k];
+  return PIT_OK;
+}
+
+// ---- validation ------------------------------------------------------------------------------
+static int expected_params(int kind, int d) {
+  switch (kind) {
+    case PIT_ODE_LOGISTIC: return 1;
+    case PIT_ODE_FITZHUGH_NAGUMO: return 3;
+    case PIT_ODE_LOTKA_VOLTERRA: return 4;
+    case PIT_ODE_LORENZ96: return 1;
+    case PIT_ODE_AFFINE: return d * d + d;
+    case PIT_ODE_RIGID_BODY: return 0;
+    case PIT_ODE_VAN_DER_POL: return 1;
+    default: return -1;
+  }
+}
+static int expected_d(int kind, int d) {
+  switch (kind) {
+    case PIT_ODE_LOGISTIC: return 1;
+    case PIT_ODE_FITZHUGH_NAGUMO:
+    case PIT_ODE_LOTKA_VOLTERRA:
+    case PIT_ODE_VAN_DER_POL: return 2;
+    case PIT_ODE_RIGID_BODY: return 3;
+    case PIT_ODE_AFFINE: return (d >= 1 && d <= 16) ? d : -1;
+    case PIT_ODE_LORENZ96: return (d >= 4 && d <= 16) ? d : -1;
+    default: return -1;
+  }
+}
+
+static int fill_problem(const pit_ode* ode, int q, const double* y0, Problem& pb,
+                        bool need_y0 = true) {
+  if (!ode) {
+    set_error("ode is NULL");
+    return PIT_EINVAL;
+  }
+  std::memset(&pb, 0, sizeof(pb));
+  pb.kind = ode->kind;
+  pb.d = ode->d;
+  pb.q = q;
+  if (expected_d(ode->kind, ode->d) != ode->d) {
+    set_error("unknown ODE family or dimension d not valid for it");
+    return PIT_EINVAL;
+  }
+  const int np = expected_params(ode->kind, ode->d);
+  if (np < 0 || ode->n_params != np || (np > 0 && !ode->params) || np > 32) {
+    set_error("n_params / params do not match the ODE family");
+    return PIT_EINVAL;
+  }
+  for (int i = 0; i < np; ++i) {
+    if (!std::isfinite(ode->params[i])) {
+      set_error("non-finite ODE parameter");
+      return PIT_EINVAL;
+    }
+    pb.params[i] = ode->params[i];
+  }
+  pb.n_params = np;
+  if (q < 1 || q > 8) {
+    set_error("prior order q must be in 1..8");
+    return PIT_EINVAL;
+  }
+  if (need_y0) {
+    if (!y0) {
+      set_error("y0 is NULL");
+      return PIT_EINVAL;
+    }
+    for (int i = 0; i < ode->d; ++i) {
+      if (!std::isfinite(y0[i])) {
+        set_error("non-finite y0");
+        return PIT_EINVAL;
+      }
+      pb.y0[i] = y0[i];
+    }
+  }
+  return PIT_OK;
+}
+
+static int fill_grid(const pit_grid* grid, Problem& pb) {
+  if (!grid) {
+    set_error("grid is NULL");
+    return PIT_EINVAL;
+  }
+  if (!(grid->N >= 1) || grid->N > (int64_t(1) << 31) - 2) {
+    set_error("grid N must be in 1..2^31-2");
+    return PIT_EINVAL;
+  }
+  if (!std::isfinite(grid->t0) || !std::isfinite(grid->t1) || !(grid->t1 > grid->t0)) {
+    set_error("grid needs finite t0 < t1");
+    return PIT_EINVAL;
+  }
+  pb.t0 = grid->t0;
+  pb.t1 = grid->t1;
+  pb.N = grid->N;
+  return PIT_OK;
+}
+
+static int check_opts(const pit_opts* in, pit_opts& o) {
+  pit_opts_default(&o);
+  if (in) o = *in;
+  if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||
+      (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20)) {
+    set_error("invalid pit_opts");
+    return PIT_EINVAL;
+  }
+  return PIT_OK;
+}
+
+// ---- pit_linearize kernel ---------------------------------------------------------------------
+template <typename T, int DD>
+__global__ void k_linearize(OdeParams<T> ode, int64_t N, int Q1, double t0, double h,
+                            const T* __restrict__ traj, T* __restrict__ H, T* __restrict__ dv) {
+  const int D = DD * Q1;
+  for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    T y[DD], f[DD], F[DD][DD];
+    for (int k = 0; k < DD; ++k) y[k] = traj[n * D + k * Q1];
+    ode_eval<T, DD>(ode, y, f, F);
+    T* Hn = H + (n - 1) * DD * D;
+    for (int k = 0; k < DD; ++k) {
+      T acc = f[k];
+      for (int c = 0; c < D; ++c) Hn[k * D + c] = T(0);
+      Hn[k * D + k * Q1 + 1] = T(1);
+      for (int m = 0; m < DD; ++m) {
+        Hn[k * D + m * Q1] -= F[k][m];
+        acc -= F[k][m] * y[m];
+      }
+      dv[(n - 1) * DD + k] = acc;
+    }
+  }
+}
+
+template <typename T, int DD>
+static int launch_linearize(const Problem& pb, const void* traj, void* H, void* dv,
+                            cudaStream_t s) {
+  OdeParams<T> op;
+  std::memset(&op, 0, sizeof(op));
+  op.kind = pb.kind;
+  op.d = pb.d;
+  for (int i = 0; i < pb.n_params; ++i) op.p[i] = static_cast<T>(pb.params[i]);
+  const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>((pb.N + 255) / 256, 152 * 16));
+  k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h,
+                                           static_cast<const T*>(traj), static_cast<T*>(H),
+                                           static_cast<T*>(dv));
+  count_launches(1);
+  PIT_CUDA_TRY(cudaGetLastError());
+  return PIT_OK;
+}
+
+}  // namespace pit
+
+using namespace pit;
+
+extern "C" {
+
+const char* pit_version(void) { return "pit 0.1 sm_103a"; }
+
+const char* pit_status_string(int32_t s) {
+  switch (s) {
+    case PIT_OK: return "ok";
+    case PIT_EINVAL: return "invalid argument";
+    case PIT_ENOMEM: return "workspace too small";
+    case PIT_ECUDA: return "CUDA runtime error";
+    case PIT_ENOCONV: return "stopping rule not met within max_iter";
+    case PIT_ETIMEOUT: return "bounded device wait expired";
+    case PIT_ENONFINITE: return "non-finite value in the computation";
+    case PIT_EINTERNAL: return "internal error";
+    case PIT_EUNSUPPORTED: return "configuration not compiled";
+    default: return "unknown status";
+  }
+}
+
+const char* pit_last_error(void) { return g_err.c_str(); }
+
+int64_t pit_launch_count(void) { return launches_total(); }
+
+void pit_opts_default(pit_opts* o) {
+  if (!o) return;
+  o->max_iter = 20;
+  o->fixed_iters = 0;
+  o->atol_delta = 1e-10;
+  o->rtol_delta = 0.0;
+  o->dtype = PIT_F64;
+  o->calibrate = 1;
+  o->want_cov = 1;
+  o->chain_len = 0;
+}
+
+int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
+                  double* Tdiag) {
+  g_err.clear();
+  const int st = prior_blocks(q, h, Phi, Q, Phibar, sqrtQbar, Tdiag);
+  if (st != PIT_OK) set_error("pit_prior: need 1 <= q <= 8 and finite h > 0");
+  return st;
+}
+
+int32_t pit_init_state(const pit_ode* ode, int32_t q, const double* y0, double* mu0) {
+  g_err.clear();
+  Problem pb;
+  int st = fill_problem(ode, q, y0, pb);
+  if (st != PIT_OK) return st;
+  if (!mu0) {
+    set_error("mu0 is NULL");
+    return PIT_EINVAL;
+  }
+  return taylor_init(pb, mu0);
+}
+
+int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
+                      const void* traj, void* H, void* dvec, void* stream) {
+  g_err.clear();
+  Problem pb;
+  int st = fill_problem(ode, q, nullptr, pb, false);
+  if (st != PIT_OK) return st;
+  st = fill_grid(grid, pb);
+  if (st != PIT_OK) return st;
+  if (!traj || !H || !dvec || (dtype != PIT_F32 && dtype != PIT_F64)) {
+    set_error("pit_linearize: null buffer or bad dtype");
+    return PIT_EINVAL;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool f64 = dtype == PIT_F64;
+  switch (pb.d) {
+    case 1: return f64 ? launch_linearize<double, 1>(pb, traj, H, dvec, s)
+                       : launch_linearize<float, 1>(pb, traj, H, dvec, s);
+    case 2: return f64 ? launch_linearize<double, 2>(pb, traj, H, dvec, s)
+                       : launch_linearize<float, 2>(pb, traj, H, dvec, s);
+    case 3: return f64 ? launch_linearize<double, 3>(pb, traj, H, dvec, s)
+                       : launch_linearize<float, 3>(pb, traj, H, dvec, s);
+    default:
+      set_error("pit_linearize: compiled for d <= 3");
+      return PIT_EUNSUPPORTED;
+  }
+}
+
+static int32_t scan_common(bool filter, int64_t N, int32_t D, int32_t dtype, void* x0, void* x1,
+                           void* x2, void* x3, void* x4, int want_L, void* ws, size_t wsb,
+                           void* stream, size_t* query) {
+  if (N < 1 || D < 1 || (dtype != PIT_F32 && dtype != PIT_F64)) {
+    set_error("scan: need N >= 1, D >= 1, dtype F32/F64");
+    return PIT_EINVAL;
+  }
+  ScanFn fn = filter ? find_filter_scan(dtype, D) : find_smooth_scan(dtype, D);
+  if (!fn) {
+    set_error("scan: D=" + std::to_string(D) + " not compiled (2, 3, 4, 6, 8)");
+    return PIT_EUNSUPPORTED;
+  }
+  ScanArgs a{N, x0, x1, x2, x3, x4, want_L, ws, wsb, static_cast<cudaStream_t>(stream)};
+  if (query) return fn(a, query);
+  if (!x0 || !x1 || (filter && (!x2 || !x3 || !x4)) || (!filter && want_L && !x2) || !ws) {
+    set_error("scan: null buffer");
+    return PIT_EINVAL;
+  }
+  return fn(a, nullptr);
+}
+
+int32_t pit_filter_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return PIT_EINVAL;
+  return scan_common(true, N, D, dtype, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr,
+                     0, nullptr, bytes);
+}
+
+int32_t pit_filter_scan(int64_t N, int32_t D, int32_t dtype, void* A, void* b, void* C,
+                        void* eta, void* J, void* workspace, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  return scan_common(true, N, D, dtype, A, b, C, eta, J, 0, workspace, ws_bytes, stream,
+                     nullptr);
+}
+
+int32_t pit_smooth_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, int32_t want_L,
+                                       size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return PIT_EINVAL;
+  return scan_common(false, N, D, dtype, nullptr, nullptr, nullptr, nullptr, nullptr, want_L,
+                     nullptr, 0, nullptr, bytes);
+}
+
+int32_t pit_smooth_scan(int64_t N, int32_t D, int32_t dtype, void* E, void* g, void* L,
+                        int32_t want_L, void* workspace, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  return scan_common(false, N, D, dtype, E, g, L, nullptr, nullptr, want_L, workspace, ws_bytes,
+                     stream, nullptr);
+}
+
+static int32_t solve_common(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                            const double* y0, const pit_opts* opts, const void* init_traj,
+                            void* mean, void* sqrtcov, pit_solve_info* info, void* workspace,
+                            size_t ws_bytes, void* stream, size_t* query, bool eks) {
+  SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
+  int st = fill_problem(ode, q, y0, a.pb, query == nullptr);
+  if (st != PIT_OK) return st;
+  st = fill_grid(grid, a.pb);
+  if (st != PIT_OK) return st;
+  st = check_opts(opts, a.opts);
+  if (st != PIT_OK) return st;
+  SolveFn fn = find_solver(a.opts.dtype, a.pb.d, q);
+  if (!fn) {
+    set_error("no compiled kernels for this (dtype, d, q); compiled: d in 1..3, q in 1..3 (d=3: q <= 2)");
+    return PIT_EUNSUPPORTED;
+  }
+  a.init_traj = init_traj;
+  a.mean = mean;
+  a.sqrtcov = sqrtcov;
+  a.info = info;
+  a.workspace = workspace;
+  a.ws_bytes = ws_bytes;
+  a.stream = static_cast<cudaStream_t>(stream);
+  if (query) {
+    if (query) *query = 0;
+    return fn(a, query, eks);
+  }
+  if (!mean || (a.opts.want_cov && !sqrtcov) || !workspace) {
+    set_error("null output or workspace buffer");
+    return PIT_EINVAL;
+  }
+  return fn(a, nullptr, eks);
+}
+
+int32_t pit_solve_workspace_size(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                                 const pit_opts* opts, size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return PIT_EINVAL;
+  return solve_common(ode, grid, q, nullptr, opts, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      0, nullptr, bytes, false);
+}
+
+int32_t pit_solve(const pit_ode* ode, const pit_grid* grid, int32_t q, const double* y0,
+                  const pit_opts* opts, const void* init_traj, void* mean, void* sqrtcov,
+                  pit_solve_info* info, void* workspace, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  return solve_common(ode, grid, q, y0, opts, init_traj, mean, sqrtcov, info, workspace,
+                      ws_bytes, stream, nullptr, false);
+}
+
+int32_t pit_eks_workspace_size(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                               const pit_opts* opts, size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return PIT_EINVAL;
+  return solve_common(ode, grid, q, nullptr, opts, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      0, nullptr, bytes, true);
+}
+
+int32_t pit_eks_sequential(const pit_ode* ode, const pit_grid* grid, int32_t q,
+                           const double* y0, const pit_opts* opts, void* mean, void* sqrtcov,
+                           pit_solve_info* info, void* workspace, size_t ws_bytes,
+                           void* stream) {
+  g_err.clear();
+  return solve_common(ode, grid, q, y0, opts, nullptr, mean, sqrtcov, info, workspace, ws_bytes,
+                      stream, nullptr, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,642 @@
+// Chain kernels of one IEKS iteration and the block-level/grid-level tree scans.
+#pragma once
+
+#include "pit_kernels.cuh"
+
+namespace pit {
+
+constexpr int kThreads = 128;  // threads per block of every chain / tree kernel
+
+template <class C>
+__device__ __forceinline__ int64_t chain_index(int grp_in_block) {
+  return static_cast<int64_t>(blockIdx.x) * (kThreads / C::G) + grp_in_block;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Filter reduce: chain c folds its leaves n = cL+1 .. min(cL+L, N) into the aggregate
+// a_{cL+1} (x)_f ... (x)_f a_{end}; chain 0 starts from the initial state (A = 0, b = mu0,
+// C = 0), the others from the neutral element.  Output: one filter item per chain, with C and J
+// lower-triangular.
+// ---------------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(kThreads)
+k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ traj,
+                typename C::Tp* __restrict__ agg) {
+  using T = typename C::Tp;
+  using GR = typename C::GR;
+  constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  T* scr = smem + grp * C::SCR;
+  LaneConst<C> lc;
+  lc.init(g, p);
+
+  T A[RL][D], b[RL], sC[RL][W], eta[RL], sJ[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      A[l][c] = (chain != 0 && c == r) ? T(1) : T(0);
+      sJ[0][l][c] = T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) sC[l][c] = T(0);
+    b[l] = (chain == 0 && r < D) ? p.mu0[r] : T(0);
+    eta[l] = T(0);
+  }
+  const int64_t n0 = chain * p.L + 1;
+  const int64_t n1 = min(chain * p.L + p.L, p.N);
+  for (int64_t n = n0; n <= n1; ++n) {
+    T Ft[DD][DD], dt[DD];
+    linearize_at<C>(p, traj, n, Ft, dt);
+    // predict the conditional filter: A' = Phi A, b' = Phi b, C- = tria([sqrtQ | Phi sqrtC])
+    publish<GR, D, LDM>(g, A, scr + C::MAT0);
+    publish<GR, W, LDM>(g, sC, scr + C::MAT1);
+    publish_vec(g, b, scr + C::VEC0);
+    g.sync();
+    T Ap[RL][D], bp[RL], tri[1][RL][D], ext[1][RL][W];
+    phi_rows<C, D>(lc, scr + C::MAT0, Ap);
+    phi_rows<C, W>(lc, scr + C::MAT1, ext[0]);
+    phi_vec<C>(lc, scr + C::VEC0, bp);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) tri[0][l][c] = lc.sqrow[l][c];
+    g.sync();
+    lq_tri_ext<GR, 1, W>(g, tri, ext, scr + C::PIV);
+    // update with the linearised observation
+    publish<GR, D, LDM>(g, tri[0], scr + C::MAT0);
+    publish<GR, D, LDM>(g, Ap, scr + C::MAT1);
+    publish_vec(g, bp, scr + C::VEC0);
+    g.sync();
+    T HA[DD][D];
+#pragma unroll
+    for (int kk = 0; kk < DD; ++kk)
+#pragma unroll
+      for (int c = 0; c < D; ++c) HA[kk][c] = hrow_entry<C>(scr + C::MAT1, Ft, kk, c);
+    T HAcol[RL][DD];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const int r = g.valid(l) ? g.row(l) : 0;
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) HAcol[l][kk] = hrow_entry<C>(scr + C::MAT1, Ft, kk, r);
+    }
+    UpdateOut<C> u;
+    sqrt_update<C>(g, scr, tri[0], Ft, dt, sC, u);
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      T acc = bp[l];
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) acc += u.K[l][kk] * u.nu[kk];
+      b[l] = acc;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T a = Ap[l][c];
+#pragma unroll
+        for (int kk = 0; kk < DD; ++kk) a -= u.K[l][kk] * HA[kk][c];
+        A[l][c] = a;
+      }
+    }
+    // information part: G = sqrtS^-1 Htilde A';  J += G^T G (square root), eta += G^T sqrtS^-1 nu
+    T znu[DD];
+    solve_sS<C>(u.sS, u.nu, znu);
+    T Gt[1][RL][DD];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      T z[DD];
+      solve_sS<C>(u.sS, HAcol[l], z);
+      T acc = eta[l];
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) {
+        Gt[0][l][kk] = g.valid(l) ? z[kk] : T(0);
+        acc += z[kk] * znu[kk];
+      }
+      eta[l] = acc;
+    }
+    lq_tri_ext<GR, 1, DD>(g, sJ, Gt, scr + C::PIV);
+  }
+  // triangularise sqrtC (D x W -> D x D lower) and write the chain item
+  T Cfull[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l)
+#pragma unroll
+    for (int c = 0; c < D; ++c) Cfull[0][l][c] = (c < W) ? sC[l][c] : T(0);
+  lq_dense<GR, 1, D, 0, D, 0>(g, Cfull, scr + C::PIV);
+  T* out = agg + chain * C::FA;
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      out[C::F_A + r * D + c] = A[l][c];
+      out[C::F_C + r * D + c] = Cfull[0][l][c];
+      out[C::F_J + r * D + c] = sJ[0][l][c];
+    }
+    out[C::F_B + r] = b[l];
+    out[C::F_ETA + r] = eta[l];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Filter down-sweep: chain c starts from the filtering marginal at n = cL (its exclusive
+// prefix, or the initial state for c = 0) and runs square-root Kalman steps over its leaves.
+// Step n also forms the smoothing element b_{n-1} from the Pi-triangularisation of Eq.
+// sqrt-smoothing-elements (whose top block is the prediction of step n) and folds it into the
+// chain's smoothing aggregate.  The chain owning n = N also emits b_N = (0, m^f_N, sqrtP^f_N).
+// Accumulates the calibration sum (1/(N d) normalisation on the host).
+// ---------------------------------------------------------------------------------------------
+template <class C, bool WITH_L, bool LOCAL_LIN>
+__global__ void __launch_bounds__(kThreads)
+k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ traj,
+              const typename C::Tp* __restrict__ fprefix, typename C::Tp* __restrict__ Es,
+              typename C::Tp* __restrict__ gs, typename C::Tp* __restrict__ Ls,
+              typename C::Tp* __restrict__ sagg, SolveScalars* __restrict__ scal) {
+  using T = typename C::Tp;
+  using GR = typename C::GR;
+  constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  T* scr = smem + grp * C::SCR;
+  LaneConst<C> lc;
+  lc.init(g, p);
+
+  // filter state (m, sqrtP) with sqrtP kept D wide (zero-padded)
+  T m[RL], sP[RL][D];
+  {
+    const T* pre = fprefix + chain * C::FA;
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const int r = g.valid(l) ? g.row(l) : 0;
+      const bool v = g.valid(l);
+      if (chain == 0) {
+        m[l] = v ? p.mu0[r] : T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) sP[l][c] = T(0);
+      } else {
+        m[l] = v ? pre[C::F_B + r] : T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) sP[l][c] = v ? pre[C::F_C + r * D + c] : T(0);
+      }
+    }
+  }
+  // smoothing aggregate (E~, x, L~), starts neutral
+  T Ea[RL][D], xa[RL], La[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      Ea[l][c] = (c == r) ? T(1) : T(0);
+      La[0][l][c] = T(0);
+    }
+    xa[l] = T(0);
+  }
+  double s2acc = 0.0;
+
+  // fold one smoothing element (rows e, entry gg, rows lrow) into the chain aggregate and store it
+  auto emit = [&](int64_t idx, const T (&e)[RL][D], const T (&gg)[RL], const T (&lrow)[RL][D]) {
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      if (!g.valid(l)) continue;
+      const int r = g.row(l);
+#pragma unroll
+      for (int c = 0; c < D; ++c) Es[idx * D * D + r * D + c] = e[l][c];
+      gs[idx * D + r] = gg[l];
+      if constexpr (WITH_L) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) Ls[idx * D * D + r * D + c] = lrow[l][c];
+      }
+    }
+    g.sync();
+    publish<GR, D, LDM>(g, e, scr + C::MAT2);
+    publish_vec(g, gg, scr + C::VEC2);
+    if constexpr (WITH_L) publish<GR, D, LDM>(g, lrow, scr + C::MAT1);
+    g.sync();
+    T Enew[RL][D], ext[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      T acc = xa[l];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Ea[l][k] * scr[C::VEC2 + k];
+      xa[l] = acc;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T a1 = T(0), a2 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          a1 += Ea[l][k] * scr[C::MAT2 + k * LDM + c];
+          if constexpr (WITH_L) a2 += Ea[l][k] * scr[C::MAT1 + k * LDM + c];
+        }
+        Enew[l][c] = a1;
+        ext[0][l][c] = g.valid(l) ? a2 : T(0);
+      }
+    }
+    g.sync();
+    if constexpr (WITH_L) lq_tri_ext<GR, 1, D>(g, La, ext, scr + C::PIV);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Ea[l][c] = Enew[l][c];
+  };
+
+  const int64_t n0 = chain * p.L + 1;
+  const int64_t n1 = min(chain * p.L + p.L, p.N);
+  for (int64_t n = n0; n <= n1; ++n) {
+    T Ft[DD][DD], dt[DD];
+    if constexpr (!LOCAL_LIN) linearize_at<C>(p, traj, n, Ft, dt);
+    publish<GR, D, LDM>(g, sP, scr + C::MAT0);
+    publish_vec(g, m, scr + C::VEC0);
+    g.sync();
+    // Pi input: top rows [sqrtQ | Phi sqrtP], bottom rows [0 | sqrtP]
+    T tri[2][RL][D], ext[2][RL][D], mp[RL];
+    phi_rows<C, D>(lc, scr + C::MAT0, ext[0]);
+    phi_vec<C>(lc, scr + C::VEC0, mp);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        tri[0][l][c] = lc.sqrow[l][c];
+        tri[1][l][c] = T(0);
+        ext[1][l][c] = sP[l][c];
+      }
+    g.sync();
+    lq_tri_ext<GR, 2, D>(g, tri, ext, scr + C::PIV);
+    // Pi11 = tri[0] (= predicted factor of step n), Pi21 = tri[1], remainder ext[1]
+    publish<GR, D, LDM>(g, tri[0], scr + C::MAT0);
+    publish_vec(g, mp, scr + C::VEC0);
+    g.sync();
+    // smoothing element n-1: E = Pi21 Pi11^-1, g = m^f - E m-
+    T e[RL][D], gg[RL], lrow[RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      solve_xL<D, LDM>(scr + C::MAT0, tri[1][l], e[l]);
+      T acc = m[l];
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc -= e[l][c] * scr[C::VEC0 + c];
+      gg[l] = g.valid(l) ? acc : T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (!g.valid(l)) e[l][c] = T(0);
+        lrow[l][c] = T(0);
+      }
+    }
+    if constexpr (WITH_L) {
+      // sqrtL = Pi22 = tria(remainder)
+      T R[1][RL][D];
+#pragma unroll
+      for (int l = 0; l < RL; ++l)
+#pragma unroll
+        for (int c = 0; c < D; ++c) R[0][l][c] = ext[1][l][c];
+      lq_dense<GR, 1, D, 0, D, 0>(g, R, scr + C::PIV);
+#pragma unroll
+      for (int l = 0; l < RL; ++l)
+#pragma unroll
+        for (int c = 0; c < D; ++c) lrow[l][c] = R[0][l][c];
+    }
+    emit(n - 1, e, gg, lrow);
+    if constexpr (LOCAL_LIN) {
+      // sequential EKS: linearise at the predicted mean m-_n (published at VEC0)
+      T y[DD];
+#pragma unroll
+      for (int k = 0; k < DD; ++k) y[k] = p.T0 * scr[C::VEC0 + k * C::Q1];
+      linearize_y<C>(p, y, Ft, dt);
+    }
+    // Kalman update of step n (Pi11 is still published at MAT0, m- at VEC0)
+    T sPn[RL][W];
+    UpdateOut<C> u;
+    sqrt_update<C>(g, scr, tri[0], Ft, dt, sPn, u);
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      T acc = mp[l];
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) acc += u.K[l][kk] * u.nu[kk];
+      m[l] = acc;
+#pragma unroll
+      for (int c = 0; c < D; ++c) sP[l][c] = (c < W) ? sPn[l][c] : T(0);
+    }
+    if (g.gl == 0) {
+      T z[DD];
+      solve_sS<C>(u.sS, u.nu, z);
+      double s = 0.0;
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) s += static_cast<double>(z[kk]) * static_cast<double>(z[kk]);
+      s2acc += s;
+    }
+  }
+  // the chain owning n = N emits b_N = (E = 0, g = m^f_N, sqrtL = tria(sqrtP^f_N))
+  if (chain == p.N / p.L) {
+    T e[RL][D], lrow[RL][D];
+    T R[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        e[l][c] = T(0);
+        R[0][l][c] = sP[l][c];
+      }
+    if constexpr (WITH_L) lq_dense<GR, 1, D, 0, D, 0>(g, R, scr + C::PIV);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) lrow[l][c] = WITH_L ? R[0][l][c] : T(0);
+    T gg[RL];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) gg[l] = g.valid(l) ? m[l] : T(0);
+    emit(p.N, e, gg, lrow);
+  }
+  // write the chain's smoothing aggregate
+  T* out = sagg + chain * C::SA;
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      out[C::S_E + r * D + c] = Ea[l][c];
+      out[C::S_L + r * D + c] = WITH_L ? La[0][l][c] : T(0);
+    }
+    out[C::S_G + r] = xa[l];
+  }
+  if (g.gl == 0 && s2acc != 0.0) atomicAdd(&scal->sigma2_sum, s2acc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Smoothing down-sweep: chain c starts from m^s at its right end (the reverse exclusive prefix,
+// or nothing for the chain holding n = N) and walks its elements backwards:
+//   m^s_n = E_n m^s_{n+1} + g_n,   sqrtP^s_n = tria([sqrtL_n | E_n sqrtP^s_{n+1}])
+// Non-final passes write the new trajectory (preconditioned) and reduce max|change of y|;
+// the covariance pass writes the outputs in original coordinates.
+// ---------------------------------------------------------------------------------------------
+template <class C, bool WITH_L>
+__global__ void __launch_bounds__(kThreads)
+k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
+              const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
+              const typename C::Tp* __restrict__ sprefix,
+              const typename C::Tp* __restrict__ traj_old, typename C::Tp* __restrict__ traj_new,
+              typename C::Tp* __restrict__ mean_out, typename C::Tp* __restrict__ cov_out,
+              SolveScalars* __restrict__ scal) {
+  using T = typename C::Tp;
+  using GR = typename C::GR;
+  constexpr int D = C::D, RL = C::RL, LDM = C::LDM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  T* scr = smem + grp * C::SCR;
+  int rr[RL];
+  bool vv[RL];
+  T Trow[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    vv[l] = g.valid(l);
+    rr[l] = vv[l] ? g.row(l) : 0;
+    Trow[l] = p.Tdiag[rr[l] % C::Q1];
+  }
+  const bool last = (chain == p.N / p.L);
+  T m[RL], sPs[RL][D];
+  {
+    const T* pre = sprefix + chain * C::SA;
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      m[l] = (!last && vv[l]) ? pre[C::S_G + rr[l]] : T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        sPs[l][c] = (WITH_L && !last && vv[l]) ? pre[C::S_L + rr[l] * D + c] : T(0);
+    }
+  }
+  double dmax = 0.0, ymax = 0.0;
+  // quasi-MLE diffusion of this (final) pass: sigma^2 = sum / (N d)
+  const double sigma =
+      (WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD)) : 1.0;
+  const int64_t s0 = chain * p.L;
+  const int64_t s1 = min(chain * p.L + p.L - 1, p.N);
+  for (int64_t n = s1; n >= s0; --n) {
+    publish_vec(g, m, scr + C::VEC0);
+    if constexpr (WITH_L) publish<GR, D, LDM>(g, sPs, scr + C::MAT0);
+    g.sync();
+    T mn[RL];
+    T tri[1][RL][D], ext[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const T* Er = Es + n * D * D + rr[l] * D;
+      T acc = gs[n * D + rr[l]];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Er[k] * scr[C::VEC0 + k];
+      mn[l] = vv[l] ? acc : T(0);
+      if constexpr (WITH_L) {
+        const T* Lr = Ls + n * D * D + rr[l] * D;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          T a2 = T(0);
+#pragma unroll
+          for (int k = 0; k < D; ++k) a2 += Er[k] * scr[C::MAT0 + k * LDM + c];
+          ext[0][l][c] = vv[l] ? a2 : T(0);
+          tri[0][l][c] = vv[l] ? Lr[c] : T(0);
+        }
+      }
+    }
+    g.sync();
+    if constexpr (WITH_L) {
+      lq_tri_ext<GR, 1, D>(g, tri, ext, scr + C::PIV);
+#pragma unroll
+      for (int l = 0; l < RL; ++l)
+#pragma unroll
+        for (int c = 0; c < D; ++c) sPs[l][c] = tri[0][l][c];
+    }
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      m[l] = mn[l];
+      if (!vv[l]) continue;
+      const int r = rr[l];
+      if constexpr (WITH_L) {
+        mean_out[n * D + r] = Trow[l] * mn[l];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          cov_out[n * D * D + r * D + c] = static_cast<T>(sigma) * Trow[l] * sPs[l][c];
+      } else {
+        traj_new[n * D + r] = mn[l];
+        if (r % C::Q1 == 0) {
+          const double ynew = static_cast<double>(p.T0) * static_cast<double>(mn[l]);
+          const double yold =
+              static_cast<double>(p.T0) * static_cast<double>(traj_old[n * D + r]);
+          const double dd = fabs(ynew - yold);
+          dmax = (dd > dmax || dd != dd) ? dd : dmax;
+          ymax = fmax(ymax, fabs(ynew));
+        }
+      }
+    }
+  }
+  if constexpr (!WITH_L) {
+    // reduce over the group (groups past the last chain have returned), one atomic per group
+#pragma unroll
+    for (int o = C::G / 2; o > 0; o >>= 1) {
+      const double od = __shfl_xor_sync(g.mask, dmax, o);
+      const double oy = __shfl_xor_sync(g.mask, ymax, o);
+      dmax = (od > dmax || od != od) ? od : dmax;
+      ymax = fmax(ymax, oy);
+    }
+    if (g.gl == 0) {
+      if (dmax != dmax) {
+        atomicOr(&scal->flags, 1u);
+      } else {
+        atomic_max_nonneg(&scal->delta_max, dmax);
+      }
+      atomic_max_nonneg(&scal->y_max, ymax);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tree scans over items (filter: FA elements, smoothing: SA elements) in blocks of B items.
+// Position p of a level maps to item index p, or to n-1-p when `rev_index` is set (only the
+// bottom level of a reverse scan; upper levels hold block totals in position order).  With
+// REVERSE the operator's operands are swapped so that the result at item k is
+// item_k (x) item_{k+1} (x) ... (the reverse scan of Section 3.1.3).
+// ---------------------------------------------------------------------------------------------
+template <class C, bool FILTER, bool WITH_L>
+struct TreeOps {
+  using T = typename C::Tp;
+  static constexpr int SZ = FILTER ? C::FA : C::SA;
+  static __device__ __forceinline__ void identity(const typename C::GR& g, T* x) {
+    if constexpr (FILTER) set_identity_f<C>(g, x); else set_identity_s<C>(g, x);
+  }
+  // out = earlier (x) later   (forward);  out = later (x)_s earlier  in reverse mode
+  template <bool REVERSE>
+  static __device__ __forceinline__ void op(const typename C::GR& g, const T* earlier,
+                                            const T* later, T* out, T* scr) {
+    if constexpr (FILTER) {
+      combine_f<C, false>(g, earlier, later, out, scr);
+    } else {
+      if constexpr (REVERSE) combine_s<C, WITH_L>(g, later, earlier, out, scr);
+      else combine_s<C, WITH_L>(g, earlier, later, out, scr);
+    }
+  }
+};
+
+__device__ __forceinline__ int64_t tree_item_index(int64_t n, int64_t pos, bool reverse) {
+  return reverse ? (n - 1 - pos) : pos;
+}
+
+// Brent-Kung up-sweep over B items in shared memory (`items`), then (DOWN) Blelloch down-sweep
+// with `prefix` as the block's exclusive prefix.  ngroups groups of the block take the combines.
+template <class C, class OPS, bool REVERSE>
+__device__ void block_tree(typename C::Tp* items, int B, typename C::Tp* tmp,
+                           typename C::Tp* scr, const typename C::GR& g, int grp, int ngroups,
+                           bool up, bool down, const typename C::Tp* prefix) {
+  using T = typename C::Tp;
+  constexpr int SZ = OPS::SZ;
+  if (up) {
+    for (int stride = 1; stride < B; stride *= 2) {
+      const int npairs = B / (2 * stride);
+      for (int pr = grp; pr < npairs; pr += ngroups) {
+        const int i = (pr + 1) * 2 * stride - 1;
+        const int j = i - stride;
+        OPS::template op<REVERSE>(g, items + j * SZ, items + i * SZ, items + i * SZ, scr);
+      }
+      __syncthreads();
+    }
+  }
+  if (down) {
+    if (grp == 0) {
+      if (prefix) copy_item<C, SZ>(g, prefix, items + (B - 1) * SZ);
+      else OPS::identity(g, items + (B - 1) * SZ);
+    }
+    __syncthreads();
+    for (int stride = B / 2; stride >= 1; stride /= 2) {
+      const int npairs = B / (2 * stride);
+      for (int pr = grp; pr < npairs; pr += ngroups) {
+        const int i = (pr + 1) * 2 * stride - 1;
+        const int j = i - stride;
+        T* tj = tmp;
+        copy_item<C, SZ>(g, items + j * SZ, tj);
+        g.sync();
+        copy_item<C, SZ>(g, items + i * SZ, items + j * SZ);
+        g.sync();
+        OPS::template op<REVERSE>(g, items + j * SZ, tj, items + i * SZ, scr);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Up-sweep kernel: block b loads items [b B, (b+1) B) (identity padding), reduces, writes the
+// up-swept block back in place and its total to `totals[b]`.  If `single` (one block covers all
+// items) it also runs the down-sweep with the neutral prefix and writes exclusive prefixes.
+template <class C, class OPS, bool REVERSE>
+__global__ void __launch_bounds__(kThreads)
+k_tree_up(typename C::Tp* __restrict__ items, int64_t n, int B,
+          typename C::Tp* __restrict__ totals, int single, int rev_index) {
+  using T = typename C::Tp;
+  constexpr int SZ = OPS::SZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int ngroups = kThreads / C::G;
+  T* sitems = sm;
+  T* scr = sm + (size_t)B * SZ + grp * (C::SCR + SZ);
+  T* tmp = scr + C::SCR;
+  const int64_t base = (int64_t)blockIdx.x * B;
+  for (int pos = grp; pos < B; pos += ngroups) {
+    const int64_t gp = base + pos;
+    if (gp < n) copy_item<C, SZ>(g, items + tree_item_index(n, gp, rev_index != 0) * SZ, sitems + pos * SZ);
+    else OPS::identity(g, sitems + pos * SZ);
+  }
+  __syncthreads();
+  block_tree<C, OPS, REVERSE>(sitems, B, tmp, scr, g, grp, ngroups, true, single != 0, nullptr);
+  for (int pos = grp; pos < B; pos += ngroups) {
+    const int64_t gp = base + pos;
+    if (gp < n) copy_item<C, SZ>(g, sitems + pos * SZ, items + tree_item_index(n, gp, rev_index != 0) * SZ);
+  }
+  if (!single && grp == 0) copy_item<C, SZ>(g, sitems + (B - 1) * SZ, totals + blockIdx.x * SZ);
+}
+
+// Down-sweep kernel: block b loads its up-swept items and its exclusive prefix
+// `block_prefix[b]`, and writes exclusive prefixes in place.
+template <class C, class OPS, bool REVERSE>
+__global__ void __launch_bounds__(kThreads)
+k_tree_down(typename C::Tp* __restrict__ items, int64_t n, int B,
+            const typename C::Tp* __restrict__ block_prefix, int rev_index) {
+  using T = typename C::Tp;
+  constexpr int SZ = OPS::SZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int ngroups = kThreads / C::G;
+  T* sitems = sm;
+  T* scr = sm + (size_t)B * SZ + grp * (C::SCR + SZ);
+  T* tmp = scr + C::SCR;
+  const int64_t base = (int64_t)blockIdx.x * B;
+  for (int pos = grp; pos < B; pos += ngroups) {
+    const int64_t gp = base + pos;
+    if (gp < n) copy_item<C, SZ>(g, items + tree_item_index(n, gp, rev_index != 0) * SZ, sitems + pos * SZ);
+    else OPS::identity(g, sitems + pos * SZ);
+  }
+  __syncthreads();
+  block_tree<C, OPS, REVERSE>(sitems, B, tmp, scr, g, grp, ngroups, false, true,
+                              block_prefix + blockIdx.x * SZ);
+  for (int pos = grp; pos < B; pos += ngroups) {
+    const int64_t gp = base + pos;
+    if (gp < n) copy_item<C, SZ>(g, sitems + pos * SZ, items + tree_item_index(n, gp, rev_index != 0) * SZ);
+  }
+}
+
+}  // namespace pit

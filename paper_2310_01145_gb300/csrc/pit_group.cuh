@@ -1,0 +1,253 @@
+// Group-cooperative dense linear algebra on small square-root factors.
+//
+// A *group* is G consecutive lanes of one warp that work on one sequential chain of time steps
+// or on one associative combine.  Every D-row matrix is distributed by rows: lane `gl` of the
+// group owns rows gl*RL .. gl*RL+RL-1 and keeps them in registers.  Rows >= D (padding rows of
+// the last lane) exist, stay zero and are never written to global memory.  Matrices that other
+// lanes need are *published* to the group's shared-memory scratch, then read back after a
+// warp barrier.
+//
+// The triangularisation tria(M) of Section 3.1.2 (QR of M^T, return R^T) is computed here as
+// the equivalent LQ factorisation of M by Householder reflections from the right, one pivot row
+// at a time: reflection i annihilates the entries of row i to the right of column i.  Two
+// variants exploit the structure that occurs in the solver:
+//   lq_tri_ext  -- M = [L | X] with L lower-triangular (D x D) and X dense (D x NE): reflection
+//                  i touches only column i and the NE columns of X;
+//   lq_dense    -- general pivot rows with support from the pivot column to the last column.
+// Diagonal signs of the factors are left as the reflections produce them; every consumer only
+// uses S S^T or solves with the (non-singular) factor, so the sign freedom of tria (its
+// factor is unique only up to column signs) does not matter.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pit {
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x);
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <int N, int A>
+struct RoundUp {
+  static constexpr int value = ((N + A - 1) / A) * A;
+};
+
+// Group geometry.  D rows, G lanes, RL rows per lane.
+template <typename T, int D_, int G_, int RL_>
+struct Grp {
+  static constexpr int D = D_;
+  static constexpr int G = G_;
+  static constexpr int RL = RL_;
+  static constexpr int RP = G_ * RL_;  // padded row count
+  static_assert(G_ * RL_ >= D_, "group too small for D");
+  static_assert(32 % G_ == 0, "group size must divide 32");
+  int gl;         // lane index inside the group
+  unsigned mask;  // lanes of this group within the warp
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+  __device__ __forceinline__ void init() {
+    const int lane = threadIdx.x & 31;
+    gl = lane % G_;
+    const unsigned base = (G_ == 32) ? 0xffffffffu : ((1u << G_) - 1u);
+    mask = (G_ == 32) ? base : (base << (lane - gl));
+  }
+  __device__ __forceinline__ int row(int l) const { return gl * RL_ + l; }
+  __device__ __forceinline__ bool valid(int l) const { return gl * RL_ + l < D_; }
+};
+
+// Publish RL rows of an NC-column register matrix into scratch with leading dimension LD.
+template <class GR, int NC, int LD, typename T>
+__device__ __forceinline__ void publish(const GR& g, const T (&x)[GR::RL][NC], T* buf) {
+#pragma unroll
+  for (int l = 0; l < GR::RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) buf[r * LD + c] = x[l][c];
+  }
+}
+
+template <class GR, typename T>
+__device__ __forceinline__ void publish_vec(const GR& g, const T (&x)[GR::RL], T* buf) {
+#pragma unroll
+  for (int l = 0; l < GR::RL; ++l) buf[g.row(l)] = x[l];
+}
+
+// One Householder reflection from the right.  The pivot row is given by its diagonal entry x0
+// and the remaining support entries xe[0..NE-1]; the reflection maps it to (alpha, 0, ..., 0).
+template <typename T>
+struct Reflector {
+  T v0, tau, alpha;
+  bool active;
+};
+
+template <typename T, int NE>
+__device__ __forceinline__ Reflector<T> make_reflector(T x0, const T (&xe)[NE]) {
+  T sig = T(0);
+#pragma unroll
+  for (int j = 0; j < NE; ++j) sig += xe[j] * xe[j];
+  Reflector<T> h;
+  const T nrm = dsqrt<T>(x0 * x0 + sig);
+  h.alpha = (x0 >= T(0)) ? -nrm : nrm;
+  h.v0 = x0 - h.alpha;
+  const T vtv = h.v0 * h.v0 + sig;
+  h.active = sig > T(0);
+  h.tau = h.active ? T(2) / vtv : T(0);
+  return h;
+}
+
+// ---- structured LQ: [L | X], L lower-triangular ------------------------------------------
+// NS row sets; set 0 provides the D pivots.  tri[s][l][*] are the D "triangular" columns and
+// ext[s][l][*] the NE extra columns of row (s, l).  After the call, set 0 holds the
+// lower-triangular factor in tri and zeros in ext; the other sets hold the transformed rows.
+// `piv` is group scratch of at least 2*(NE+1) elements.
+template <class GR, int NS, int NE, typename T>
+__device__ __forceinline__ void lq_tri_ext(const GR& g, T (&tri)[NS][GR::RL][GR::D],
+                                           T (&ext)[NS][GR::RL][NE], T* piv) {
+  constexpr int D = GR::D;
+  constexpr int RL = GR::RL;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const int owner = i / RL;
+    const int li = i % RL;
+    T* pb = piv + (i & 1) * (NE + 1);
+    if (g.gl == owner) {
+#pragma unroll
+      for (int l = 0; l < RL; ++l) {
+        if (l == li) {
+          pb[0] = tri[0][l][i];
+#pragma unroll
+          for (int j = 0; j < NE; ++j) pb[1 + j] = ext[0][l][j];
+        }
+      }
+    }
+    g.sync();
+    T x0 = pb[0];
+    T xe[NE];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) xe[j] = pb[1 + j];
+    const Reflector<T> h = make_reflector<T, NE>(x0, xe);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+      for (int l = 0; l < RL; ++l) {
+        T dot = tri[s][l][i] * h.v0;
+#pragma unroll
+        for (int j = 0; j < NE; ++j) dot += ext[s][l][j] * xe[j];
+        const T f = h.tau * dot;
+        tri[s][l][i] -= f * h.v0;
+#pragma unroll
+        for (int j = 0; j < NE; ++j) ext[s][l][j] -= f * xe[j];
+        if (s == 0 && l == li && g.gl == owner && h.active) {
+          tri[s][l][i] = h.alpha;
+#pragma unroll
+          for (int j = 0; j < NE; ++j) ext[s][l][j] = T(0);
+        }
+      }
+    }
+  }
+  g.sync();
+}
+
+// ---- dense LQ ----------------------------------------------------------------------------
+// Rows of NS sets with NC columns each.  Pivot rows k = 0..NPIV-1 of set PS, pivot column
+// PC0 + k, support columns PC0+k .. NC-1.  Every row of every set is transformed; after the
+// call pivot row k is (..., alpha_k at column PC0+k, 0, ..., 0).
+template <class GR, int NS, int NC, int PS, int NPIV, int PC0, typename T>
+__device__ __forceinline__ void lq_dense(const GR& g, T (&rows)[NS][GR::RL][NC], T* piv) {
+  constexpr int RL = GR::RL;
+  static_assert(PC0 + NPIV <= NC, "pivot columns out of range");
+#pragma unroll
+  for (int k = 0; k < NPIV; ++k) {
+    const int c0 = PC0 + k;
+    const int owner = k / RL;
+    const int lk = k % RL;
+    T* pb = piv + (k & 1) * NC;
+    if (g.gl == owner) {
+#pragma unroll
+      for (int l = 0; l < RL; ++l) {
+        if (l == lk) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            if (c >= c0) pb[c] = rows[PS][l][c];
+        }
+      }
+    }
+    g.sync();
+    T x[NC];
+    T sig = T(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      x[c] = (c >= c0) ? pb[c] : T(0);
+      if (c > c0) sig += x[c] * x[c];
+    }
+    const T x0 = x[c0];
+    const T nrm = dsqrt<T>(x0 * x0 + sig);
+    const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+    const T v0 = x0 - alpha;
+    const bool active = sig > T(0);
+    const T tau = active ? T(2) / (v0 * v0 + sig) : T(0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+      for (int l = 0; l < RL; ++l) {
+        T dot = rows[s][l][c0] * v0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c > c0) dot += rows[s][l][c] * x[c];
+        const T f = tau * dot;
+        rows[s][l][c0] -= f * v0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c > c0) rows[s][l][c] -= f * x[c];
+        if (s == PS && l == lk && g.gl == owner && active) {
+          rows[s][l][c0] = alpha;
+#pragma unroll
+          for (int c = 0; c < NC; ++c)
+            if (c > c0) rows[s][l][c] = T(0);
+        }
+      }
+    }
+  }
+  g.sync();
+}
+
+// ---- small helpers -------------------------------------------------------------------------
+// Solve x * L^T = y for x (row vector), L lower-triangular D x D in scratch (ld LD):
+//   x[c] = (y[c] - sum_{k<c} x[k] L[c][k]) / L[c][c]     (forward substitution)
+template <int D, int LD, typename T>
+__device__ __forceinline__ void solve_xLt(const T* Lm, const T (&y)[D], T (&x)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    T acc = y[c];
+#pragma unroll
+    for (int k = 0; k < c; ++k) acc -= x[k] * Lm[c * LD + k];
+    x[c] = acc / Lm[c * LD + c];
+  }
+}
+
+// Solve x * L = y for x (row vector), L lower-triangular:
+//   x[c] = (y[c] - sum_{k>c} x[k] L[k][c]) / L[c][c]      (backward substitution)
+template <int D, int LD, typename T>
+__device__ __forceinline__ void solve_xL(const T* Lm, const T (&y)[D], T (&x)[D]) {
+#pragma unroll
+  for (int c = D - 1; c >= 0; --c) {
+    T acc = y[c];
+#pragma unroll
+    for (int k = c + 1; k < D; ++k) acc -= x[k] * Lm[k * LD + c];
+    x[c] = acc / Lm[c * LD + c];
+  }
+}
+
+// Non-negative floating point values as monotone unsigned integers (for atomicMax).
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v) {
+  atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr),
+            static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+}  // namespace pit

@@ -1,0 +1,20 @@
+// Kernel instantiations for F32 arithmetic, ODE dimension d = 2 (generated list; one
+// translation unit per (dtype, d) so that the build compiles them in parallel).
+#include "pit_solve_impl.cuh"
+
+namespace pit {
+namespace {
+int solve_2_1(const SolveArgs& a, size_t* w, bool e) {
+  return SolverImpl<float, 2, 2, 4, 1>::run(a, w, e);
+}
+Registrar reg_2_1(PIT_F32, 2, 1, solve_2_1);
+int solve_2_2(const SolveArgs& a, size_t* w, bool e) {
+  return SolverImpl<float, 2, 3, 8, 1>::run(a, w, e);
+}
+Registrar reg_2_2(PIT_F32, 2, 2, solve_2_2);
+int solve_2_3(const SolveArgs& a, size_t* w, bool e) {
+  return SolverImpl<float, 2, 4, 8, 1>::run(a, w, e);
+}
+Registrar reg_2_3(PIT_F32, 2, 3, solve_2_3);
+}  // namespace
+}  // namespace pit

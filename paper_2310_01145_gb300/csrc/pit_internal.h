@@ -1,0 +1,103 @@
+// Internal host-side interface between the C ABI (pit_abi.cu) and the per-configuration
+// kernel instantiations (pit_inst_*.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pit.h"
+
+namespace pit {
+
+// Problem description after host-side validation.
+struct Problem {
+  int kind;
+  int d;
+  int q;
+  double params[32];
+  int n_params;
+  double t0, t1;
+  int64_t N;
+  double y0[16];
+};
+
+struct SolveArgs {
+  Problem pb;
+  pit_opts opts;
+  const void* init_traj;
+  void* mean;
+  void* sqrtcov;
+  pit_solve_info* info;
+  void* workspace;
+  size_t ws_bytes;
+  cudaStream_t stream;
+};
+
+struct ScanArgs {
+  int64_t N;
+  void* x0;  // A or E
+  void* x1;  // b or g
+  void* x2;  // C or L
+  void* x3;  // eta
+  void* x4;  // J
+  int want_L;
+  void* workspace;
+  size_t ws_bytes;
+  cudaStream_t stream;
+};
+
+// Error reporting (thread-local message) and launch accounting.
+void set_error(const std::string& msg);
+void count_launches(int64_t n);
+int64_t launches_total();
+
+// Host FP64 helpers shared by the instantiations.
+int prior_blocks(int q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
+                 double* Tdiag);
+int taylor_init(const Problem& pb, double* mu0);
+
+// Per-configuration entry points (defined in the pit_inst_*.cu files).
+using SolveFn = int (*)(const SolveArgs&, size_t* ws_query, bool eks);
+using ScanFn = int (*)(const ScanArgs&, size_t* ws_query);
+
+SolveFn find_solver(int dtype, int d, int q);
+ScanFn find_filter_scan(int dtype, int D);
+ScanFn find_smooth_scan(int dtype, int D);
+
+// Registration (each instantiation file registers its functions at static-init time).
+struct Registrar {
+  Registrar(int dtype, int d, int q, SolveFn fn);
+};
+struct ScanRegistrar {
+  ScanRegistrar(int dtype, int D, ScanFn filter_fn, ScanFn smooth_fn);
+};
+
+// Workspace carving: 256-byte aligned bump allocator over a caller buffer.
+struct Carver {
+  char* base;
+  size_t cap;
+  size_t off;
+  explicit Carver(void* b, size_t c) : base(static_cast<char*>(b)), cap(c), off(0) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+  size_t used() const { return (off + 255) & ~size_t(255); }
+};
+
+#define PIT_CUDA_TRY(expr)                                                          \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      ::pit::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));         \
+      return PIT_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+}  // namespace pit

@@ -1,0 +1,602 @@
+// Kernels of the time-parallel IEKS (Algorithms 1 and 2) for small state dimension D = d (q+1).
+//
+// Work decomposition.  The N filtering elements (and N+1 smoothing elements) are cut into
+// chains of L consecutive time steps; one lane group (see pit_group.cuh) walks one chain.
+// Inside a chain the associative operators are applied left to right, which the structure of
+// the elements makes cheap:
+//   * filter reduce:  aggregate (x)_f a_n, where a_n is a rank-d leaf element, is one
+//     square-root Kalman prediction + update of the "conditional" filter (A, b, sqrtC) plus a
+//     rank-d update of the information part (eta, sqrtJ);
+//   * filter down:    (m^f_{n-1}, sqrtP^f_{n-1}) (x)_f a_n is one square-root Kalman step; the
+//     same Pi-triangularisation yields the smoothing element b_{n-1} (Eq.
+//     sqrt-smoothing-elements), which is written out, and the chain's smoothing aggregate;
+//   * smooth down:    m^s_n = E_n m^s_{n+1} + g_n (and the square-root covariance with one
+//     tria) walking the chain backwards.
+// The chain aggregates are combined with the full square-root operators of Eqs.
+// sqrt-associative-filtering / sqrt-associative-smoothing in a work-efficient
+// (Brent-Kung/Blelloch) tree, first inside a thread block in shared memory, then across blocks.
+//
+// Coordinates.  The device works in preconditioned coordinates x = T xbar with
+// T = I_d (x) sqrt(h) diag(h^(q-i)/(q-i)!) (Section 2.4): the transitions become the
+// step-size-free Phibar = binom(q-i, j-i), Qbar = 1/(2q+1-i-j).  The observation rows are scaled
+// by 1/T_1, which leaves the Dirac conditioning unchanged: Htilde = E1 - (h/q) F E0,
+// dtilde = d / T_1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pit_group.cuh"
+#include "pit_ode.cuh"
+
+namespace pit {
+
+constexpr int kMaxQ1 = 8;
+constexpr int kMaxD = 16;
+
+// Per-solve constants (kernel argument).
+template <typename T>
+struct IeksParams {
+  OdeParams<T> ode;
+  int64_t N;        // time steps (observations at n = 1..N)
+  int64_t P;        // chains = N / L + 1
+  int L;            // chain length
+  int want_cov;     // this pass produces square-root covariances
+  int calibrate;    // scale square-root covariances by the quasi-MLE sigma
+  T t0, h;
+  T T0;             // T_0(h): y = T_0 xbar_{k(q+1)}
+  T T1inv;          // 1 / T_1(h)
+  T hq;             // h / q
+  T Tdiag[kMaxQ1];  // T_i(h), i = 0..q
+  T phib[kMaxQ1 * kMaxQ1];   // Phibar (q+1)x(q+1), row-major
+  T sqb[kMaxQ1 * kMaxQ1];    // lower Cholesky factor of Qbar
+  T mu0[kMaxD];              // preconditioned exact initial state
+};
+
+// Scalars shared by the kernels of one solve (device memory, FP64).
+struct SolveScalars {
+  double sigma2_sum;   // sum_n ||sqrtS_n^-1 r_n||^2 of the current filter pass
+  double delta_max;    // max |change of E0 mean| (original coordinates)
+  double y_max;        // max |E0 mean| (original coordinates)
+  unsigned int flags;  // bit 0: non-finite value seen
+  unsigned int pad;
+};
+
+template <typename T, int DD_, int Q1_, int G_, int RL_>
+struct Cfg {
+  using Tp = T;
+  static constexpr int DD = DD_;
+  static constexpr int Q1 = Q1_;
+  static constexpr int D = DD_ * Q1_;
+  static constexpr int W = D - DD_;
+  static constexpr int G = G_;
+  static constexpr int RL = RL_;
+  static constexpr int RP = G_ * RL_;
+  static constexpr int LDM = D;
+  // group scratch layout (elements of T)
+  static constexpr int MAT0 = 0;
+  static constexpr int MAT1 = MAT0 + RP * LDM;
+  static constexpr int MAT2 = MAT1 + RP * LDM;
+  static constexpr int VEC0 = MAT2 + RP * LDM;
+  static constexpr int VEC1 = VEC0 + RP;
+  static constexpr int VEC2 = VEC1 + RP;
+  static constexpr int VEC3 = VEC2 + RP;
+  static constexpr int SV = VEC3 + RP;
+  static constexpr int PIV = SV + RoundUp<(DD_ * DD_ > 1 ? DD_ * DD_ : 1), 2>::value;
+  static constexpr int SCR = RoundUp<PIV + 2 * (2 * D + 1), 4>::value;
+  // item sizes
+  static constexpr int FA = 3 * D * D + 2 * D;   // filter element (A, b, C, eta, J)
+  static constexpr int SA = 2 * D * D + D;       // smoothing element (E, g, L)
+  static constexpr int F_A = 0, F_B = D * D, F_C = D * D + D, F_ETA = 2 * D * D + D,
+                       F_J = 2 * D * D + 2 * D;
+  static constexpr int S_E = 0, S_G = D * D, S_L = D * D + D;
+  using GR = Grp<T, D, G_, RL_>;
+};
+
+// Per-lane constant rows of Phibar and sqrt(Qbar) (I_d (x) blocks).
+template <class C>
+struct LaneConst {
+  using T = typename C::Tp;
+  T phirow[C::RL][C::Q1];  // Phibar1[r % Q1][j], j = 0..Q1-1 (row of the block)
+  T sqrow[C::RL][C::D];    // row r of I_d (x) sqrt(Qbar1)
+  int blk[C::RL];          // first row of r's block
+  __device__ __forceinline__ void init(const typename C::GR& g, const IeksParams<T>& p) {
+#pragma unroll
+    for (int l = 0; l < C::RL; ++l) {
+      const int r = g.row(l);
+      const bool v = r < C::D;
+      const int ir = v ? r % C::Q1 : 0;
+      const int b = v ? (r / C::Q1) * C::Q1 : 0;
+      blk[l] = b;
+#pragma unroll
+      for (int j = 0; j < C::Q1; ++j) phirow[l][j] = v ? p.phib[ir * kMaxQ1 + j] : T(0);
+#pragma unroll
+      for (int c = 0; c < C::D; ++c) {
+        const int cb = (c / C::Q1) * C::Q1;
+        const int jc = c % C::Q1;
+        sqrow[l][c] = (v && cb == b && jc <= ir) ? p.sqb[ir * kMaxQ1 + jc] : T(0);
+      }
+    }
+  }
+};
+
+// Linearisation of the information operator at trajectory row n (Section 3.2.1), returned in
+// scaled preconditioned form: Ft = (h/q) F_y, dt = (f - F_y y) / T_1.
+template <class C>
+__device__ __forceinline__ void linearize_y(const IeksParams<typename C::Tp>& p,
+                                            const typename C::Tp (&y)[C::DD],
+                                            typename C::Tp (&Ft)[C::DD][C::DD],
+                                            typename C::Tp (&dt)[C::DD]) {
+  using T = typename C::Tp;
+  T f[C::DD], F[C::DD][C::DD];
+  ode_eval<T, C::DD>(p.ode, y, f, F);
+#pragma unroll
+  for (int k = 0; k < C::DD; ++k) {
+    T acc = f[k];
+#pragma unroll
+    for (int m = 0; m < C::DD; ++m) acc -= F[k][m] * y[m];
+    dt[k] = acc * p.T1inv;
+#pragma unroll
+    for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * p.hq;
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void linearize_at(const IeksParams<typename C::Tp>& p,
+                                             const typename C::Tp* __restrict__ traj,
+                                             int64_t n, typename C::Tp (&Ft)[C::DD][C::DD],
+                                             typename C::Tp (&dt)[C::DD]) {
+  typename C::Tp y[C::DD];
+#pragma unroll
+  for (int k = 0; k < C::DD; ++k) y[k] = p.T0 * traj[n * C::D + k * C::Q1];
+  linearize_y<C>(p, y, Ft, dt);
+}
+
+// Row kk of Htilde X for X published in scratch (rows of length LDM).
+template <class C>
+__device__ __forceinline__ typename C::Tp hrow_entry(const typename C::Tp* X,
+                                                     const typename C::Tp (&Ft)[C::DD][C::DD],
+                                                     int kk, int c) {
+  typename C::Tp v = X[(kk * C::Q1 + 1) * C::LDM + c];
+#pragma unroll
+  for (int m = 0; m < C::DD; ++m) v -= Ft[kk][m] * X[(m * C::Q1) * C::LDM + c];
+  return v;
+}
+
+// Apply Phibar (block upper-triangular) to a published matrix: out[l][c] = (Phibar X)[r][c].
+template <class C, int NC>
+__device__ __forceinline__ void phi_rows(const LaneConst<C>& lc, const typename C::Tp* X,
+                                         typename C::Tp (&out)[C::RL][NC]) {
+#pragma unroll
+  for (int l = 0; l < C::RL; ++l) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[l][c] = typename C::Tp(0);
+#pragma unroll
+    for (int j = 0; j < C::Q1; ++j) {
+      const typename C::Tp ph = lc.phirow[l][j];
+      const typename C::Tp* xr = X + (lc.blk[l] + j) * C::LDM;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) out[l][c] += ph * xr[c];
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void phi_vec(const LaneConst<C>& lc, const typename C::Tp* x,
+                                        typename C::Tp (&out)[C::RL]) {
+#pragma unroll
+  for (int l = 0; l < C::RL; ++l) {
+    typename C::Tp acc = 0;
+#pragma unroll
+    for (int j = 0; j < C::Q1; ++j) acc += lc.phirow[l][j] * x[lc.blk[l] + j];
+    out[l] = acc;
+  }
+}
+
+// Square-root Kalman update in the scaled observation model (Psi-tria of Eq.
+// sqrt-filtering-elements with sqrt(R) = 0).  Input: the lower-triangular predicted factor
+// Lp (lane rows) already published at scr+MAT0 and the predicted mean published at scr+VEC0.
+// Output: Psi21 columns -> K (gain rows), Psi22 -> sP_new (width W), sqrtS (all lanes),
+// nu = dtilde - Htilde m- (all lanes).
+template <class C>
+struct UpdateOut {
+  using T = typename C::Tp;
+  T K[C::RL][C::DD];
+  T sS[C::DD][C::DD];
+  T nu[C::DD];
+};
+
+template <class C>
+__device__ __forceinline__ void sqrt_update(const typename C::GR& g, typename C::Tp* scr,
+                                            const typename C::Tp (&Lp)[C::RL][C::D],
+                                            const typename C::Tp (&Ft)[C::DD][C::DD],
+                                            const typename C::Tp (&dt)[C::DD],
+                                            typename C::Tp (&sPnew)[C::RL][C::W],
+                                            UpdateOut<C>& u) {
+  using T = typename C::Tp;
+  constexpr int D = C::D, DD = C::DD, RL = C::RL;
+  T U[2][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      U[1][l][c] = Lp[l][c];
+      U[0][l][c] = T(0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < DD; ++kk) {
+      const bool mine = (r == kk);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const T v = hrow_entry<C>(scr + C::MAT0, Ft, kk, c);
+        if (mine) U[0][l][c] = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < DD; ++kk) {
+    T v = scr[C::VEC0 + kk * C::Q1 + 1];
+#pragma unroll
+    for (int m = 0; m < DD; ++m) v -= Ft[kk][m] * scr[C::VEC0 + m * C::Q1];
+    u.nu[kk] = dt[kk] - v;
+  }
+  lq_dense<typename C::GR, 2, D, 0, DD, 0>(g, U, scr + C::PIV);
+  // publish sqrtS (obs rows, first DD columns)
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int kk = 0; kk < DD; ++kk)
+      if (r == kk) {
+#pragma unroll
+        for (int c = 0; c < DD; ++c) scr[C::SV + kk * DD + c] = U[0][l][c];
+      }
+  }
+  g.sync();
+#pragma unroll
+  for (int a = 0; a < DD; ++a)
+#pragma unroll
+    for (int b = 0; b < DD; ++b) u.sS[a][b] = (b <= a) ? scr[C::SV + a * DD + b] : T(0);
+  g.sync();
+  // K = Psi21 sqrtS^-1 :  K[l] sqrtS = Psi21[l]  (backward substitution)
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+#pragma unroll
+    for (int c = DD - 1; c >= 0; --c) {
+      T acc = U[1][l][c];
+#pragma unroll
+      for (int k = c + 1; k < DD; ++k) acc -= u.K[l][k] * u.sS[k][c];
+      u.K[l][c] = acc / u.sS[c][c];
+    }
+#pragma unroll
+    for (int c = 0; c < C::W; ++c) sPnew[l][c] = U[1][l][DD + c];
+  }
+}
+
+// Forward substitution with sqrtS: z = sqrtS^-1 x.
+template <class C>
+__device__ __forceinline__ void solve_sS(const typename C::Tp (&sS)[C::DD][C::DD],
+                                         const typename C::Tp (&x)[C::DD],
+                                         typename C::Tp (&z)[C::DD]) {
+#pragma unroll
+  for (int a = 0; a < C::DD; ++a) {
+    typename C::Tp acc = x[a];
+#pragma unroll
+    for (int b = 0; b < a; ++b) acc -= sS[a][b] * z[b];
+    z[a] = acc / sS[a][a];
+  }
+}
+
+// =============================================================================================
+// Full associative operators on items in shared memory (group-cooperative).
+// =============================================================================================
+
+// a_out = a_l (x)_f a_r   (Eq. sqrt-associative-filtering).  Items: [A | b | C | eta | J].
+// C of the right operand and J of the left operand must be lower-triangular (true for every
+// item the library produces: tria outputs, identity, triangularised inputs).
+// a_out may alias a_r or a_l (writes happen after all reads).  VALUES_ONLY skips A, eta, J.
+template <class C, bool VALUES_ONLY = false>
+__device__ void combine_f(const typename C::GR& g, const typename C::Tp* al,
+                          const typename C::Tp* ar, typename C::Tp* aout,
+                          typename C::Tp* scr) {
+  using T = typename C::Tp;
+  constexpr int D = C::D, RL = C::RL, LDM = C::LDM;
+  const T* Ai = al + C::F_A;
+  const T* bi = al + C::F_B;
+  const T* Ci = al + C::F_C;
+  const T* ei = al + C::F_ETA;
+  const T* Ji = al + C::F_J;
+  const T* Aj = ar + C::F_A;
+  const T* bj = ar + C::F_B;
+  const T* Cj = ar + C::F_C;
+  const T* ej = ar + C::F_ETA;
+  const T* Jj = ar + C::F_J;
+  int rr[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) rr[l] = g.valid(l) ? g.row(l) : 0;
+  // 1. Xi input: top rows [Ci^T Jj | I], bottom rows [Jj | 0]; 2D columns.
+  T X[2][RL][2 * D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = rr[l];
+    const bool v = g.valid(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Ci[k * D + r] * Jj[k * D + c];
+      X[0][l][c] = v ? acc : T(0);
+      X[0][l][D + c] = (v && c == r) ? T(1) : T(0);
+      X[1][l][c] = v ? Jj[r * D + c] : T(0);
+      X[1][l][D + c] = T(0);
+    }
+  }
+  lq_dense<typename C::GR, 2, 2 * D, 0, D, 0>(g, X, scr + C::PIV);
+  lq_dense<typename C::GR, 2, 2 * D, 1, D, D>(g, X, scr + C::PIV);
+  // Xi11 = X[0][.][0..D-1], Xi21 = X[1][.][0..D-1], Xi22 = X[1][.][D..2D-1]
+  T X11r[RL][D], X21r[RL][D], X22r[RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      X11r[l][c] = X[0][l][c];
+      X21r[l][c] = X[1][l][c];
+      X22r[l][c] = X[1][l][D + c];
+    }
+  publish<typename C::GR, D, LDM>(g, X11r, scr + C::MAT0);
+  publish<typename C::GR, D, LDM>(g, X21r, scr + C::MAT1);
+  g.sync();
+  // 2. M = Ci Xi11^-T (row r: solve M_r Xi11^T = Ci_r); Y = I - M Xi21^T
+  T Mr[RL][D], Yr[RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    T y[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = Ci[rr[l] * D + c];
+    solve_xLt<D, LDM>(scr + C::MAT0, y, Mr[l]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Mr[l][k] * scr[C::MAT1 + c * LDM + k];
+      Yr[l][c] = ((c == rr[l]) ? T(1) : T(0)) - acc;
+    }
+  }
+  g.sync();
+  // 3. U = Y Ai (rows), publish U -> MAT0, M -> MAT1
+  T Ur[RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += Yr[l][k] * Ai[k * D + c];
+      Ur[l][c] = acc;
+    }
+  publish<typename C::GR, D, LDM>(g, Ur, scr + C::MAT0);
+  publish<typename C::GR, D, LDM>(g, Mr, scr + C::MAT1);
+  // vector t = Ci^T eta_j (entry r per lane)
+  T tv[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Ci[k * D + rr[l]] * ej[k];
+    tv[l] = acc;
+  }
+  publish_vec(g, tv, scr + C::VEC0);
+  // s = Jj^T b_i (entry r)
+  T sv[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Jj[k * D + rr[l]] * bi[k];
+    sv[l] = acc;
+  }
+  publish_vec(g, sv, scr + C::VEC1);
+  g.sync();
+  // 4. new A row: Aj[r] U ; (Aj M) rows for C ; v = b_i + Ci t
+  T Anew[RL][D], AjM[RL][D], vv[RL], uu[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = rr[l];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const T ajk = Aj[r * D + k];
+        a1 += ajk * scr[C::MAT0 + k * LDM + c];
+        a2 += ajk * scr[C::MAT1 + k * LDM + c];
+      }
+      Anew[l][c] = a1;
+      AjM[l][c] = a2;
+    }
+    T acc = bi[r];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc += Ci[r * D + c] * scr[C::VEC0 + c];
+    vv[l] = acc;
+    T acc2 = ej[r];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc2 -= Jj[r * D + c] * scr[C::VEC1 + c];
+    uu[l] = acc2;
+  }
+  g.sync();
+  publish_vec(g, vv, scr + C::VEC2);
+  publish_vec(g, uu, scr + C::VEC3);
+  g.sync();
+  // w = Y v (entry r), eta_new = U^T u + eta_i (entry r)
+  T wv[RL], etan[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = rr[l];
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Yr[l][k] * scr[C::VEC2 + k];
+    wv[l] = acc;
+    T acc2 = ei[r];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc2 += scr[C::MAT0 + k * LDM + r] * scr[C::VEC3 + k];
+    etan[l] = acc2;
+  }
+  g.sync();
+  publish_vec(g, wv, scr + C::VEC0);
+  g.sync();
+  T bnew[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = rr[l];
+    T acc = bj[r];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Aj[r * D + k] * scr[C::VEC0 + k];
+    bnew[l] = acc;
+  }
+  // 5. sqrtC_new = tria([Cj | Aj M])  (Cj lower-triangular)
+  T triC[1][RL][D], extC[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      triC[0][l][c] = g.valid(l) ? Cj[rr[l] * D + c] : T(0);
+      extC[0][l][c] = g.valid(l) ? AjM[l][c] : T(0);
+    }
+  lq_tri_ext<typename C::GR, 1, D>(g, triC, extC, scr + C::PIV);
+  // 6. sqrtJ_new = tria([Ji | Ai^T Xi22])  (Ji lower-triangular)
+  T triJ[1][RL][D], extJ[1][RL][D];
+  if constexpr (!VALUES_ONLY) {
+    publish<typename C::GR, D, LDM>(g, X22r, scr + C::MAT1);
+    g.sync();
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const int r = rr[l];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc += Ai[k * D + r] * scr[C::MAT1 + k * LDM + c];
+        extJ[0][l][c] = g.valid(l) ? acc : T(0);
+        triJ[0][l][c] = g.valid(l) ? Ji[r * D + c] : T(0);
+      }
+    }
+    lq_tri_ext<typename C::GR, 1, D>(g, triJ, extJ, scr + C::PIV);
+  }
+  g.sync();
+  // 7. write
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = rr[l];
+#pragma unroll
+    for (int c = 0; c < D; ++c) aout[C::F_C + r * D + c] = triC[0][l][c];
+    aout[C::F_B + r] = bnew[l];
+    if constexpr (!VALUES_ONLY) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        aout[C::F_A + r * D + c] = Anew[l][c];
+        aout[C::F_J + r * D + c] = triJ[0][l][c];
+      }
+      aout[C::F_ETA + r] = etan[l];
+    }
+  }
+  g.sync();
+}
+
+// b_out = b_l (x)_s b_r   (Eq. sqrt-associative-smoothing).  Items [E | g | L].
+// L of the left operand must be lower-triangular.  WITH_L = false skips the L part.
+template <class C, bool WITH_L>
+__device__ void combine_s(const typename C::GR& g, const typename C::Tp* bl,
+                          const typename C::Tp* br, typename C::Tp* bout,
+                          typename C::Tp* scr) {
+  using T = typename C::Tp;
+  constexpr int D = C::D, RL = C::RL;
+  const T* Ei = bl + C::S_E;
+  const T* gi = bl + C::S_G;
+  const T* Li = bl + C::S_L;
+  const T* Ej = br + C::S_E;
+  const T* gj = br + C::S_G;
+  const T* Lj = br + C::S_L;
+  int rr[RL];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) rr[l] = g.valid(l) ? g.row(l) : 0;
+  T En[RL][D], gn[RL];
+  T tri[1][RL][D], ext[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const int r = rr[l];
+    T acc = gi[r];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc += Ei[r * D + k] * gj[k];
+    gn[l] = acc;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T a1 = T(0), a2 = T(0);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        a1 += Ei[r * D + k] * Ej[k * D + c];
+        if constexpr (WITH_L) a2 += Ei[r * D + k] * Lj[k * D + c];
+      }
+      En[l][c] = a1;
+      ext[0][l][c] = g.valid(l) ? a2 : T(0);
+      tri[0][l][c] = (WITH_L && g.valid(l)) ? Li[r * D + c] : T(0);
+    }
+  }
+  if constexpr (WITH_L) lq_tri_ext<typename C::GR, 1, D>(g, tri, ext, scr + C::PIV);
+  g.sync();
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = rr[l];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bout[C::S_E + r * D + c] = En[l][c];
+      if constexpr (WITH_L) bout[C::S_L + r * D + c] = tri[0][l][c];
+    }
+    bout[C::S_G + r] = gn[l];
+  }
+  g.sync();
+}
+
+template <class C>
+__device__ __forceinline__ void set_identity_f(const typename C::GR& g, typename C::Tp* a) {
+  constexpr int D = C::D;
+#pragma unroll
+  for (int l = 0; l < C::RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      a[C::F_A + r * D + c] = (c == r) ? 1 : 0;
+      a[C::F_C + r * D + c] = 0;
+      a[C::F_J + r * D + c] = 0;
+    }
+    a[C::F_B + r] = 0;
+    a[C::F_ETA + r] = 0;
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void set_identity_s(const typename C::GR& g, typename C::Tp* b) {
+  constexpr int D = C::D;
+#pragma unroll
+  for (int l = 0; l < C::RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      b[C::S_E + r * D + c] = (c == r) ? 1 : 0;
+      b[C::S_L + r * D + c] = 0;
+    }
+    b[C::S_G + r] = 0;
+  }
+}
+
+template <class C, int SZ>
+__device__ __forceinline__ void copy_item(const typename C::GR& g, const typename C::Tp* src,
+                                          typename C::Tp* dst) {
+  for (int i = g.gl; i < SZ; i += C::G) dst[i] = src[i];
+}
+
+}  // namespace pit

@@ -1,0 +1,557 @@
+// Host orchestration of the time-parallel IEKS (Algorithm 2) and of the element scans, templated
+// on the configuration.  Included only by the pit_inst_*.cu instantiation files.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pit_chains.cuh"
+#include "pit_internal.h"
+
+namespace pit {
+
+// ---- small elementwise kernels ---------------------------------------------------------------
+template <class C>
+__global__ void k_init_traj(const IeksParams<typename C::Tp> p,
+                            const typename C::Tp* __restrict__ init, typename C::Tp* traj) {
+  const int64_t total = (p.N + 1) * C::D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = static_cast<int>(i % C::D);
+    traj[i] = init ? init[i] / p.Tdiag[r % C::Q1] : p.mu0[r];
+  }
+}
+
+template <class C>
+__global__ void k_export_mean(const IeksParams<typename C::Tp> p,
+                              const typename C::Tp* __restrict__ traj,
+                              typename C::Tp* __restrict__ mean) {
+  const int64_t total = (p.N + 1) * C::D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = static_cast<int>(i % C::D);
+    mean[i] = p.Tdiag[r % C::Q1] * traj[i];
+  }
+}
+
+// ---- generic element scans (pit_filter_scan / pit_smooth_scan) -------------------------------
+template <class C>
+__device__ void load_filter_elem(const typename C::GR& g, int64_t n, const typename C::Tp* A,
+                                 const typename C::Tp* b, const typename C::Tp* Cm,
+                                 const typename C::Tp* eta, const typename C::Tp* J,
+                                 typename C::Tp* item, typename C::Tp* scr) {
+  using T = typename C::Tp;
+  constexpr int D = C::D, RL = C::RL;
+  T Cr[1][RL][D];
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    const bool v = g.valid(l);
+    const int r = v ? g.row(l) : 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) Cr[0][l][c] = v ? Cm[(n * D + r) * D + c] : T(0);
+  }
+  lq_dense<typename C::GR, 1, D, 0, D, 0>(g, Cr, scr + C::PIV);
+#pragma unroll
+  for (int l = 0; l < RL; ++l) {
+    if (!g.valid(l)) continue;
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      item[C::F_A + r * D + c] = A[(n * D + r) * D + c];
+      item[C::F_C + r * D + c] = Cr[0][l][c];
+      item[C::F_J + r * D + c] = J[(n * D + r) * D + c];
+    }
+    item[C::F_B + r] = b[n * D + r];
+    item[C::F_ETA + r] = eta[n * D + r];
+  }
+  g.sync();
+}
+
+template <class C>
+__global__ void __launch_bounds__(kThreads)
+k_gen_filter(int64_t N, int L, int64_t P, typename C::Tp* A, typename C::Tp* b,
+             typename C::Tp* Cm, typename C::Tp* eta, typename C::Tp* J,
+             typename C::Tp* items, int down) {
+  using T = typename C::Tp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= P) return;
+  T* scr = smem + grp * (C::SCR + 2 * C::FA);
+  T* acc = scr + C::SCR;
+  T* el = acc + C::FA;
+  if (down) copy_item<C, C::FA>(g, items + chain * C::FA, acc);
+  else set_identity_f<C>(g, acc);
+  g.sync();
+  const int64_t n0 = chain * L, n1 = min(chain * L + L, N);
+  for (int64_t n = n0; n < n1; ++n) {
+    load_filter_elem<C>(g, n, A, b, Cm, eta, J, el, scr);
+    combine_f<C, false>(g, acc, el, acc, scr);
+    if (down) {
+      for (int i = g.gl; i < C::D * C::D; i += C::G) {
+        A[n * C::D * C::D + i] = acc[C::F_A + i];
+        Cm[n * C::D * C::D + i] = acc[C::F_C + i];
+        J[n * C::D * C::D + i] = acc[C::F_J + i];
+      }
+      for (int i = g.gl; i < C::D; i += C::G) {
+        b[n * C::D + i] = acc[C::F_B + i];
+        eta[n * C::D + i] = acc[C::F_ETA + i];
+      }
+      g.sync();
+    }
+  }
+  if (!down) copy_item<C, C::FA>(g, acc, items + chain * C::FA);
+}
+
+template <class C, bool WITH_L>
+__global__ void __launch_bounds__(kThreads)
+k_gen_smooth(int64_t N, int L, int64_t P, typename C::Tp* E, typename C::Tp* gv,
+             typename C::Tp* Lm, typename C::Tp* items, int down) {
+  using T = typename C::Tp;
+  constexpr int D = C::D, RL = C::RL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= P) return;
+  T* scr = smem + grp * (C::SCR + 2 * C::SA);
+  T* acc = scr + C::SCR;
+  T* el = acc + C::SA;
+  if (down) copy_item<C, C::SA>(g, items + chain * C::SA, acc);
+  else set_identity_s<C>(g, acc);
+  g.sync();
+  const int64_t n0 = chain * L, n1 = min(chain * L + L, N);
+  auto load = [&](int64_t n) {
+    T Lr[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const bool v = g.valid(l);
+      const int r = v ? g.row(l) : 0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) Lr[0][l][c] = (WITH_L && v) ? Lm[(n * D + r) * D + c] : T(0);
+    }
+    if constexpr (WITH_L) lq_dense<typename C::GR, 1, D, 0, D, 0>(g, Lr, scr + C::PIV);
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      if (!g.valid(l)) continue;
+      const int r = g.row(l);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        el[C::S_E + r * D + c] = E[(n * D + r) * D + c];
+        el[C::S_L + r * D + c] = Lr[0][l][c];
+      }
+      el[C::S_G + r] = gv[n * D + r];
+    }
+    g.sync();
+  };
+  if (!down) {
+    // forward fold acc = b_n0 (x) ... (x) b_{n1-1}
+    for (int64_t n = n0; n < n1; ++n) {
+      load(n);
+      combine_s<C, WITH_L>(g, acc, el, acc, scr);
+    }
+    copy_item<C, C::SA>(g, acc, items + chain * C::SA);
+  } else {
+    for (int64_t n = n1 - 1; n >= n0; --n) {
+      load(n);
+      combine_s<C, WITH_L>(g, el, acc, acc, scr);
+      for (int i = g.gl; i < D * D; i += C::G) {
+        E[n * D * D + i] = acc[C::S_E + i];
+        if (WITH_L) Lm[n * D * D + i] = acc[C::S_L + i];
+      }
+      for (int i = g.gl; i < D; i += C::G) gv[n * D + i] = acc[C::S_G + i];
+      g.sync();
+    }
+  }
+}
+
+// ---- tree driver -----------------------------------------------------------------------------
+template <class C, bool FILTER, bool WITH_L, bool REVERSE>
+struct Tree {
+  using T = typename C::Tp;
+  using OPS = TreeOps<C, FILTER, WITH_L>;
+  static constexpr int SZ = OPS::SZ;
+  static constexpr int NG = kThreads / C::G;
+  static int block_items() {
+    int B = 64;
+    while (B > 2 && smem_bytes(B) > 200 * 1024) B /= 2;
+    return B;
+  }
+  static size_t smem_bytes(int B) {
+    return (static_cast<size_t>(B) * SZ + static_cast<size_t>(NG) * (C::SCR + SZ)) * sizeof(T);
+  }
+  // element counts of the upper levels for n bottom items
+  static std::vector<int64_t> levels(int64_t n, int B) {
+    std::vector<int64_t> v;
+    int64_t cur = n;
+    while (cur > B) {
+      cur = (cur + B - 1) / B;
+      v.push_back(cur);
+    }
+    return v;
+  }
+  static size_t upper_bytes(int64_t n) {
+    const int B = block_items();
+    size_t tot = 0;
+    for (int64_t c : levels(n, B)) tot += ((c * SZ * sizeof(T) + 255) / 256) * 256;
+    return tot;
+  }
+  // Exclusive scan of items[0..n) in place (rev_bottom: bottom level indexed in reverse).
+  static int run(T* items, int64_t n, T* upper, bool rev_bottom, cudaStream_t s) {
+    const int B = block_items();
+    const size_t smem = smem_bytes(B);
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_tree_up<C, OPS, REVERSE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_tree_down<C, OPS, REVERSE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    std::vector<int64_t> lv = levels(n, B);
+    std::vector<T*> arr;
+    std::vector<int64_t> cnt;
+    arr.push_back(items);
+    cnt.push_back(n);
+    char* up = reinterpret_cast<char*>(upper);
+    for (int64_t c : lv) {
+      arr.push_back(reinterpret_cast<T*>(up));
+      cnt.push_back(c);
+      up += ((c * SZ * sizeof(T) + 255) / 256) * 256;
+    }
+    const int top = static_cast<int>(arr.size()) - 1;
+    for (int lvl = 0; lvl < top; ++lvl) {
+      const unsigned grid = static_cast<unsigned>((cnt[lvl] + B - 1) / B);
+      k_tree_up<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(arr[lvl], cnt[lvl], B,
+                                                              arr[lvl + 1], 0,
+                                                              (lvl == 0 && rev_bottom) ? 1 : 0);
+      count_launches(1);
+    }
+    k_tree_up<C, OPS, REVERSE><<<1, kThreads, smem, s>>>(arr[top], cnt[top], B, nullptr, 1,
+                                                         (top == 0 && rev_bottom) ? 1 : 0);
+    count_launches(1);
+    for (int lvl = top - 1; lvl >= 0; --lvl) {
+      const unsigned grid = static_cast<unsigned>((cnt[lvl] + B - 1) / B);
+      k_tree_down<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(
+          arr[lvl], cnt[lvl], B, arr[lvl + 1], (lvl == 0 && rev_bottom) ? 1 : 0);
+      count_launches(1);
+    }
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+};
+
+// ---- the solver ------------------------------------------------------------------------------
+template <typename T, int DD, int Q1, int G, int RL>
+struct SolverImpl {
+  using C = Cfg<T, DD, Q1, G, RL>;
+  static constexpr int D = C::D;
+  static constexpr int NG = kThreads / G;
+
+  static int default_chain_len(int64_t N) {
+    // enough chains to fill every SM with several resident groups
+    const int64_t target_chains = 152LL * 8 * NG;
+    int64_t L = (N + target_chains - 1) / target_chains;
+    L = std::max<int64_t>(L, 4);
+    L = std::min<int64_t>(L, 512);
+    return static_cast<int>(L);
+  }
+
+  static int fill_params(const SolveArgs& a, IeksParams<T>& p, int want_cov) {
+    const Problem& pb = a.pb;
+    std::memset(&p, 0, sizeof(p));
+    p.ode.kind = pb.kind;
+    p.ode.d = pb.d;
+    for (int i = 0; i < pb.n_params && i < kMaxParams; ++i) p.ode.p[i] = static_cast<T>(pb.params[i]);
+    p.N = pb.N;
+    p.L = a.opts.chain_len > 0 ? a.opts.chain_len : default_chain_len(pb.N);
+    p.P = pb.N / p.L + 1;
+    p.want_cov = want_cov;
+    p.calibrate = a.opts.calibrate;
+    const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
+    double Phib[64], sqb[64], Td[8];
+    if (prior_blocks(pb.q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
+    for (int i = 0; i < Q1; ++i) {
+      p.Tdiag[i] = static_cast<T>(Td[i]);
+      for (int j = 0; j < Q1; ++j) {
+        p.phib[i * kMaxQ1 + j] = static_cast<T>(Phib[i * Q1 + j]);
+        p.sqb[i * kMaxQ1 + j] = static_cast<T>(sqb[i * Q1 + j]);
+      }
+    }
+    p.t0 = static_cast<T>(pb.t0);
+    p.h = static_cast<T>(h);
+    p.T0 = static_cast<T>(Td[0]);
+    p.T1inv = static_cast<T>(1.0 / Td[1]);
+    p.hq = static_cast<T>(h / pb.q);
+    double mu0[kMaxD];
+    if (taylor_init(pb, mu0) != PIT_OK) return PIT_EINVAL;
+    for (int r = 0; r < D; ++r) p.mu0[r] = static_cast<T>(mu0[r] / Td[r % Q1]);
+    return PIT_OK;
+  }
+
+  struct Buffers {
+    T *trajA, *trajB, *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
+    SolveScalars* scal;
+  };
+
+  static size_t carve(const SolveArgs& a, const IeksParams<T>& p, bool want_cov, Buffers& b) {
+    Carver cv(a.workspace, a.ws_bytes);
+    const int64_t N1 = p.N + 1;
+    b.trajA = cv.take<T>(N1 * D);
+    b.trajB = cv.take<T>(N1 * D);
+    b.Es = cv.take<T>(N1 * D * D);
+    b.gs = cv.take<T>(N1 * D);
+    b.Ls = want_cov ? cv.take<T>(N1 * D * D) : nullptr;
+    b.fagg = cv.take<T>(p.P * C::FA);
+    b.fup = cv.take<T>(Tree<C, true, false, false>::upper_bytes(p.P) / sizeof(T) + 1);
+    b.sagg = cv.take<T>(p.P * C::SA);
+    const size_t sup_bytes = std::max(Tree<C, false, false, true>::upper_bytes(p.P),
+                                      Tree<C, false, true, true>::upper_bytes(p.P));
+    b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
+    b.scal = cv.take<SolveScalars>(1);
+    return cv.used();
+  }
+
+  static size_t chain_smem() { return static_cast<size_t>(NG) * C::SCR * sizeof(T); }
+
+  // One filter pass + smoother pass at trajectory `lin` (Algorithm 1 in the linearised model).
+  template <bool WITH_L>
+  static int pass(const IeksParams<T>& p, const Buffers& b, const T* lin, T* out_traj,
+                  T* mean_out, T* cov_out, cudaStream_t s) {
+    const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
+    const size_t sm = chain_smem();
+    PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
+    k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, lin, b.fagg);
+    count_launches(1);
+    int st = Tree<C, true, false, false>::run(b.fagg, p.P, b.fup, false, s);
+    if (st != PIT_OK) return st;
+    k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, lin, b.fagg, b.Es, b.gs, b.Ls,
+                                                               b.sagg, b.scal);
+    count_launches(1);
+    st = Tree<C, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
+    if (st != PIT_OK) return st;
+    k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
+                                                        out_traj, mean_out, cov_out, b.scal);
+    count_launches(1);
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  static int set_smem_attrs() {
+    const int sm = static_cast<int>(chain_smem());
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_reduce<C>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, true, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return PIT_OK;
+  }
+
+  static int run(const SolveArgs& a, size_t* wsq, bool eks) {
+    const bool want_cov = a.opts.want_cov != 0;
+    IeksParams<T> p;
+    int st = fill_params(a, p, want_cov ? 1 : 0);
+    if (st != PIT_OK) return st;
+    Buffers b;
+    const size_t need = carve(a, p, want_cov, b);
+    if (wsq) {
+      *wsq = need;
+      return PIT_OK;
+    }
+    if (a.ws_bytes < need) {
+      set_error("workspace too small: need " + std::to_string(need) + " bytes, got " +
+                std::to_string(a.ws_bytes));
+      return PIT_ENOMEM;
+    }
+    if (reinterpret_cast<uintptr_t>(a.workspace) % 256 != 0) {
+      set_error("workspace must be 256-byte aligned");
+      return PIT_EINVAL;
+    }
+    st = set_smem_attrs();
+    if (st != PIT_OK) return st;
+    cudaStream_t s = a.stream;
+    const int64_t total = (p.N + 1) * D;
+    const unsigned eg = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+    T* mean = static_cast<T*>(a.mean);
+    T* cov = static_cast<T*>(a.sqrtcov);
+    pit_solve_info info;
+    std::memset(&info, 0, sizeof(info));
+    const int64_t launches0 = launches_total();
+    SolveScalars hs;
+    std::memset(&hs, 0, sizeof(hs));
+
+    if (eks) {
+      // sequential EKS: one chain, local linearisation at the predicted mean
+      const size_t sm = chain_smem();
+      PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
+      IeksParams<T> ps = p;
+      ps.L = static_cast<int>(p.N + 1);  // one chain: leaves n = 1..N, owns b_N
+      ps.P = 1;
+      if (want_cov)
+        k_filter_down<C, true, true><<<1, kThreads, sm, s>>>(ps, b.trajA, b.fagg, b.Es, b.gs,
+                                                              b.Ls, b.sagg, b.scal);
+      else
+        k_filter_down<C, false, true><<<1, kThreads, sm, s>>>(ps, b.trajA, b.fagg, b.Es, b.gs,
+                                                               b.Ls, b.sagg, b.scal);
+      count_launches(1);
+      IeksParams<T> pm = p;
+      pm.L = static_cast<int>(p.N + 1);  // smoothing chain covers n = 0..N
+      pm.P = 1;
+      if (want_cov) {
+        k_smooth_down<C, true><<<1, kThreads, sm, s>>>(pm, b.Es, b.gs, b.Ls, b.sagg, b.trajA,
+                                                       b.trajB, mean, cov, b.scal);
+      } else {
+        k_smooth_down<C, false><<<1, kThreads, sm, s>>>(pm, b.Es, b.gs, b.Ls, b.sagg, b.trajB,
+                                                        b.trajB, mean, cov, b.scal);
+        count_launches(1);
+        k_export_mean<C><<<eg, 256, 0, s>>>(p, b.trajB, mean);
+      }
+      count_launches(1);
+      PIT_CUDA_TRY(cudaGetLastError());
+      PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      PIT_CUDA_TRY(cudaStreamSynchronize(s));
+      info.iterations = 1;
+      info.converged = 1;
+      info.sigma2 = a.opts.calibrate ? hs.sigma2_sum / (static_cast<double>(p.N) * DD) : 1.0;
+      info.kernel_launches = launches_total() - launches0;
+      if (a.info) *a.info = info;
+      return PIT_OK;
+    }
+
+    k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.trajA);
+    count_launches(1);
+    PIT_CUDA_TRY(cudaGetLastError());
+    T* cur = b.trajA;  // linearisation trajectory of the current iteration
+    T* nxt = b.trajB;  // its smoothing means
+    const int fixed = a.opts.fixed_iters;
+    const int limit = fixed > 0 ? fixed : std::max(1, a.opts.max_iter);
+    bool converged = fixed > 0;
+    int k = 0;
+    while (k < limit) {
+      st = pass<false>(p, b, cur, nxt, nullptr, nullptr, s);
+      if (st != PIT_OK) return st;
+      ++k;
+      bool stop = (k == limit);
+      if (fixed <= 0) {
+        PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        PIT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs.flags & 1u) {
+          set_error("non-finite value in the smoothing means at iteration " + std::to_string(k));
+          return PIT_ENONFINITE;
+        }
+        info.last_delta = hs.delta_max;
+        if (hs.delta_max <= a.opts.atol_delta + a.opts.rtol_delta * hs.y_max) {
+          converged = true;
+          stop = true;
+        }
+      }
+      if (stop) break;
+      std::swap(cur, nxt);
+    }
+    // outputs: the last iteration's means (nxt) and, if requested, covariances from a pass with
+    // the same linearisation trajectory (cur); that pass reproduces the same means.
+    if (want_cov) {
+      st = pass<true>(p, b, cur, nullptr, mean, cov, s);
+      if (st != PIT_OK) return st;
+    } else {
+      k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean);
+      count_launches(1);
+    }
+    PIT_CUDA_TRY(cudaGetLastError());
+    PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (fixed > 0) info.last_delta = want_cov ? info.last_delta : hs.delta_max;
+    info.iterations = k;
+    info.converged = converged ? 1 : 0;
+    info.sigma2 = a.opts.calibrate ? hs.sigma2_sum / (static_cast<double>(p.N) * DD) : 1.0;
+    info.kernel_launches = launches_total() - launches0;
+    if (a.info) *a.info = info;
+    return converged ? PIT_OK : PIT_ENOCONV;
+  }
+};
+
+// ---- generic scans ---------------------------------------------------------------------------
+template <typename T, int D, int G, int RL>
+struct ScanImpl {
+  using C = Cfg<T, 1, D, G, RL>;
+  static constexpr int NG = kThreads / G;
+  static int chain_len(int64_t N) {
+    int64_t L = (N + 152LL * 4 * NG - 1) / (152LL * 4 * NG);
+    return static_cast<int>(std::max<int64_t>(4, std::min<int64_t>(L, 256)));
+  }
+  static int filter(const ScanArgs& a, size_t* wsq) {
+    const int L = chain_len(a.N);
+    const int64_t P = (a.N + L - 1) / L;
+    Carver cv(a.workspace, a.ws_bytes);
+    T* items = cv.take<T>(P * C::FA);
+    T* up = cv.take<T>(Tree<C, true, false, false>::upper_bytes(P) / sizeof(T) + 1);
+    if (wsq) {
+      *wsq = cv.used();
+      return PIT_OK;
+    }
+    if (a.ws_bytes < cv.used()) {
+      set_error("workspace too small");
+      return PIT_ENOMEM;
+    }
+    const size_t sm = static_cast<size_t>(NG) * (C::SCR + 2 * C::FA) * sizeof(T);
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_gen_filter<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
+    const unsigned grid = static_cast<unsigned>((P + NG - 1) / NG);
+    T *A = (T*)a.x0, *b = (T*)a.x1, *Cm = (T*)a.x2, *eta = (T*)a.x3, *J = (T*)a.x4;
+    k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 0);
+    count_launches(1);
+    int st = Tree<C, true, false, false>::run(items, P, up, false, a.stream);
+    if (st != PIT_OK) return st;
+    k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 1);
+    count_launches(1);
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+  template <bool WITH_L>
+  static int smooth_t(const ScanArgs& a, size_t* wsq) {
+    const int L = chain_len(a.N);
+    const int64_t P = (a.N + L - 1) / L;
+    Carver cv(a.workspace, a.ws_bytes);
+    T* items = cv.take<T>(P * C::SA);
+    T* up = cv.take<T>(Tree<C, false, WITH_L, true>::upper_bytes(P) / sizeof(T) + 1);
+    if (wsq) {
+      *wsq = cv.used();
+      return PIT_OK;
+    }
+    if (a.ws_bytes < cv.used()) {
+      set_error("workspace too small");
+      return PIT_ENOMEM;
+    }
+    const size_t sm = static_cast<size_t>(NG) * (C::SCR + 2 * C::SA) * sizeof(T);
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_gen_smooth<C, WITH_L>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const unsigned grid = static_cast<unsigned>((P + NG - 1) / NG);
+    T *E = (T*)a.x0, *g = (T*)a.x1, *Lm = (T*)a.x2;
+    k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 0);
+    count_launches(1);
+    int st = Tree<C, false, WITH_L, true>::run(items, P, up, true, a.stream);
+    if (st != PIT_OK) return st;
+    k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 1);
+    count_launches(1);
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+  static int smooth(const ScanArgs& a, size_t* wsq) {
+    return a.want_L ? smooth_t<true>(a, wsq) : smooth_t<false>(a, wsq);
+  }
+};
+
+}  // namespace pit

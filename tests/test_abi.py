@@ -1,0 +1,128 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every function
+include/pit.h declares, and its host-only entry points (FP64 prior, exact initial state,
+argument validation, workspace queries) agree with the oracle / reject bad input."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import prior, taylor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pit.h")
+
+
+@pytest.fixture(scope="module")
+def pit():
+    import paper_2310_01145_gb300 as P
+    from paper_2310_01145_gb300.build import LIB, build
+    if not os.path.exists(LIB):
+        build()
+    P.load()
+    return P
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(pit_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pit_prior", "pit_linearize", "pit_filter_scan", "pit_smooth_scan",
+                     "pit_solve", "pit_solve_workspace_size", "pit_status_string",
+                     "pit_last_error", "pit_eks_sequential"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pit):
+    lib = ctypes.CDLL(pit.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # the Python binding wraps exactly these names
+    assert set(pit.SIGNATURES) == set(declared_functions())
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 5])
+@pytest.mark.parametrize("h", [1e-4, 0.03, 0.9])
+def test_host_prior_matches_oracle(pit, q, h):
+    out = pit.pit_prior(q, h)
+    Phi, Q = prior.iwp_1d(q, h)
+    Pb, Qb = prior.preconditioned_1d(q)
+    np.testing.assert_allclose(out["Phi"], Phi, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(out["Q"], Q, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(out["Phibar"], Pb, rtol=0, atol=0)
+    np.testing.assert_allclose(out["sqrtQbar"] @ out["sqrtQbar"].T, Qb, rtol=1e-13)
+    assert np.allclose(np.triu(out["sqrtQbar"], 1), 0)
+    np.testing.assert_allclose(out["Tdiag"], prior.preconditioner_1d(q, h), rtol=1e-14)
+
+
+@pytest.mark.parametrize("problem", [W.logistic(q=3), W.fitzhugh_nagumo(q=3), W.rigid_body(q=2),
+                                     W.van_der_pol(q=3), W.lotka_volterra(q=2),
+                                     W.affine([[0.0, 1.0], [-1.0, -0.1]], [0.3, 0.0], [1.0, 0.5], q=3),
+                                     W.lorenz96(d=8, q=2)],
+                         ids=lambda p: p.name)
+def test_host_initial_state_matches_oracle(pit, problem):
+    mu = pit.pit_init_state(pit.ode_from_problem(problem), problem.q, problem.y0)
+    ref = taylor.initial_state(problem.kind, problem.params, problem.y0, problem.q)
+    np.testing.assert_allclose(mu, ref, rtol=1e-13, atol=1e-15)
+
+
+def test_validation_errors(pit):
+    ode = pit.Ode(W.LOGISTIC, 1, np.array([3.0]))
+    with pytest.raises(pit.PitError) as e:
+        pit.pit_init_state(pit.Ode(W.LOGISTIC, 1, np.array([3.0, 1.0])), 2, [0.1])
+    assert e.value.status == 1
+    with pytest.raises(pit.PitError):
+        pit.pit_init_state(ode, 0, [0.1])
+    with pytest.raises(pit.PitError):
+        pit.pit_init_state(ode, 2, [float("nan")])
+    with pytest.raises(pit.PitError):
+        pit.pit_init_state(pit.Ode(W.FITZHUGH_NAGUMO, 3, np.array([0.2, 0.2, 3.0])), 2, [0, 0, 0])
+    with pytest.raises(pit.PitError):
+        pit.pit_prior(0, 0.1)
+    with pytest.raises(pit.PitError):
+        pit.pit_prior(2, -1.0)
+    lib = pit.load()
+    c = ode.c()
+    sz = ctypes.c_size_t(0)
+    bad_grid = pit._Grid(1.0, 0.0, 10)
+    st = lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(bad_grid), 2,
+                                      ctypes.byref(pit.make_opts()), ctypes.byref(sz))
+    assert st == 1 and b"t0 < t1" in lib.pit_last_error()
+    good = pit._Grid(0.0, 1.0, 10)
+    bad_opts = pit.make_opts()
+    bad_opts.max_iter = 0
+    assert lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(good), 2,
+                                        ctypes.byref(bad_opts), ctypes.byref(sz)) == 1
+    # d / q outside the compiled kernel set
+    st = lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(good), 5,
+                                      ctypes.byref(pit.make_opts()), ctypes.byref(sz))
+    assert st == 8
+    assert lib.pit_status_string(8) == b"configuration not compiled"
+
+
+def test_workspace_queries_scale_with_n(pit):
+    lib = pit.load()
+    ode = pit.ode_from_problem(W.fitzhugh_nagumo(q=3))
+    c = ode.c()
+    sizes = []
+    for N in (1, 1000, 2 ** 20):
+        g = pit._Grid(0.0, 20.0, N)
+        sz = ctypes.c_size_t(0)
+        assert lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(g), 3,
+                                            ctypes.byref(pit.make_opts(dtype="f32")),
+                                            ctypes.byref(sz)) == 0
+        sizes.append(sz.value)
+    assert sizes[0] < sizes[1] < sizes[2]
+    # dominated by the smoothing elements: (N+1) (D^2 + D) + (N+1) D^2 (covariance pass) floats
+    D = 8
+    assert sizes[2] >= (2 ** 20 + 1) * (2 * D * D + 3 * D) * 4
+    sz = ctypes.c_size_t(0)
+    assert lib.pit_filter_scan_workspace_size(1000, 8, 0, ctypes.byref(sz)) == 0 and sz.value > 0
+    assert lib.pit_filter_scan_workspace_size(1000, 5, 0, ctypes.byref(sz)) == 8
