@@ -13,15 +13,52 @@ __device__ __forceinline__ int64_t chain_index(int grp_in_block) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Per-step model inputs.  The IEKS solves for the Gauss-Newton increment delta = Y - lin of
+// iteration k (lin = the linearisation trajectory, kept in double or double-float):
+//   delta_0 = mu0 - lin_0,   delta_n = Phibar delta_{n-1} + u_{n-1} + w,   u_{n-1} = Phibar lin_{n-1} - lin_n,
+//   Htilde_n delta_n = r_n,  r_n = (f(E0 lin_n) - E1 lin_n) / T_1      (scaled preconditioned form)
+// which is the linearised model of Section 3.2.1 shifted by lin (its posterior mean is
+// m^s - lin).  u, r and y = E0 lin are evaluated once per iteration in extended precision by
+// k_residuals; the scans then handle only increment-sized numbers in FP32.
+// ---------------------------------------------------------------------------------------------
+template <class C>
+__device__ __forceinline__ void step_inputs(const IeksParams<typename C::Tp>& p,
+                                            const typename C::Tp* __restrict__ Yv,
+                                            const typename C::Tp* __restrict__ R, int64_t n,
+                                            typename C::Tp (&Ft)[C::DD][C::DD],
+                                            typename C::Tp (&rr)[C::DD]) {
+  using T = typename C::Tp;
+  T y[C::DD], f[C::DD], F[C::DD][C::DD];
+#pragma unroll
+  for (int k = 0; k < C::DD; ++k) y[k] = Yv[n * C::DD + k];
+  ode_eval<T, C::DD>(p.ode, y, f, F);
+#pragma unroll
+  for (int k = 0; k < C::DD; ++k) {
+    rr[k] = R[n * C::DD + k];
+#pragma unroll
+    for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * p.hq;
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void load_forcing(const typename C::GR& g,
+                                             const typename C::Tp* __restrict__ U, int64_t n,
+                                             typename C::Tp (&uf)[C::RL]) {
+#pragma unroll
+  for (int l = 0; l < C::RL; ++l) uf[l] = g.valid(l) ? U[n * C::D + g.row(l)] : typename C::Tp(0);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Filter reduce: chain c folds its leaves n = cL+1 .. min(cL+L, N) into the aggregate
-// a_{cL+1} (x)_f ... (x)_f a_{end}; chain 0 starts from the initial state (A = 0, b = mu0,
+// a_{cL+1} (x)_f ... (x)_f a_{end}; chain 0 starts from the initial state (A = 0, b = delta_0,
 // C = 0), the others from the neutral element.  Output: one filter item per chain, with C and J
 // lower-triangular.
 // ---------------------------------------------------------------------------------------------
 template <class C>
 __global__ void __launch_bounds__(kThreads)
-k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ traj,
-                typename C::Tp* __restrict__ agg) {
+k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
+                const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
+                const typename C::Tp* __restrict__ d0, typename C::Tp* __restrict__ agg) {
   using T = typename C::Tp;
   using GR = typename C::GR;
   constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
@@ -47,15 +84,16 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     }
 #pragma unroll
     for (int c = 0; c < W; ++c) sC[l][c] = T(0);
-    b[l] = (chain == 0 && r < D) ? p.mu0[r] : T(0);
+    b[l] = (chain == 0 && r < D) ? d0[r] : T(0);
     eta[l] = T(0);
   }
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
   for (int64_t n = n0; n <= n1; ++n) {
-    T Ft[DD][DD], dt[DD];
-    linearize_at<C>(p, traj, n, Ft, dt);
-    // predict the conditional filter: A' = Phi A, b' = Phi b, C- = tria([sqrtQ | Phi sqrtC])
+    T Ft[DD][DD], rr[DD], uf[RL];
+    step_inputs<C>(p, Yv, R, n, Ft, rr);
+    load_forcing<C>(g, U, n - 1, uf);
+    // predict the conditional filter: A' = Phi A, b' = Phi b + u, C- = tria([sqrtQ | Phi sqrtC])
     publish<GR, D, LDM>(g, A, scr + C::MAT0);
     publish<GR, W, LDM>(g, sC, scr + C::MAT1);
     publish_vec(g, b, scr + C::VEC0);
@@ -65,9 +103,11 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     phi_rows<C, W>(lc, scr + C::MAT1, ext[0]);
     phi_vec<C>(lc, scr + C::VEC0, bp);
 #pragma unroll
-    for (int l = 0; l < RL; ++l)
+    for (int l = 0; l < RL; ++l) {
+      bp[l] += uf[l];
 #pragma unroll
       for (int c = 0; c < D; ++c) tri[0][l][c] = lc.sqrow[l][c];
+    }
     g.sync();
     lq_tri_ext<GR, 1, W>(g, tri, ext, scr + C::PIV);
     // update with the linearised observation
@@ -88,7 +128,7 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
       for (int kk = 0; kk < DD; ++kk) HAcol[l][kk] = hrow_entry<C>(scr + C::MAT1, Ft, kk, r);
     }
     UpdateOut<C> u;
-    sqrt_update<C>(g, scr, tri[0], Ft, dt, sC, u);
+    sqrt_update<C>(g, scr, tri[0], Ft, rr, sC, u);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       T acc = bp[l];
@@ -150,11 +190,14 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
 // Step n also forms the smoothing element b_{n-1} from the Pi-triangularisation of Eq.
 // sqrt-smoothing-elements (whose top block is the prediction of step n) and folds it into the
 // chain's smoothing aggregate.  The chain owning n = N also emits b_N = (0, m^f_N, sqrtP^f_N).
-// Accumulates the calibration sum (1/(N d) normalisation on the host).
+// Accumulates the calibration sum sum_n ||sqrtS_n^-1 nu_n||^2 in FP64.
+// LOCAL_LIN: the sequential EKS; linearise at the predicted mean (plain model, no increment).
 // ---------------------------------------------------------------------------------------------
 template <class C, bool WITH_L, bool LOCAL_LIN>
 __global__ void __launch_bounds__(kThreads)
-k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ traj,
+k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
+              const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
+              const typename C::Tp* __restrict__ d0,
               const typename C::Tp* __restrict__ fprefix, typename C::Tp* __restrict__ Es,
               typename C::Tp* __restrict__ gs, typename C::Tp* __restrict__ Ls,
               typename C::Tp* __restrict__ sagg, SolveScalars* __restrict__ scal) {
@@ -181,7 +224,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       const int r = g.valid(l) ? g.row(l) : 0;
       const bool v = g.valid(l);
       if (chain == 0) {
-        m[l] = v ? p.mu0[r] : T(0);
+        m[l] = v ? (LOCAL_LIN ? p.mu0[r] : d0[r]) : T(0);
 #pragma unroll
         for (int c = 0; c < D; ++c) sP[l][c] = T(0);
       } else {
@@ -254,8 +297,14 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
   for (int64_t n = n0; n <= n1; ++n) {
-    T Ft[DD][DD], dt[DD];
-    if constexpr (!LOCAL_LIN) linearize_at<C>(p, traj, n, Ft, dt);
+    T Ft[DD][DD], rr[DD], uf[RL];
+    if constexpr (!LOCAL_LIN) {
+      step_inputs<C>(p, Yv, R, n, Ft, rr);
+      load_forcing<C>(g, U, n - 1, uf);
+    } else {
+#pragma unroll
+      for (int l = 0; l < RL; ++l) uf[l] = T(0);
+    }
     publish<GR, D, LDM>(g, sP, scr + C::MAT0);
     publish_vec(g, m, scr + C::VEC0);
     g.sync();
@@ -264,13 +313,15 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     phi_rows<C, D>(lc, scr + C::MAT0, ext[0]);
     phi_vec<C>(lc, scr + C::VEC0, mp);
 #pragma unroll
-    for (int l = 0; l < RL; ++l)
+    for (int l = 0; l < RL; ++l) {
+      mp[l] += uf[l];
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         tri[0][l][c] = lc.sqrow[l][c];
         tri[1][l][c] = T(0);
         ext[1][l][c] = sP[l][c];
       }
+    }
     g.sync();
     lq_tri_ext<GR, 2, D>(g, tri, ext, scr + C::PIV);
     // Pi11 = tri[0] (= predicted factor of step n), Pi21 = tri[1], remainder ext[1]
@@ -294,16 +345,16 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     }
     if constexpr (WITH_L) {
       // sqrtL = Pi22 = tria(remainder)
-      T R[1][RL][D];
+      T Rm[1][RL][D];
 #pragma unroll
       for (int l = 0; l < RL; ++l)
 #pragma unroll
-        for (int c = 0; c < D; ++c) R[0][l][c] = ext[1][l][c];
-      lq_dense<GR, 1, D, 0, D, 0>(g, R, scr + C::PIV);
+        for (int c = 0; c < D; ++c) Rm[0][l][c] = ext[1][l][c];
+      lq_dense<GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
 #pragma unroll
       for (int l = 0; l < RL; ++l)
 #pragma unroll
-        for (int c = 0; c < D; ++c) lrow[l][c] = R[0][l][c];
+        for (int c = 0; c < D; ++c) lrow[l][c] = Rm[0][l][c];
     }
     emit(n - 1, e, gg, lrow);
     if constexpr (LOCAL_LIN) {
@@ -311,12 +362,12 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       T y[DD];
 #pragma unroll
       for (int k = 0; k < DD; ++k) y[k] = p.T0 * scr[C::VEC0 + k * C::Q1];
-      linearize_y<C>(p, y, Ft, dt);
+      linearize_y<C>(p, y, Ft, rr);
     }
     // Kalman update of step n (Pi11 is still published at MAT0, m- at VEC0)
     T sPn[RL][W];
     UpdateOut<C> u;
-    sqrt_update<C>(g, scr, tri[0], Ft, dt, sPn, u);
+    sqrt_update<C>(g, scr, tri[0], Ft, rr, sPn, u);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       T acc = mp[l];
@@ -338,19 +389,19 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   // the chain owning n = N emits b_N = (E = 0, g = m^f_N, sqrtL = tria(sqrtP^f_N))
   if (chain == p.N / p.L) {
     T e[RL][D], lrow[RL][D];
-    T R[1][RL][D];
+    T Rm[1][RL][D];
 #pragma unroll
     for (int l = 0; l < RL; ++l)
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         e[l][c] = T(0);
-        R[0][l][c] = sP[l][c];
+        Rm[0][l][c] = sP[l][c];
       }
-    if constexpr (WITH_L) lq_dense<GR, 1, D, 0, D, 0>(g, R, scr + C::PIV);
+    if constexpr (WITH_L) lq_dense<GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
 #pragma unroll
     for (int l = 0; l < RL; ++l)
 #pragma unroll
-      for (int c = 0; c < D; ++c) lrow[l][c] = WITH_L ? R[0][l][c] : T(0);
+      for (int c = 0; c < D; ++c) lrow[l][c] = WITH_L ? Rm[0][l][c] : T(0);
     T gg[RL];
 #pragma unroll
     for (int l = 0; l < RL; ++l) gg[l] = g.valid(l) ? m[l] : T(0);
@@ -373,21 +424,24 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 }
 
 // ---------------------------------------------------------------------------------------------
-// Smoothing down-sweep: chain c starts from m^s at its right end (the reverse exclusive prefix,
-// or nothing for the chain holding n = N) and walks its elements backwards:
-//   m^s_n = E_n m^s_{n+1} + g_n,   sqrtP^s_n = tria([sqrtL_n | E_n sqrtP^s_{n+1}])
-// Non-final passes write the new trajectory (preconditioned) and reduce max|change of y|;
-// the covariance pass writes the outputs in original coordinates.
+// Smoothing down-sweep: chain c starts from the smoothing mean at its right end (the reverse
+// exclusive prefix, or nothing for the chain holding n = N) and walks its elements backwards:
+//   delta^s_n = E_n delta^s_{n+1} + g_n,   sqrtP^s_n = tria([sqrtL_n | E_n sqrtP^s_{n+1}])
+// Means passes write lin_new = lin + delta^s and reduce max|change of y| = max|T_0 delta^s_0|;
+// the covariance pass writes the outputs in original coordinates.  lin == nullptr means a zero
+// trajectory (the sequential EKS).
 // ---------------------------------------------------------------------------------------------
 template <class C, bool WITH_L>
 __global__ void __launch_bounds__(kThreads)
 k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
               const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
               const typename C::Tp* __restrict__ sprefix,
-              const typename C::Tp* __restrict__ traj_old, typename C::Tp* __restrict__ traj_new,
+              const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+              typename TrajType<typename C::Tp>::type* __restrict__ lin_new,
               typename C::Tp* __restrict__ mean_out, typename C::Tp* __restrict__ cov_out,
               SolveScalars* __restrict__ scal) {
   using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
   using GR = typename C::GR;
   constexpr int D = C::D, RL = C::RL, LDM = C::LDM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -419,10 +473,11 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
         sPs[l][c] = (WITH_L && !last && vv[l]) ? pre[C::S_L + rr[l] * D + c] : T(0);
     }
   }
-  double dmax = 0.0, ymax = 0.0;
+  T dmax = T(0), ymax = T(0);
+  bool bad = false;
   // quasi-MLE diffusion of this (final) pass: sigma^2 = sum / (N d)
-  const double sigma =
-      (WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD)) : 1.0;
+  const T sigma = static_cast<T>(
+      (WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD)) : 1.0);
   const int64_t s0 = chain * p.L;
   const int64_t s1 = min(chain * p.L + p.L - 1, p.N);
   for (int64_t n = s1; n >= s0; --n) {
@@ -463,20 +518,19 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       m[l] = mn[l];
       if (!vv[l]) continue;
       const int r = rr[l];
+      const V lv = lin ? lin[n * D + r] : v_from_zero<V>();
+      const V ln = v_add_small(lv, mn[l]);
       if constexpr (WITH_L) {
-        mean_out[n * D + r] = Trow[l] * mn[l];
+        mean_out[n * D + r] = Trow[l] * v_to_T<T>(ln);
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          cov_out[n * D * D + r * D + c] = static_cast<T>(sigma) * Trow[l] * sPs[l][c];
+        for (int c = 0; c < D; ++c) cov_out[n * D * D + r * D + c] = sigma * Trow[l] * sPs[l][c];
       } else {
-        traj_new[n * D + r] = mn[l];
+        lin_new[n * D + r] = ln;
         if (r % C::Q1 == 0) {
-          const double ynew = static_cast<double>(p.T0) * static_cast<double>(mn[l]);
-          const double yold =
-              static_cast<double>(p.T0) * static_cast<double>(traj_old[n * D + r]);
-          const double dd = fabs(ynew - yold);
-          dmax = (dd > dmax || dd != dd) ? dd : dmax;
-          ymax = fmax(ymax, fabs(ynew));
+          const T dd = fabs(p.T0 * mn[l]);
+          bad = bad || !(dd == dd);
+          dmax = fmax(dmax, dd);
+          ymax = fmax(ymax, fabs(p.T0 * v_to_T<T>(ln)));
         }
       }
     }
@@ -485,22 +539,17 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     // reduce over the group (groups past the last chain have returned), one atomic per group
 #pragma unroll
     for (int o = C::G / 2; o > 0; o >>= 1) {
-      const double od = __shfl_xor_sync(g.mask, dmax, o);
-      const double oy = __shfl_xor_sync(g.mask, ymax, o);
-      dmax = (od > dmax || od != od) ? od : dmax;
-      ymax = fmax(ymax, oy);
+      dmax = fmax(dmax, __shfl_xor_sync(g.mask, dmax, o));
+      ymax = fmax(ymax, __shfl_xor_sync(g.mask, ymax, o));
     }
+    const unsigned anybad = __any_sync(g.mask, bad);
     if (g.gl == 0) {
-      if (dmax != dmax) {
-        atomicOr(&scal->flags, 1u);
-      } else {
-        atomic_max_nonneg(&scal->delta_max, dmax);
-      }
-      atomic_max_nonneg(&scal->y_max, ymax);
+      if (anybad) atomicOr(&scal->flags, 1u);
+      atomic_max_nonneg(&scal->delta_max, static_cast<double>(dmax));
+      atomic_max_nonneg(&scal->y_max, static_cast<double>(ymax));
     }
   }
 }
-
 // ---------------------------------------------------------------------------------------------
 // Tree scans over items (filter: FA elements, smoothing: SA elements) in blocks of B items.
 // Position p of a level maps to item index p, or to n-1-p when `rev_index` is set (only the

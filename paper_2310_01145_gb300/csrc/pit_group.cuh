@@ -75,27 +75,65 @@ __device__ __forceinline__ void publish_vec(const GR& g, const T (&x)[GR::RL], T
   for (int l = 0; l < GR::RL; ++l) buf[g.row(l)] = x[l];
 }
 
-// One Householder reflection from the right.  The pivot row is given by its diagonal entry x0
-// and the remaining support entries xe[0..NE-1]; the reflection maps it to (alpha, 0, ..., 0).
+// One Householder reflection from the right, normalised as in LAPACK's larfg: for the pivot
+// row x = (x0, xe) it returns beta = -sign(x0) ||x||, tau = (beta - x0) / beta in [1, 2] and
+// w = 1 / (x0 - beta), so that v = (1, w xe) and (I - tau v v^T) maps x to (beta, 0, ..., 0).
+// With v0 = 1 and |w xe_j| <= 1 nothing overflows even when ||x|| is tiny (rank-deficient
+// factors leave round-off-sized pivots).  ||x|| is computed with scaling when x0^2 + sum xe^2
+// leaves the safe range of T.  A row y is transformed as
+//   f = tau (y0 + w sum_j y_j xe_j),  y0 -= f,  y_j -= (f w) xe_j.
 template <typename T>
 struct Reflector {
-  T v0, tau, alpha;
+  T beta, tau, w;
   bool active;
 };
 
-template <typename T, int NE>
-__device__ __forceinline__ Reflector<T> make_reflector(T x0, const T (&xe)[NE]) {
+template <typename T>
+struct SafeRange;
+template <>
+struct SafeRange<float> {
+  static constexpr float lo = 1e-30f, hi = 1e30f;
+};
+template <>
+struct SafeRange<double> {
+  static constexpr double lo = 1e-280, hi = 1e280;
+};
+
+template <typename T, int NE, class GetX>
+__device__ __forceinline__ Reflector<T> make_reflector_g(T x0, GetX xe) {
   T sig = T(0);
 #pragma unroll
-  for (int j = 0; j < NE; ++j) sig += xe[j] * xe[j];
+  for (int j = 0; j < NE; ++j) sig += xe(j) * xe(j);
   Reflector<T> h;
-  const T nrm = dsqrt<T>(x0 * x0 + sig);
-  h.alpha = (x0 >= T(0)) ? -nrm : nrm;
-  h.v0 = x0 - h.alpha;
-  const T vtv = h.v0 * h.v0 + sig;
-  h.active = sig > T(0);
-  h.tau = h.active ? T(2) / vtv : T(0);
+  T ss = x0 * x0 + sig;
+  T nrm;
+  if (ss > SafeRange<T>::lo && ss < SafeRange<T>::hi) {
+    nrm = dsqrt<T>(ss);
+  } else {
+    T amax = fabs(x0);
+#pragma unroll
+    for (int j = 0; j < NE; ++j) amax = fmax(amax, fabs(xe(j)));
+    if (amax > T(0)) {
+      const T inv = T(1) / amax;
+      T acc = (x0 * inv) * (x0 * inv);
+#pragma unroll
+      for (int j = 0; j < NE; ++j) acc += (xe(j) * inv) * (xe(j) * inv);
+      nrm = amax * dsqrt<T>(acc);
+    } else {
+      nrm = T(0);
+    }
+    sig = (nrm > fabs(x0)) ? T(1) : T(0);  // only its sign (> 0) is used below
+  }
+  h.active = sig > T(0) && nrm > T(0);
+  h.beta = (x0 >= T(0)) ? -nrm : nrm;
+  h.tau = h.active ? (h.beta - x0) / h.beta : T(0);
+  h.w = h.active ? T(1) / (x0 - h.beta) : T(0);
   return h;
+}
+
+template <typename T, int NE>
+__device__ __forceinline__ Reflector<T> make_reflector(T x0, const T (&xe)[NE]) {
+  return make_reflector_g<T, NE>(x0, [&](int j) { return xe[j]; });
 }
 
 // ---- structured LQ: [L | X], L lower-triangular ------------------------------------------
@@ -133,15 +171,16 @@ __device__ __forceinline__ void lq_tri_ext(const GR& g, T (&tri)[NS][GR::RL][GR:
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
       for (int l = 0; l < RL; ++l) {
-        T dot = tri[s][l][i] * h.v0;
+        T acc = T(0);
 #pragma unroll
-        for (int j = 0; j < NE; ++j) dot += ext[s][l][j] * xe[j];
-        const T f = h.tau * dot;
-        tri[s][l][i] -= f * h.v0;
+        for (int j = 0; j < NE; ++j) acc += ext[s][l][j] * xe[j];
+        const T f = h.tau * (tri[s][l][i] + h.w * acc);
+        const T fw = f * h.w;
+        tri[s][l][i] -= f;
 #pragma unroll
-        for (int j = 0; j < NE; ++j) ext[s][l][j] -= f * xe[j];
+        for (int j = 0; j < NE; ++j) ext[s][l][j] -= fw * xe[j];
         if (s == 0 && l == li && g.gl == owner && h.active) {
-          tri[s][l][i] = h.alpha;
+          tri[s][l][i] = h.beta;
 #pragma unroll
           for (int j = 0; j < NE; ++j) ext[s][l][j] = T(0);
         }
@@ -154,7 +193,7 @@ __device__ __forceinline__ void lq_tri_ext(const GR& g, T (&tri)[NS][GR::RL][GR:
 // ---- dense LQ ----------------------------------------------------------------------------
 // Rows of NS sets with NC columns each.  Pivot rows k = 0..NPIV-1 of set PS, pivot column
 // PC0 + k, support columns PC0+k .. NC-1.  Every row of every set is transformed; after the
-// call pivot row k is (..., alpha_k at column PC0+k, 0, ..., 0).
+// call pivot row k is (..., beta_k at column PC0+k, 0, ..., 0).
 template <class GR, int NS, int NC, int PS, int NPIV, int PC0, typename T>
 __device__ __forceinline__ void lq_dense(const GR& g, T (&rows)[NS][GR::RL][NC], T* piv) {
   constexpr int RL = GR::RL;
@@ -177,33 +216,26 @@ __device__ __forceinline__ void lq_dense(const GR& g, T (&rows)[NS][GR::RL][NC],
     }
     g.sync();
     T x[NC];
-    T sig = T(0);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      x[c] = (c >= c0) ? pb[c] : T(0);
-      if (c > c0) sig += x[c] * x[c];
-    }
-    const T x0 = x[c0];
-    const T nrm = dsqrt<T>(x0 * x0 + sig);
-    const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-    const T v0 = x0 - alpha;
-    const bool active = sig > T(0);
-    const T tau = active ? T(2) / (v0 * v0 + sig) : T(0);
+    for (int c = 0; c < NC; ++c) x[c] = (c > c0) ? pb[c] : T(0);
+    const T x0 = pb[c0];
+    const Reflector<T> h = make_reflector_g<T, NC>(x0, [&](int j) { return x[j]; });
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
       for (int l = 0; l < RL; ++l) {
-        T dot = rows[s][l][c0] * v0;
+        T acc = T(0);
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          if (c > c0) dot += rows[s][l][c] * x[c];
-        const T f = tau * dot;
-        rows[s][l][c0] -= f * v0;
+          if (c > c0) acc += rows[s][l][c] * x[c];
+        const T f = h.tau * (rows[s][l][c0] + h.w * acc);
+        const T fw = f * h.w;
+        rows[s][l][c0] -= f;
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          if (c > c0) rows[s][l][c] -= f * x[c];
-        if (s == PS && l == lk && g.gl == owner && active) {
-          rows[s][l][c0] = alpha;
+          if (c > c0) rows[s][l][c] -= fw * x[c];
+        if (s == PS && l == lk && g.gl == owner && h.active) {
+          rows[s][l][c0] = h.beta;
 #pragma unroll
           for (int c = 0; c < NC; ++c)
             if (c > c0) rows[s][l][c] = T(0);

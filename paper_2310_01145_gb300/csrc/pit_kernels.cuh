@@ -51,6 +51,24 @@ struct IeksParams {
   T phib[kMaxQ1 * kMaxQ1];   // Phibar (q+1)x(q+1), row-major
   T sqb[kMaxQ1 * kMaxQ1];    // lower Cholesky factor of Qbar
   T mu0[kMaxD];              // preconditioned exact initial state
+  // FP64 copies for the trajectory arithmetic (double or double-float on the device)
+  double mu0d[kMaxD];
+  double pd[kMaxParams];
+  double T0d, T1invd;
+  double Tdiagd[kMaxQ1];
+};
+
+// Number type of the linearisation trajectory: double-float for the FP32 solver, double for the
+// FP64 solver.
+template <typename T>
+struct TrajType;
+template <>
+struct TrajType<float> {
+  using type = df32;
+};
+template <>
+struct TrajType<double> {
+  using type = double;
 };
 
 // Scalars shared by the kernels of one solve (device memory, FP64).

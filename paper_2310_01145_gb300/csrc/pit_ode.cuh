@@ -107,3 +107,187 @@ __device__ __forceinline__ void ode_eval(const OdeParams<T>& P, const T (&y)[DD]
 }
 
 }  // namespace pit
+
+// ---------------------------------------------------------------------------------------------
+// Double-float arithmetic (a value is hi + lo, two FP32 numbers, about 48 significant bits),
+// after the error-free transformations of Knuth (TwoSum), Dekker (Fast2Sum) and the fused
+// multiply-add form of TwoProd.  Used for the linearisation trajectory and the residuals of the
+// FP32 solver, where FP32 rounding of large, slowly varying values would otherwise accumulate.
+// ---------------------------------------------------------------------------------------------
+namespace pit {
+
+struct df32 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ df32 operator+(df32 x, df32 y) {
+  float s, e, t, f;
+  two_sum(x.hi, y.hi, s, e);
+  two_sum(x.lo, y.lo, t, f);
+  e += t;
+  fast_two_sum(s, e, s, e);
+  e += f;
+  fast_two_sum(s, e, s, e);
+  return {s, e};
+}
+__device__ __forceinline__ df32 operator-(df32 x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df32 operator-(df32 x, df32 y) { return x + (-y); }
+__device__ __forceinline__ df32 operator*(df32 x, df32 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  float s;
+  fast_two_sum(p, e, s, e);
+  return {s, e};
+}
+__device__ __forceinline__ df32 operator*(df32 x, float b) {
+  const float p = x.hi * b;
+  float e = fmaf(x.hi, b, -p);
+  e = fmaf(x.lo, b, e);
+  float s;
+  fast_two_sum(p, e, s, e);
+  return {s, e};
+}
+__device__ __forceinline__ df32 operator+(df32 x, float b) {
+  float s, e;
+  two_sum(x.hi, b, s, e);
+  e += x.lo;
+  fast_two_sum(s, e, s, e);
+  return {s, e};
+}
+
+// conversions
+template <typename V>
+__device__ __forceinline__ V v_from_double(double x);
+template <>
+__device__ __forceinline__ double v_from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ df32 v_from_double<df32>(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - static_cast<double>(h))};
+}
+__device__ __forceinline__ float v_to_float(df32 x) { return x.hi + x.lo; }
+__device__ __forceinline__ double v_to_double(df32 x) {
+  return static_cast<double>(x.hi) + static_cast<double>(x.lo);
+}
+__device__ __forceinline__ double v_to_double(double x) { return x; }
+__device__ __forceinline__ df32 v_add_small(df32 x, float d) { return x + d; }
+__device__ __forceinline__ double v_add_small(double x, double d) { return x + d; }
+template <typename V>
+__device__ __forceinline__ V v_from_zero() {
+  return v_from_double<V>(0.0);
+}
+template <>
+__device__ __forceinline__ df32 v_from_zero<df32>() {
+  return {0.f, 0.f};
+}
+// round a trajectory value to the arithmetic type T of the scans
+template <typename T>
+__device__ __forceinline__ T v_to_T(df32 x) {
+  return static_cast<T>(x.hi + x.lo);
+}
+template <typename T>
+__device__ __forceinline__ T v_to_T(double x) {
+  return static_cast<T>(x);
+}
+__device__ __forceinline__ df32 operator*(df32 x, double) = delete;
+
+// Constants of the vector field in the trajectory number type V (double or df32).
+template <typename V>
+struct OdeConstsV {
+  int kind;
+  V k[8];
+  V L[12];  // affine (d <= 3): L (d x d) then c (d)
+};
+
+// Vector field f(y) in number type V (no Jacobian); parameter layouts as in pit.h.
+template <typename V, int DD>
+__device__ __forceinline__ void ode_f_v(const OdeConstsV<V>& P, const V (&y)[DD], V (&f)[DD]) {
+  switch (P.kind) {
+    case 0:
+      if constexpr (DD == 1) f[0] = P.k[0] * y[0] - P.k[0] * (y[0] * y[0]);
+      break;
+    case 1:  // k = [a, b, c, 1/c, 1/3]
+      if constexpr (DD == 2) {
+        const V v3 = y[0] * y[0] * y[0];
+        f[0] = P.k[2] * (y[0] - v3 * P.k[4] + y[1]);
+        f[1] = -((y[0] - P.k[0] + P.k[1] * y[1]) * P.k[3]);
+      }
+      break;
+    case 2:  // k = [al, be, ga, de]
+      if constexpr (DD == 2) {
+        const V xz = y[0] * y[1];
+        f[0] = P.k[0] * y[0] - P.k[1] * xz;
+        f[1] = P.k[3] * xz - P.k[2] * y[1];
+      }
+      break;
+    case 4:
+#pragma unroll
+      for (int i = 0; i < DD; ++i) {
+        V acc = P.L[DD * DD + i];
+#pragma unroll
+        for (int j = 0; j < DD; ++j) acc = acc + P.L[i * DD + j] * y[j];
+        f[i] = acc;
+      }
+      break;
+    case 5:  // k = [-2, 1.25, -0.5]
+      if constexpr (DD == 3) {
+        f[0] = P.k[0] * (y[1] * y[2]);
+        f[1] = P.k[1] * (y[0] * y[2]);
+        f[2] = P.k[2] * (y[0] * y[1]);
+      }
+      break;
+    case 6:  // k = [mu, 1]
+      if constexpr (DD == 2) {
+        f[0] = y[1];
+        f[1] = P.k[0] * ((P.k[1] - y[0] * y[0]) * y[1] - y[0]);
+      }
+      break;
+    default:
+      break;
+  }
+}
+
+template <typename V, typename T, int DD>
+__device__ __forceinline__ void ode_consts_v(const OdeParams<T>& P, const double* pd,
+                                             OdeConstsV<V>& c) {
+  c.kind = P.kind;
+  switch (P.kind) {
+    case 0: c.k[0] = v_from_double<V>(pd[0]); break;
+    case 1:
+      c.k[0] = v_from_double<V>(pd[0]);
+      c.k[1] = v_from_double<V>(pd[1]);
+      c.k[2] = v_from_double<V>(pd[2]);
+      c.k[3] = v_from_double<V>(1.0 / pd[2]);
+      c.k[4] = v_from_double<V>(1.0 / 3.0);
+      break;
+    case 2:
+      for (int i = 0; i < 4; ++i) c.k[i] = v_from_double<V>(pd[i]);
+      break;
+    case 4:
+      for (int i = 0; i < DD * DD + DD; ++i) c.L[i] = v_from_double<V>(pd[i]);
+      break;
+    case 5:
+      c.k[0] = v_from_double<V>(-2.0);
+      c.k[1] = v_from_double<V>(1.25);
+      c.k[2] = v_from_double<V>(-0.5);
+      break;
+    case 6:
+      c.k[0] = v_from_double<V>(pd[0]);
+      c.k[1] = v_from_double<V>(1.0);
+      break;
+    default: break;
+  }
+}
+
+}  // namespace pit

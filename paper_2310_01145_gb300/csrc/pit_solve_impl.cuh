@@ -14,26 +14,82 @@
 namespace pit {
 
 // ---- small elementwise kernels ---------------------------------------------------------------
+// Initial linearisation trajectory (preconditioned, trajectory number type V): the constant
+// mu0 of Algorithm 2, or a caller-provided warm start in original coordinates.
 template <class C>
 __global__ void k_init_traj(const IeksParams<typename C::Tp> p,
-                            const typename C::Tp* __restrict__ init, typename C::Tp* traj) {
+                            const typename C::Tp* __restrict__ init,
+                            typename TrajType<typename C::Tp>::type* __restrict__ lin) {
+  using V = typename TrajType<typename C::Tp>::type;
   const int64_t total = (p.N + 1) * C::D;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % C::D);
-    traj[i] = init ? init[i] / p.Tdiag[r % C::Q1] : p.mu0[r];
+    const double x = init ? static_cast<double>(init[i]) / p.Tdiagd[r % C::Q1] : p.mu0d[r];
+    lin[i] = v_from_double<V>(x);
+  }
+}
+
+// Inputs of the increment model of one iteration, in extended precision (double-float for the
+// FP32 solver): u_n = Phibar lin_n - lin_{n+1} (n < N), r_n = f(y_n)/T_1 - xbar_{1,n} (n >= 1)
+// with y_n = T_0 xbar_{0,n} (the solution components of lin_n, also stored in T for the
+// Jacobian), and delta_0 = mu0 - lin_0.  One thread per time step.
+template <class C>
+__global__ void __launch_bounds__(256)
+k_residuals(const IeksParams<typename C::Tp> p,
+            const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+            typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
+            typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  OdeConstsV<V> oc;
+  ode_consts_v<V, T, DD>(p.ode, p.pd, oc);
+  const V T0v = v_from_double<V>(p.T0d);
+  const V T1iv = v_from_double<V>(p.T1invd);
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= p.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    V x[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[r] = lin[n * D + r];
+    if (n < p.N) {
+#pragma unroll
+      for (int k = 0; k < DD; ++k) {
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+          V acc = x[k * Q1 + i];
+#pragma unroll
+          for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+          acc = acc - lin[(n + 1) * D + k * Q1 + i];
+          U[n * D + k * Q1 + i] = v_to_T<T>(acc);
+        }
+      }
+    }
+    V y[DD], f[DD];
+#pragma unroll
+    for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
+    ode_f_v<V, DD>(oc, y, f);
+#pragma unroll
+    for (int k = 0; k < DD; ++k) {
+      Yv[n * DD + k] = v_to_T<T>(y[k]);
+      R[n * DD + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
+    }
+    if (n == 0) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) d0[r] = v_to_T<T>(v_from_double<V>(p.mu0d[r]) - x[r]);
+    }
   }
 }
 
 template <class C>
 __global__ void k_export_mean(const IeksParams<typename C::Tp> p,
-                              const typename C::Tp* __restrict__ traj,
+                              const typename TrajType<typename C::Tp>::type* __restrict__ lin,
                               typename C::Tp* __restrict__ mean) {
   const int64_t total = (p.N + 1) * C::D;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % C::D);
-    mean[i] = p.Tdiag[r % C::Q1] * traj[i];
+    mean[i] = p.Tdiag[r % C::Q1] * v_to_T<typename C::Tp>(lin[i]);
   }
 }
 
@@ -249,6 +305,7 @@ struct Tree {
 template <typename T, int DD, int Q1, int G, int RL>
 struct SolverImpl {
   using C = Cfg<T, DD, Q1, G, RL>;
+  using V = typename TrajType<T>::type;
   static constexpr int D = C::D;
   static constexpr int NG = kThreads / G;
 
@@ -266,7 +323,10 @@ struct SolverImpl {
     std::memset(&p, 0, sizeof(p));
     p.ode.kind = pb.kind;
     p.ode.d = pb.d;
-    for (int i = 0; i < pb.n_params && i < kMaxParams; ++i) p.ode.p[i] = static_cast<T>(pb.params[i]);
+    for (int i = 0; i < pb.n_params && i < kMaxParams; ++i) {
+      p.ode.p[i] = static_cast<T>(pb.params[i]);
+      p.pd[i] = pb.params[i];
+    }
     p.N = pb.N;
     p.L = a.opts.chain_len > 0 ? a.opts.chain_len : default_chain_len(pb.N);
     p.P = pb.N / p.L + 1;
@@ -277,6 +337,7 @@ struct SolverImpl {
     if (prior_blocks(pb.q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
     for (int i = 0; i < Q1; ++i) {
       p.Tdiag[i] = static_cast<T>(Td[i]);
+      p.Tdiagd[i] = Td[i];
       for (int j = 0; j < Q1; ++j) {
         p.phib[i * kMaxQ1 + j] = static_cast<T>(Phib[i * Q1 + j]);
         p.sqb[i * kMaxQ1 + j] = static_cast<T>(sqb[i * Q1 + j]);
@@ -286,23 +347,34 @@ struct SolverImpl {
     p.h = static_cast<T>(h);
     p.T0 = static_cast<T>(Td[0]);
     p.T1inv = static_cast<T>(1.0 / Td[1]);
+    p.T0d = Td[0];
+    p.T1invd = 1.0 / Td[1];
     p.hq = static_cast<T>(h / pb.q);
     double mu0[kMaxD];
     if (taylor_init(pb, mu0) != PIT_OK) return PIT_EINVAL;
-    for (int r = 0; r < D; ++r) p.mu0[r] = static_cast<T>(mu0[r] / Td[r % Q1]);
+    for (int r = 0; r < D; ++r) {
+      p.mu0d[r] = mu0[r] / Td[r % Q1];
+      p.mu0[r] = static_cast<T>(p.mu0d[r]);
+    }
     return PIT_OK;
   }
 
   struct Buffers {
-    T *trajA, *trajB, *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
+    V *linA, *linB;
+    T *U, *R, *Yv, *d0;
+    T *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
     SolveScalars* scal;
   };
 
   static size_t carve(const SolveArgs& a, const IeksParams<T>& p, bool want_cov, Buffers& b) {
     Carver cv(a.workspace, a.ws_bytes);
     const int64_t N1 = p.N + 1;
-    b.trajA = cv.take<T>(N1 * D);
-    b.trajB = cv.take<T>(N1 * D);
+    b.linA = cv.take<V>(N1 * D);
+    b.linB = cv.take<V>(N1 * D);
+    b.U = cv.take<T>(N1 * D);
+    b.R = cv.take<T>(N1 * DD);
+    b.Yv = cv.take<T>(N1 * DD);
+    b.d0 = cv.take<T>(D);
     b.Es = cv.take<T>(N1 * D * D);
     b.gs = cv.take<T>(N1 * D);
     b.Ls = want_cov ? cv.take<T>(N1 * D * D) : nullptr;
@@ -318,24 +390,37 @@ struct SolverImpl {
 
   static size_t chain_smem() { return static_cast<size_t>(NG) * C::SCR * sizeof(T); }
 
-  // One filter pass + smoother pass at trajectory `lin` (Algorithm 1 in the linearised model).
+  static unsigned elem_grid(int64_t count, int threads) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, 152 * 16)));
+  }
+
+  // Residuals of the increment model at trajectory `lin` (once per iteration).
+  static int residuals(const IeksParams<T>& p, const Buffers& b, const V* lin, cudaStream_t s) {
+    k_residuals<C><<<elem_grid(p.N + 1, 256), 256, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0);
+    count_launches(1);
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  // One filter pass + smoother pass at trajectory `lin` (Algorithm 1 in the linearised model);
+  // needs residuals(lin) to have run.
   template <bool WITH_L>
-  static int pass(const IeksParams<T>& p, const Buffers& b, const T* lin, T* out_traj,
+  static int pass(const IeksParams<T>& p, const Buffers& b, const V* lin, V* lin_out,
                   T* mean_out, T* cov_out, cudaStream_t s) {
     const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
     const size_t sm = chain_smem();
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
-    k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, lin, b.fagg);
+    k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg);
     count_launches(1);
     int st = Tree<C, true, false, false>::run(b.fagg, p.P, b.fup, false, s);
     if (st != PIT_OK) return st;
-    k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, lin, b.fagg, b.Es, b.gs, b.Ls,
-                                                               b.sagg, b.scal);
+    k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg,
+                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal);
     count_launches(1);
     st = Tree<C, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
     if (st != PIT_OK) return st;
     k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
-                                                        out_traj, mean_out, cov_out, b.scal);
+                                                        lin_out, mean_out, cov_out, b.scal);
     count_launches(1);
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
@@ -384,7 +469,7 @@ struct SolverImpl {
     if (st != PIT_OK) return st;
     cudaStream_t s = a.stream;
     const int64_t total = (p.N + 1) * D;
-    const unsigned eg = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+    const unsigned eg = elem_grid(total, 256);
     T* mean = static_cast<T*>(a.mean);
     T* cov = static_cast<T*>(a.sqrtcov);
     pit_solve_info info;
@@ -394,32 +479,30 @@ struct SolverImpl {
     std::memset(&hs, 0, sizeof(hs));
 
     if (eks) {
-      // sequential EKS: one chain, local linearisation at the predicted mean
+      // sequential EKS: one chain, local linearisation at the predicted mean, plain model
       const size_t sm = chain_smem();
       PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
       IeksParams<T> ps = p;
       ps.L = static_cast<int>(p.N + 1);  // one chain: leaves n = 1..N, owns b_N
       ps.P = 1;
       if (want_cov)
-        k_filter_down<C, true, true><<<1, kThreads, sm, s>>>(ps, b.trajA, b.fagg, b.Es, b.gs,
-                                                              b.Ls, b.sagg, b.scal);
+        k_filter_down<C, true, true><<<1, kThreads, sm, s>>>(ps, b.U, b.R, b.Yv, b.d0, b.fagg,
+                                                              b.Es, b.gs, b.Ls, b.sagg, b.scal);
       else
-        k_filter_down<C, false, true><<<1, kThreads, sm, s>>>(ps, b.trajA, b.fagg, b.Es, b.gs,
-                                                               b.Ls, b.sagg, b.scal);
+        k_filter_down<C, false, true><<<1, kThreads, sm, s>>>(ps, b.U, b.R, b.Yv, b.d0, b.fagg,
+                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal);
       count_launches(1);
-      IeksParams<T> pm = p;
-      pm.L = static_cast<int>(p.N + 1);  // smoothing chain covers n = 0..N
-      pm.P = 1;
       if (want_cov) {
-        k_smooth_down<C, true><<<1, kThreads, sm, s>>>(pm, b.Es, b.gs, b.Ls, b.sagg, b.trajA,
-                                                       b.trajB, mean, cov, b.scal);
-      } else {
-        k_smooth_down<C, false><<<1, kThreads, sm, s>>>(pm, b.Es, b.gs, b.Ls, b.sagg, b.trajB,
-                                                        b.trajB, mean, cov, b.scal);
+        k_smooth_down<C, true><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
+                                                       nullptr, mean, cov, b.scal);
         count_launches(1);
-        k_export_mean<C><<<eg, 256, 0, s>>>(p, b.trajB, mean);
+      } else {
+        k_smooth_down<C, false><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
+                                                        b.linB, mean, cov, b.scal);
+        count_launches(1);
+        k_export_mean<C><<<eg, 256, 0, s>>>(p, b.linB, mean);
+        count_launches(1);
       }
-      count_launches(1);
       PIT_CUDA_TRY(cudaGetLastError());
       PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
       PIT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -431,16 +514,18 @@ struct SolverImpl {
       return PIT_OK;
     }
 
-    k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.trajA);
+    k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA);
     count_launches(1);
     PIT_CUDA_TRY(cudaGetLastError());
-    T* cur = b.trajA;  // linearisation trajectory of the current iteration
-    T* nxt = b.trajB;  // its smoothing means
+    V* cur = b.linA;  // linearisation trajectory of the current iteration
+    V* nxt = b.linB;  // its smoothing means
     const int fixed = a.opts.fixed_iters;
     const int limit = fixed > 0 ? fixed : std::max(1, a.opts.max_iter);
     bool converged = fixed > 0;
     int k = 0;
     while (k < limit) {
+      st = residuals(p, b, cur, s);
+      if (st != PIT_OK) return st;
       st = pass<false>(p, b, cur, nxt, nullptr, nullptr, s);
       if (st != PIT_OK) return st;
       ++k;
@@ -462,7 +547,8 @@ struct SolverImpl {
       std::swap(cur, nxt);
     }
     // outputs: the last iteration's means (nxt) and, if requested, covariances from a pass with
-    // the same linearisation trajectory (cur); that pass reproduces the same means.
+    // the same linearisation trajectory (cur, whose residuals are still in U, R, Yv); that pass
+    // reproduces the same means.
     if (want_cov) {
       st = pass<true>(p, b, cur, nullptr, mean, cov, s);
       if (st != PIT_OK) return st;
@@ -471,12 +557,13 @@ struct SolverImpl {
       count_launches(1);
     }
     PIT_CUDA_TRY(cudaGetLastError());
-    PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    SolveScalars hs2;
+    PIT_CUDA_TRY(cudaMemcpyAsync(&hs2, b.scal, sizeof(hs2), cudaMemcpyDeviceToHost, s));
     PIT_CUDA_TRY(cudaStreamSynchronize(s));
-    if (fixed > 0) info.last_delta = want_cov ? info.last_delta : hs.delta_max;
+    if (fixed > 0 && !want_cov) info.last_delta = hs2.delta_max;
     info.iterations = k;
     info.converged = converged ? 1 : 0;
-    info.sigma2 = a.opts.calibrate ? hs.sigma2_sum / (static_cast<double>(p.N) * DD) : 1.0;
+    info.sigma2 = a.opts.calibrate ? hs2.sigma2_sum / (static_cast<double>(p.N) * DD) : 1.0;
     info.kernel_launches = launches_total() - launches0;
     if (a.info) *a.info = info;
     return converged ? PIT_OK : PIT_ENOCONV;
