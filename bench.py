@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the time-parallel IEKS (ParaIEKS) on GB300.
+
+Workload (one "step" = one complete solve, i.e. one pass of the whole hot path): the
+FitzHugh-Nagumo ODE (a = b = 0.2, c = 3, y0 = (-1, 1), t in [0, 20]) under an IWP(3) prior
+(d = 2, D = 8) on a uniform grid of N = 2^20 steps, FP32 arithmetic in preconditioned
+coordinates (double-float trajectory), from the exact initial state and the constant initial
+trajectory until the change of the solution estimate is <= 1e-10 (or 64 iterations), then the
+quasi-MLE calibrated square-root covariances.  Metric: IEKS steps x iterations per second,
+sum of N k over the job / wall time.
+
+--impl reference times the FP64 CPU oracle (sequential square-root IEKS, numpy) on bounded
+samples of the same workload instead.  Multi-GPU (torchrun): independent replicas per rank
+(the solver has no cross-GPU exchange at this size); value sums all ranks' work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IEKS steps*iterations/s (FitzHugh-Nagumo, IWP(3), FP32) at <=1e-5 rel err vs FP64 oracle"
+UNIT = "steps*iterations/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("pit", "reference"), default="pit")
+    ap.add_argument("--N", type=int, default=2 ** 20)
+    ap.add_argument("--q", type=int, default=3)
+    ap.add_argument("--dtype", choices=("f32", "f64"), default="f32")
+    ap.add_argument("--max-iter", type=int, default=64)
+    ap.add_argument("--atol", type=float, default=1e-10)
+    ap.add_argument("--chain-len", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16384,
+                    help="time steps in the oracle's bounded CPU sample")
+    return ap.parse_args(argv)
+
+
+# ---- distributed helpers (replicas; also exercised by the gloo tests on CPU) ------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---- GPU clock sampling during the timed region -----------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, flags in rows:
+            for nm, val in zip(names, flags[1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---- CPU oracle sample ------------------------------------------------------------------------
+def oracle_sample(N_full: int, N_sample: int, q: int, iters: int = 1) -> dict:
+    """Time `iters` IEKS iterations of the FP64 oracle on the first N_sample steps of the
+    workload's grid (same step size), single-threaded, in a child process."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np, dataclasses
+import workloads as W
+from oracle import ieks
+p = W.fitzhugh_nagumo(N={N_full}, q={q})
+h = p.h
+p = dataclasses.replace(p, N={N_sample}, t1=p.t0 + h * {N_sample})
+t = time.perf_counter()
+r = ieks.ieks(p, fixed_iters={iters}, want_cov=False, calibrate=False)
+el = time.perf_counter() - t
+print(json.dumps({{"seconds": el, "steps": {N_sample}, "iters": {iters}}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+# ---- our arm ----------------------------------------------------------------------------------
+def run_pit(args):
+    import numpy as np
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+    from paper_2310_01145_gb300 import roofline
+    import workloads as W
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    prob = W.fitzhugh_nagumo(N=args.N, q=args.q)
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    esz = 4 if args.dtype == "f32" else 8
+    opts = pit.make_opts(dtype=tdt, max_iter=args.max_iter, atol_delta=args.atol,
+                         chain_len=args.chain_len)
+    ode = pit.ode_from_problem(prob)
+    D = prob.D
+    mean = torch.empty((prob.N + 1, D), dtype=tdt, device=dev)
+    cov = torch.empty((prob.N + 1, D, D), dtype=tdt, device=dev)
+    first = pit.pit_solve(ode, prob.y0, prob.t0, prob.t1, prob.N, prob.q, opts, out=(mean, cov))
+    ws = None
+    # reuse one workspace for every step (the solve never allocates)
+    import ctypes
+    lib = pit.load()
+    sz = ctypes.c_size_t(0)
+    c_ode, c_grid = ode.c(), pit._Grid(prob.t0, prob.t1, prob.N)
+    lib.pit_solve_workspace_size(ctypes.byref(c_ode), ctypes.byref(c_grid), prob.q,
+                                 ctypes.byref(opts), ctypes.byref(sz))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return pit.pit_solve(ode, prob.y0, prob.t0, prob.t1, prob.N, prob.q, opts,
+                             workspace=ws, out=(mean, cov), stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region (inputs resident; working set > L2: no flush needed) ----
+    pit.pit_profile_reset()
+    pit.pit_profile_enable(True)
+    launches0 = pit.pit_launch_count()
+    work = 0
+    iters = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            iters.append(r.iterations)
+            work += prob.N * r.iterations
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = pit.pit_launch_count() - launches0
+    pit.pit_profile_enable(False)
+    prof = pit.pit_profile_read()
+    ms_local = e0.elapsed_time(e1)
+    ms = reduce_max(ms_local, world, dev)
+    work_all = reduce_sum(float(work), world, dev)
+    value = work_all / (ms / 1e3)
+    clocks = clk.summary()
+
+    # ---- end-to-end through the C ABI with host buffers (outputs copied to pinned memory) ----
+    host_mean = torch.empty(mean.shape, dtype=tdt, pin_memory=True)
+    host_cov = torch.empty(cov.shape, dtype=tdt, pin_memory=True)
+    h2d = (prob.params.size + prob.y0.size) * 8
+    d2h = host_mean.numel() * esz + host_cov.numel() * esz
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    work_e2e = 0
+    for _ in range(args.steps):
+        r = step()
+        host_mean.copy_(mean, non_blocking=True)
+        host_cov.copy_(cov, non_blocking=True)
+        torch.cuda.synchronize()
+        work_e2e += prob.N * r.iterations
+    t_e2e = time.perf_counter() - t0
+    t_e2e = reduce_max(t_e2e, world, dev)
+    work_e2e = reduce_sum(float(work_e2e), world, dev)
+    e2e_value = work_e2e / t_e2e
+
+    # ---- roofline of the dominant kernel ----
+    k_iters = statistics.mean(iters)
+    shares = {k: v for k, v in prof.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in shares.values())
+    dom = max(shares, key=lambda k: shares[k][0])
+    dom_ms, dom_n = shares[dom]
+    avg_ms = dom_ms / dom_n
+    steps_per_launch = prob.N  # every chain kernel covers all N time steps
+    traj_elem = 8
+    if dom in ("filter_down", "filter_reduce", "residuals"):
+        if dom == "filter_down":
+            fl = roofline.filter_down_flops(D, prob.d, prob.q + 1)
+        elif dom == "filter_reduce":
+            fl = roofline.filter_reduce_flops(D, prob.d, prob.q + 1)
+        else:
+            fl = roofline.residuals_flops(D, prob.d, prob.q + 1)
+        achieved = fl * steps_per_launch / (avg_ms / 1e3) / 1e12
+        peak = roofline.fp32_alu_peak_tflops()
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "algorithmic_flops_per_step": fl}
+    else:
+        by = roofline.bytes_per_step("smooth_down", D, prob.d, esz, traj_elem)
+        achieved = by * steps_per_launch / (avg_ms / 1e3) / 1e9
+        peak = _measured_hbm()
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_bytes_per_step": by}
+    kernel_shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                         "share": v[0] / total_ms} for k, v in shares.items()}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            s = oracle_sample(args.N, args.cpu_sample, args.q)
+            cpu = {"value": s["steps"] * s["iters"] / s["seconds"], "unit": UNIT, "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"1 IEKS iteration of the FP64 numpy oracle on the first "
+                             f"{s['steps']} of the {args.N} steps (same h), single thread, "
+                             f"{s['seconds']:.1f} s"}
+        except Exception as exc:  # report, do not fail the bench line
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": f"FitzHugh-Nagumo d=2, IWP(q={args.q}) D={D}, N={args.N} uniform "
+                               f"steps on [0,20], constant initial trajectory, stop at "
+                               f"max|dy|<={args.atol:g} or {args.max_iter} iterations, "
+                               f"calibrated covariances",
+                   "iterations_per_solve": iters, "parallelism": f"replicas x{world}",
+                   "l2": "working set (E, g, trajectories: >300 MB) exceeds the 129 MB L2; "
+                         "no flush between steps"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_shares": kernel_shares,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+# ---- reference arm: the FP64 CPU oracle -------------------------------------------------------
+def run_reference(args):
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return
+    sample = min(args.N, 2048)
+    per = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(args.N, sample, args.q)
+        if i >= args.warmup:
+            per.append(s["seconds"])
+    secs = sum(per)
+    value = sample * len(per) / secs
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"FitzHugh-Nagumo d=2, IWP(q={args.q}), sampled from N={args.N}",
+                   "step": f"1 IEKS iteration of the sequential FP64 oracle on the first "
+                           f"{sample} steps (same h)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample} of {args.N} steps, 1 iteration per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_pit(args)
+
+
+if __name__ == "__main__":
+    main()

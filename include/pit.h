@@ -107,6 +107,8 @@ typedef struct {
   double last_delta;    /* max |change of E0 mean| in the last iteration                    */
   double sigma2;        /* quasi-MLE diffusion sigma^2 (1 when calibrate == 0)              */
   int64_t kernel_launches; /* CUDA kernels this call launched                               */
+  double deltas[64];    /* max |change of E0 mean| of iterations 1..min(iterations, 64) (0 when
+                           fixed_iters skips the per-iteration readback)                     */
 } pit_solve_info;
 
 /* ---- library ------------------------------------------------------------------------- */
@@ -121,6 +123,16 @@ const char* pit_last_error(void);
 int64_t pit_launch_count(void);
 /* Fill `opts` with the defaults documented in pit_opts. */
 void pit_opts_default(pit_opts* opts);
+
+/* Opt-in launch profiler.  While enabled, each kernel launch of the library is bracketed by two
+ * CUDA events recorded on its stream.  pit_profile_read waits for outstanding events and
+ * reports, per kernel class, the accumulated device time (ms) and launch count since the last
+ * pit_profile_reset: names (may be NULL) receives max_classes entries of 32 chars each,
+ * total_ms and launches (may be NULL) max_classes values.  Returns the number of classes the
+ * library defines (fill up to min(max_classes, that number)).  Host only, thread-safe. */
+void pit_profile_enable(int32_t on);
+void pit_profile_reset(void);
+int32_t pit_profile_read(int32_t max_classes, char* names, double* total_ms, int64_t* launches);
 
 /* ---- prior and initial state (host, FP64) --------------------------------------------- */
 

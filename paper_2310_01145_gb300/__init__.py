@@ -48,7 +48,7 @@ class _Opts(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("deltas", ctypes.c_double * 64)]
 
 
 _lib = None
@@ -62,6 +62,10 @@ SIGNATURES = {
     "pit_last_error": (ctypes.c_char_p, []),
     "pit_launch_count": (_I64, []),
     "pit_opts_default": (None, [ctypes.POINTER(_Opts)]),
+    "pit_profile_enable": (None, [_I32]),
+    "pit_profile_reset": (None, []),
+    "pit_profile_read": (_I32, [_I32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int64)]),
     "pit_prior": (_I32, [_I32, _D, _DP, _DP, _DP, _DP, _DP]),
     "pit_init_state": (_I32, [ctypes.POINTER(_Ode), _I32, _DP, _DP]),
     "pit_linearize": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _I32, _P, _P, _P, _P]),
@@ -172,6 +176,29 @@ def pit_launch_count() -> int:
     return int(load().pit_launch_count())
 
 
+def pit_profile_enable(on: bool = True) -> None:
+    load().pit_profile_enable(1 if on else 0)
+
+
+def pit_profile_reset() -> None:
+    load().pit_profile_reset()
+
+
+def pit_profile_read() -> dict:
+    """{kernel class: (total device ms, launches)} accumulated since the last reset."""
+    lib = load()
+    n = lib.pit_profile_read(0, None, None, None)
+    names = ctypes.create_string_buffer(32 * n)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    lib.pit_profile_read(n, names, ms, cnt)
+    out = {}
+    for i in range(n):
+        nm = names.raw[32 * i: 32 * (i + 1)].split(b"\0")[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out
+
+
 def pit_prior(q: int, h: float):
     """Host FP64 prior blocks: dict of Phi, Q, Phibar, sqrtQbar ((q+1)^2) and Tdiag (q+1)."""
     K = q + 1
@@ -279,8 +306,10 @@ def _solve_like(fn_ws, fn_run, ode: Ode, y0, t0, t1, N, q, opts: _Opts, init_tra
                     _tptr(workspace), workspace.numel(), _stream_ptr(stream))
     if not (st == 0 or (st == 4 and allow_noconv)):
         _check(st, "pit_solve")
-    return SolveResult(mean, cov, info.iterations, bool(info.converged), info.last_delta,
-                       info.sigma2, int(info.kernel_launches), int(st))
+    res = SolveResult(mean, cov, info.iterations, bool(info.converged), info.last_delta,
+                      info.sigma2, int(info.kernel_launches), int(st))
+    res.deltas = [float(info.deltas[i]) for i in range(min(info.iterations, 64))]
+    return res
 
 
 def pit_solve(ode: Ode, y0, t0: float, t1: float, N: int, q: int, opts: Optional[_Opts] = None,

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "pit_internal.h"
 #include "pit_ode.cuh"
@@ -20,6 +21,76 @@ static std::atomic<int64_t> g_launches{0};
 void set_error(const std::string& msg) { g_err = msg; }
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---- opt-in launch profiler ------------------------------------------------------------------
+// When enabled, every kernel launch is bracketed by two CUDA events recorded on its stream;
+// pit_profile_read() waits for the pending events and accumulates elapsed device time per
+// kernel class.  Events are pooled and reused.
+static const char* kClassNames[KC_COUNT] = {
+    "init_traj",       "residuals",        "filter_reduce",    "filter_down",
+    "smooth_down",     "tree_filter_up",   "tree_filter_down", "tree_smooth_up",
+    "tree_smooth_down", "export_mean",     "scan_filter",      "scan_smooth",
+    "linearize",       "eks_filter",       "eks_smooth"};
+struct Profiler {
+  std::atomic<bool> on{false};
+  std::mutex mu;
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  double total_ms[KC_COUNT] = {};
+  int64_t count[KC_COUNT] = {};
+  cudaEvent_t take() {
+    std::lock_guard<std::mutex> lk(mu);
+    if (pool.empty()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+};
+static Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+
+LaunchScope::LaunchScope(int c, cudaStream_t s) : cls(c), stream(s), begin(nullptr) {
+  Profiler& p = profiler();
+  if (p.on.load(std::memory_order_relaxed)) {
+    begin = p.take();
+    if (begin) cudaEventRecord(begin, s);
+  }
+}
+LaunchScope::~LaunchScope() {
+  count_launches(1);
+  if (!begin) return;
+  Profiler& p = profiler();
+  cudaEvent_t end = p.take();
+  if (!end) return;
+  cudaEventRecord(end, stream);
+  std::lock_guard<std::mutex> lk(p.mu);
+  p.pending.push_back({cls, begin, end});
+}
+
+static void profile_flush() {
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> lk(p.mu);
+  for (auto& r : p.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      p.total_ms[r.cls] += ms;
+      p.count[r.cls] += 1;
+    }
+    p.pool.push_back(r.a);
+    p.pool.push_back(r.b);
+  }
+  p.pending.clear();
+}
 
 // ---- registry -------------------------------------------------------------------------------
 struct Registry {
@@ -344,10 +415,10 @@ static int launch_linearize(const Problem& pb, const void* traj, void* H, void* 
   for (int i = 0; i < pb.n_params; ++i) op.p[i] = static_cast<T>(pb.params[i]);
   const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
   const unsigned grid = static_cast<unsigned>(std::min<int64_t>((pb.N + 255) / 256, 152 * 16));
-  k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h,
+  PIT_LAUNCH(KC_LINEARIZE, s, 
+             k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h,
                                            static_cast<const T*>(traj), static_cast<T*>(H),
-                                           static_cast<T*>(dv));
-  count_launches(1);
+                                           static_cast<T*>(dv)););
   PIT_CUDA_TRY(cudaGetLastError());
   return PIT_OK;
 }
@@ -378,6 +449,37 @@ const char* pit_status_string(int32_t s) {
 const char* pit_last_error(void) { return g_err.c_str(); }
 
 int64_t pit_launch_count(void) { return launches_total(); }
+
+void pit_profile_enable(int32_t on) {
+  if (!on) profile_flush();
+  profiler().on.store(on != 0);
+}
+
+void pit_profile_reset(void) {
+  profile_flush();
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> lk(p.mu);
+  for (int i = 0; i < KC_COUNT; ++i) {
+    p.total_ms[i] = 0.0;
+    p.count[i] = 0;
+  }
+}
+
+int32_t pit_profile_read(int32_t max_classes, char* names, double* total_ms, int64_t* launches) {
+  profile_flush();
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> lk(p.mu);
+  const int n = std::min<int>(max_classes, KC_COUNT);
+  for (int i = 0; i < n; ++i) {
+    if (names) {
+      std::memset(names + 32 * i, 0, 32);
+      std::strncpy(names + 32 * i, kClassNames[i], 31);
+    }
+    if (total_ms) total_ms[i] = p.total_ms[i];
+    if (launches) launches[i] = p.count[i];
+  }
+  return KC_COUNT;
+}
 
 void pit_opts_default(pit_opts* o) {
   if (!o) return;

@@ -54,6 +54,28 @@ void set_error(const std::string& msg);
 void count_launches(int64_t n);
 int64_t launches_total();
 
+// Kernel classes for the opt-in launch profiler (pit_profile_enable / pit_profile_read).
+enum KernelClass {
+  KC_INIT = 0, KC_RESIDUALS, KC_FILTER_REDUCE, KC_FILTER_DOWN, KC_SMOOTH_DOWN,
+  KC_TREE_FILTER_UP, KC_TREE_FILTER_DOWN, KC_TREE_SMOOTH_UP, KC_TREE_SMOOTH_DOWN,
+  KC_EXPORT, KC_SCAN_FILTER, KC_SCAN_SMOOTH, KC_LINEARIZE, KC_EKS_FILTER, KC_EKS_SMOOTH,
+  KC_COUNT
+};
+// Brackets one kernel launch: counts it and, when profiling is on, records CUDA events on the
+// launch stream around it.
+struct LaunchScope {
+  int cls;
+  cudaStream_t stream;
+  cudaEvent_t begin;
+  LaunchScope(int c, cudaStream_t s);
+  ~LaunchScope();
+};
+#define PIT_LAUNCH(cls, stream, ...)            \
+  do {                                           \
+    ::pit::LaunchScope pit_scope_((cls), (stream)); \
+    __VA_ARGS__;                                 \
+  } while (0)
+
 // Host FP64 helpers shared by the instantiations.
 int prior_blocks(int q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
                  double* Tdiag);

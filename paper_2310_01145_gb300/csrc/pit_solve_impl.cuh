@@ -282,19 +282,19 @@ struct Tree {
     const int top = static_cast<int>(arr.size()) - 1;
     for (int lvl = 0; lvl < top; ++lvl) {
       const unsigned grid = static_cast<unsigned>((cnt[lvl] + B - 1) / B);
-      k_tree_up<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(arr[lvl], cnt[lvl], B,
+      PIT_LAUNCH(FILTER ? KC_TREE_FILTER_UP : KC_TREE_SMOOTH_UP, s, 
+                 k_tree_up<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(arr[lvl], cnt[lvl], B,
                                                               arr[lvl + 1], 0,
-                                                              (lvl == 0 && rev_bottom) ? 1 : 0);
-      count_launches(1);
+                                                              (lvl == 0 && rev_bottom) ? 1 : 0););
     }
-    k_tree_up<C, OPS, REVERSE><<<1, kThreads, smem, s>>>(arr[top], cnt[top], B, nullptr, 1,
-                                                         (top == 0 && rev_bottom) ? 1 : 0);
-    count_launches(1);
+    PIT_LAUNCH(FILTER ? KC_TREE_FILTER_UP : KC_TREE_SMOOTH_UP, s, 
+               k_tree_up<C, OPS, REVERSE><<<1, kThreads, smem, s>>>(arr[top], cnt[top], B, nullptr, 1,
+                                                         (top == 0 && rev_bottom) ? 1 : 0););
     for (int lvl = top - 1; lvl >= 0; --lvl) {
       const unsigned grid = static_cast<unsigned>((cnt[lvl] + B - 1) / B);
-      k_tree_down<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(
-          arr[lvl], cnt[lvl], B, arr[lvl + 1], (lvl == 0 && rev_bottom) ? 1 : 0);
-      count_launches(1);
+      PIT_LAUNCH(FILTER ? KC_TREE_FILTER_DOWN : KC_TREE_SMOOTH_DOWN, s, 
+                 k_tree_down<C, OPS, REVERSE><<<grid, kThreads, smem, s>>>(
+          arr[lvl], cnt[lvl], B, arr[lvl + 1], (lvl == 0 && rev_bottom) ? 1 : 0););
     }
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
@@ -396,8 +396,8 @@ struct SolverImpl {
 
   // Residuals of the increment model at trajectory `lin` (once per iteration).
   static int residuals(const IeksParams<T>& p, const Buffers& b, const V* lin, cudaStream_t s) {
-    k_residuals<C><<<elem_grid(p.N + 1, 256), 256, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0);
-    count_launches(1);
+    PIT_LAUNCH(KC_RESIDUALS, s, 
+               k_residuals<C><<<elem_grid(p.N + 1, 256), 256, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
@@ -410,18 +410,18 @@ struct SolverImpl {
     const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
     const size_t sm = chain_smem();
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
-    k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg);
-    count_launches(1);
+    PIT_LAUNCH(KC_FILTER_REDUCE, s, 
+               k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg););
     int st = Tree<C, true, false, false>::run(b.fagg, p.P, b.fup, false, s);
     if (st != PIT_OK) return st;
-    k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg,
-                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal);
-    count_launches(1);
+    PIT_LAUNCH(KC_FILTER_DOWN, s, 
+               k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg,
+                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal););
     st = Tree<C, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
     if (st != PIT_OK) return st;
-    k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
-                                                        lin_out, mean_out, cov_out, b.scal);
-    count_launches(1);
+    PIT_LAUNCH(KC_SMOOTH_DOWN, s, 
+               k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
+                                                        lin_out, mean_out, cov_out, b.scal););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
@@ -486,22 +486,23 @@ struct SolverImpl {
       ps.L = static_cast<int>(p.N + 1);  // one chain: leaves n = 1..N, owns b_N
       ps.P = 1;
       if (want_cov)
-        k_filter_down<C, true, true><<<1, kThreads, sm, s>>>(ps, b.U, b.R, b.Yv, b.d0, b.fagg,
-                                                              b.Es, b.gs, b.Ls, b.sagg, b.scal);
+        PIT_LAUNCH(KC_EKS_FILTER, s,
+                   k_filter_down<C, true, true><<<1, kThreads, sm, s>>>(
+                       ps, b.U, b.R, b.Yv, b.d0, b.fagg, b.Es, b.gs, b.Ls, b.sagg, b.scal));
       else
-        k_filter_down<C, false, true><<<1, kThreads, sm, s>>>(ps, b.U, b.R, b.Yv, b.d0, b.fagg,
-                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal);
-      count_launches(1);
+        PIT_LAUNCH(KC_EKS_FILTER, s,
+                   k_filter_down<C, false, true><<<1, kThreads, sm, s>>>(
+                       ps, b.U, b.R, b.Yv, b.d0, b.fagg, b.Es, b.gs, b.Ls, b.sagg, b.scal));
       if (want_cov) {
-        k_smooth_down<C, true><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
-                                                       nullptr, mean, cov, b.scal);
-        count_launches(1);
+        PIT_LAUNCH(KC_EKS_SMOOTH, s, 
+                   k_smooth_down<C, true><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
+                                                       nullptr, mean, cov, b.scal););
       } else {
-        k_smooth_down<C, false><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
-                                                        b.linB, mean, cov, b.scal);
-        count_launches(1);
-        k_export_mean<C><<<eg, 256, 0, s>>>(p, b.linB, mean);
-        count_launches(1);
+        PIT_LAUNCH(KC_EKS_SMOOTH, s, 
+                   k_smooth_down<C, false><<<1, kThreads, sm, s>>>(ps, b.Es, b.gs, b.Ls, b.sagg, nullptr,
+                                                        b.linB, mean, cov, b.scal););
+        PIT_LAUNCH(KC_EXPORT, s, 
+                   k_export_mean<C><<<eg, 256, 0, s>>>(p, b.linB, mean););
       }
       PIT_CUDA_TRY(cudaGetLastError());
       PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -514,8 +515,8 @@ struct SolverImpl {
       return PIT_OK;
     }
 
-    k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA);
-    count_launches(1);
+    PIT_LAUNCH(KC_INIT, s, 
+               k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA););
     PIT_CUDA_TRY(cudaGetLastError());
     V* cur = b.linA;  // linearisation trajectory of the current iteration
     V* nxt = b.linB;  // its smoothing means
@@ -538,6 +539,7 @@ struct SolverImpl {
           return PIT_ENONFINITE;
         }
         info.last_delta = hs.delta_max;
+        if (k <= 64) info.deltas[k - 1] = hs.delta_max;
         if (hs.delta_max <= a.opts.atol_delta + a.opts.rtol_delta * hs.y_max) {
           converged = true;
           stop = true;
@@ -553,8 +555,8 @@ struct SolverImpl {
       st = pass<true>(p, b, cur, nullptr, mean, cov, s);
       if (st != PIT_OK) return st;
     } else {
-      k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean);
-      count_launches(1);
+      PIT_LAUNCH(KC_EXPORT, s, 
+                 k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean););
     }
     PIT_CUDA_TRY(cudaGetLastError());
     SolveScalars hs2;
@@ -598,12 +600,12 @@ struct ScanImpl {
                                       (int)sm));
     const unsigned grid = static_cast<unsigned>((P + NG - 1) / NG);
     T *A = (T*)a.x0, *b = (T*)a.x1, *Cm = (T*)a.x2, *eta = (T*)a.x3, *J = (T*)a.x4;
-    k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 0);
-    count_launches(1);
+    PIT_LAUNCH(KC_SCAN_FILTER, a.stream, 
+               k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 0););
     int st = Tree<C, true, false, false>::run(items, P, up, false, a.stream);
     if (st != PIT_OK) return st;
-    k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 1);
-    count_launches(1);
+    PIT_LAUNCH(KC_SCAN_FILTER, a.stream, 
+               k_gen_filter<C><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, A, b, Cm, eta, J, items, 1););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
@@ -627,12 +629,12 @@ struct ScanImpl {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const unsigned grid = static_cast<unsigned>((P + NG - 1) / NG);
     T *E = (T*)a.x0, *g = (T*)a.x1, *Lm = (T*)a.x2;
-    k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 0);
-    count_launches(1);
+    PIT_LAUNCH(KC_SCAN_SMOOTH, a.stream, 
+               k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 0););
     int st = Tree<C, false, WITH_L, true>::run(items, P, up, true, a.stream);
     if (st != PIT_OK) return st;
-    k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 1);
-    count_launches(1);
+    PIT_LAUNCH(KC_SCAN_SMOOTH, a.stream, 
+               k_gen_smooth<C, WITH_L><<<grid, kThreads, sm, a.stream>>>(a.N, L, P, E, g, Lm, items, 1););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
