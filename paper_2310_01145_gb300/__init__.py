@@ -77,6 +77,8 @@ SIGNATURES = {
                                         ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
     "pit_solve": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                          ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P, _SZ, _P]),
+    "pit_solve_noalloc": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
+                                 ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P]),
     "pit_eks_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
                                       ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
     "pit_eks_sequential": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
