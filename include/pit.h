@@ -98,6 +98,8 @@ typedef struct {
   int32_t calibrate;    /* [1]   quasi-MLE diffusion (Section 2.4) rescales the covariances */
   int32_t want_cov;     /* [1]   write square-root covariances (needs `sqrtcov`)            */
   int32_t chain_len;    /* [0]   time steps per sequential chain inside the scans, 0 = auto  */
+  int32_t variant;      /* [0]   kernel layout: 0 = one state row per lane; 1 = two rows per
+                                 lane (half the lanes per chain); others PIT_EUNSUPPORTED    */
 } pit_opts;
 
 /* Per-solve report, written by pit_solve (host memory). */

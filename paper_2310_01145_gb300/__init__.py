@@ -42,7 +42,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
                 ("atol_delta", ctypes.c_double), ("rtol_delta", ctypes.c_double),
                 ("dtype", ctypes.c_int32), ("calibrate", ctypes.c_int32),
-                ("want_cov", ctypes.c_int32), ("chain_len", ctypes.c_int32)]
+                ("want_cov", ctypes.c_int32), ("chain_len", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -161,12 +162,13 @@ def pit_opts_default() -> _Opts:
 
 
 def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
-              calibrate=True, want_cov=True, chain_len=0) -> _Opts:
+              calibrate=True, want_cov=True, chain_len=0, variant=0) -> _Opts:
     o = pit_opts_default()
     o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
     o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
     o.dtype = _dtype_code(dtype)
     o.calibrate, o.want_cov, o.chain_len = int(bool(calibrate)), int(bool(want_cov)), int(chain_len)
+    o.variant = int(variant)
     return o
 
 

@@ -95,7 +95,7 @@ static void profile_flush() {
 // ---- registry -------------------------------------------------------------------------------
 struct Registry {
   std::mutex mu;
-  std::map<int, SolveFn> solvers;  // key dtype*10000 + d*100 + q
+  std::map<int, SolveFn> solvers;  // key variant*100000 + dtype*10000 + d*100 + q
   std::map<int, ScanFn> fscans;    // key dtype*100 + D
   std::map<int, ScanFn> sscans;
 };
@@ -103,10 +103,10 @@ static Registry& registry() {
   static Registry r;
   return r;
 }
-Registrar::Registrar(int dtype, int d, int q, SolveFn fn) {
+Registrar::Registrar(int dtype, int d, int q, int variant, SolveFn fn) {
   Registry& r = registry();
   std::lock_guard<std::mutex> lk(r.mu);
-  r.solvers[dtype * 10000 + d * 100 + q] = fn;
+  r.solvers[variant * 100000 + dtype * 10000 + d * 100 + q] = fn;
 }
 ScanRegistrar::ScanRegistrar(int dtype, int D, ScanFn f, ScanFn s) {
   Registry& r = registry();
@@ -114,10 +114,10 @@ ScanRegistrar::ScanRegistrar(int dtype, int D, ScanFn f, ScanFn s) {
   r.fscans[dtype * 100 + D] = f;
   r.sscans[dtype * 100 + D] = s;
 }
-SolveFn find_solver(int dtype, int d, int q) {
+SolveFn find_solver(int dtype, int d, int q, int variant) {
   Registry& r = registry();
   std::lock_guard<std::mutex> lk(r.mu);
-  auto it = r.solvers.find(dtype * 10000 + d * 100 + q);
+  auto it = r.solvers.find(variant * 100000 + dtype * 10000 + d * 100 + q);
   return it == r.solvers.end() ? nullptr : it->second;
 }
 ScanFn find_filter_scan(int dtype, int D) {
@@ -374,7 +374,8 @@ static int check_opts(const pit_opts* in, pit_opts& o) {
   pit_opts_default(&o);
   if (in) o = *in;
   if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||
-      (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20)) {
+      (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20) ||
+      o.variant < 0 || o.variant > 9) {
     set_error("invalid pit_opts");
     return PIT_EINVAL;
   }
@@ -491,6 +492,7 @@ void pit_opts_default(pit_opts* o) {
   o->calibrate = 1;
   o->want_cov = 1;
   o->chain_len = 0;
+  o->variant = 0;
 }
 
 int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
@@ -602,9 +604,10 @@ static int32_t solve_common(const pit_ode* ode, const pit_grid* grid, int32_t q,
   if (st != PIT_OK) return st;
   st = check_opts(opts, a.opts);
   if (st != PIT_OK) return st;
-  SolveFn fn = find_solver(a.opts.dtype, a.pb.d, q);
+  SolveFn fn = find_solver(a.opts.dtype, a.pb.d, q, a.opts.variant);
   if (!fn) {
-    set_error("no compiled kernels for this (dtype, d, q); compiled: d in 1..3, q in 1..3 (d=3: q <= 2)");
+    set_error("no compiled kernels for this (dtype, d, q, variant); compiled: d in 1..3, q in 1..3 "
+              "(d=3: q <= 2), variant 1 for D = d (q+1) in {6, 8}");
     return PIT_EUNSUPPORTED;
   }
   a.init_traj = init_traj;

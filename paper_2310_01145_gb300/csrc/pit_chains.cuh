@@ -557,19 +557,22 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 // REVERSE the operator's operands are swapped so that the result at item k is
 // item_k (x) item_{k+1} (x) ... (the reverse scan of Section 3.1.3).
 // ---------------------------------------------------------------------------------------------
-template <class C, bool FILTER, bool WITH_L>
+template <class C, bool FILTER, bool WITH_L, bool VALUES_DOWN = false>
 struct TreeOps {
   using T = typename C::Tp;
   static constexpr int SZ = FILTER ? C::FA : C::SA;
   static __device__ __forceinline__ void identity(const typename C::GR& g, T* x) {
     if constexpr (FILTER) set_identity_f<C>(g, x); else set_identity_s<C>(g, x);
   }
-  // out = earlier (x) later   (forward);  out = later (x)_s earlier  in reverse mode
-  template <bool REVERSE>
+  // out = earlier (x) later   (forward);  out = later (x)_s earlier  in reverse mode.
+  // DOWN: a down-sweep combine (prefix (x) left sum).  With VALUES_DOWN the filter down-sweep
+  // forms only b and C of the result: every prefix of the IEKS scan starts at the initial
+  // state, and b, C of (prefix (x) x) depend on the prefix only through its b, C.
+  template <bool REVERSE, bool DOWN = false>
   static __device__ __forceinline__ void op(const typename C::GR& g, const T* earlier,
                                             const T* later, T* out, T* scr) {
     if constexpr (FILTER) {
-      combine_f<C, false>(g, earlier, later, out, scr);
+      combine_f<C, DOWN && VALUES_DOWN>(g, earlier, later, out, scr);
     } else {
       if constexpr (REVERSE) combine_s<C, WITH_L>(g, later, earlier, out, scr);
       else combine_s<C, WITH_L>(g, earlier, later, out, scr);
@@ -583,8 +586,10 @@ __device__ __forceinline__ int64_t tree_item_index(int64_t n, int64_t pos, bool 
 
 // Brent-Kung up-sweep over B items in shared memory (`items`), then (DOWN) Blelloch down-sweep
 // with `prefix` as the block's exclusive prefix.  ngroups groups of the block take the combines.
+// Positions >= nv hold neutral padding: combines whose right operand covers only padding become
+// copies, combines of two padding nodes are skipped.
 template <class C, class OPS, bool REVERSE>
-__device__ void block_tree(typename C::Tp* items, int B, typename C::Tp* tmp,
+__device__ void block_tree(typename C::Tp* items, int B, int nv, typename C::Tp* tmp,
                            typename C::Tp* scr, const typename C::GR& g, int grp, int ngroups,
                            bool up, bool down, const typename C::Tp* prefix) {
   using T = typename C::Tp;
@@ -595,6 +600,12 @@ __device__ void block_tree(typename C::Tp* items, int B, typename C::Tp* tmp,
       for (int pr = grp; pr < npairs; pr += ngroups) {
         const int i = (pr + 1) * 2 * stride - 1;
         const int j = i - stride;
+        if (j - stride + 1 >= nv) continue;            // both subtrees padding
+        if (j + 1 >= nv) {                             // right subtree padding
+          copy_item<C, SZ>(g, items + j * SZ, items + i * SZ);
+          g.sync();
+          continue;
+        }
         OPS::template op<REVERSE>(g, items + j * SZ, items + i * SZ, items + i * SZ, scr);
       }
       __syncthreads();
@@ -611,12 +622,17 @@ __device__ void block_tree(typename C::Tp* items, int B, typename C::Tp* tmp,
       for (int pr = grp; pr < npairs; pr += ngroups) {
         const int i = (pr + 1) * 2 * stride - 1;
         const int j = i - stride;
+        if (j - stride + 1 >= nv) {                    // left subtree padding: prefix passes
+          copy_item<C, SZ>(g, items + i * SZ, items + j * SZ);
+          g.sync();
+          continue;
+        }
         T* tj = tmp;
         copy_item<C, SZ>(g, items + j * SZ, tj);
         g.sync();
         copy_item<C, SZ>(g, items + i * SZ, items + j * SZ);
         g.sync();
-        OPS::template op<REVERSE>(g, items + j * SZ, tj, items + i * SZ, scr);
+        OPS::template op<REVERSE, true>(g, items + j * SZ, tj, items + i * SZ, scr);
       }
       __syncthreads();
     }
@@ -648,7 +664,8 @@ k_tree_up(typename C::Tp* __restrict__ items, int64_t n, int B,
     else OPS::identity(g, sitems + pos * SZ);
   }
   __syncthreads();
-  block_tree<C, OPS, REVERSE>(sitems, B, tmp, scr, g, grp, ngroups, true, single != 0, nullptr);
+  const int nv = static_cast<int>((n - base) < B ? (n - base) : B);
+  block_tree<C, OPS, REVERSE>(sitems, B, nv, tmp, scr, g, grp, ngroups, true, single != 0, nullptr);
   for (int pos = grp; pos < B; pos += ngroups) {
     const int64_t gp = base + pos;
     if (gp < n) copy_item<C, SZ>(g, sitems + pos * SZ, items + tree_item_index(n, gp, rev_index != 0) * SZ);
@@ -680,7 +697,8 @@ k_tree_down(typename C::Tp* __restrict__ items, int64_t n, int B,
     else OPS::identity(g, sitems + pos * SZ);
   }
   __syncthreads();
-  block_tree<C, OPS, REVERSE>(sitems, B, tmp, scr, g, grp, ngroups, false, true,
+  const int nv = static_cast<int>((n - base) < B ? (n - base) : B);
+  block_tree<C, OPS, REVERSE>(sitems, B, nv, tmp, scr, g, grp, ngroups, false, true,
                               block_prefix + blockIdx.x * SZ);
   for (int pos = grp; pos < B; pos += ngroups) {
     const int64_t gp = base + pos;

@@ -36,6 +36,21 @@ struct RoundUp {
   static constexpr int value = ((N + A - 1) / A) * A;
 };
 
+// sum_{j<N} f(j) with four independent partial sums: shortens the dependent multiply-add chain
+// of dot products and norms (the summation order differs from a left fold).
+template <typename T, int N, class F>
+__device__ __forceinline__ T sum4(F f) {
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll
+  for (int j = 0; j < N; j += 4) {
+    a0 += f(j);
+    if (j + 1 < N) a1 += f(j + 1);
+    if (j + 2 < N) a2 += f(j + 2);
+    if (j + 3 < N) a3 += f(j + 3);
+  }
+  return (a0 + a1) + (a2 + a3);
+}
+
 // Group geometry.  D rows, G lanes, RL rows per lane.
 template <typename T, int D_, int G_, int RL_>
 struct Grp {
@@ -101,9 +116,7 @@ struct SafeRange<double> {
 
 template <typename T, int NE, class GetX>
 __device__ __forceinline__ Reflector<T> make_reflector_g(T x0, GetX xe) {
-  T sig = T(0);
-#pragma unroll
-  for (int j = 0; j < NE; ++j) sig += xe(j) * xe(j);
+  T sig = sum4<T, NE>([&](int j) { return xe(j) * xe(j); });
   Reflector<T> h;
   T ss = x0 * x0 + sig;
   T nrm;
@@ -171,9 +184,7 @@ __device__ __forceinline__ void lq_tri_ext(const GR& g, T (&tri)[NS][GR::RL][GR:
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
       for (int l = 0; l < RL; ++l) {
-        T acc = T(0);
-#pragma unroll
-        for (int j = 0; j < NE; ++j) acc += ext[s][l][j] * xe[j];
+        const T acc = sum4<T, NE>([&](int j) { return ext[s][l][j] * xe[j]; });
         const T f = h.tau * (tri[s][l][i] + h.w * acc);
         const T fw = f * h.w;
         tri[s][l][i] -= f;
@@ -224,10 +235,7 @@ __device__ __forceinline__ void lq_dense(const GR& g, T (&rows)[NS][GR::RL][NC],
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
       for (int l = 0; l < RL; ++l) {
-        T acc = T(0);
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          if (c > c0) acc += rows[s][l][c] * x[c];
+        const T acc = sum4<T, NC>([&](int c) { return (c > c0) ? rows[s][l][c] * x[c] : T(0); });
         const T f = h.tau * (rows[s][l][c0] + h.w * acc);
         const T fw = f * h.w;
         rows[s][l][c0] -= f;

@@ -7,14 +7,14 @@ namespace {
 int solve_1_1(const SolveArgs& a, size_t* w, bool e) {
   return SolverImpl<float, 1, 2, 4, 1>::run(a, w, e);
 }
-Registrar reg_1_1(PIT_F32, 1, 1, solve_1_1);
+Registrar reg_1_1(PIT_F32, 1, 1, 0, solve_1_1);
 int solve_1_2(const SolveArgs& a, size_t* w, bool e) {
   return SolverImpl<float, 1, 3, 4, 1>::run(a, w, e);
 }
-Registrar reg_1_2(PIT_F32, 1, 2, solve_1_2);
+Registrar reg_1_2(PIT_F32, 1, 2, 0, solve_1_2);
 int solve_1_3(const SolveArgs& a, size_t* w, bool e) {
   return SolverImpl<float, 1, 4, 4, 1>::run(a, w, e);
 }
-Registrar reg_1_3(PIT_F32, 1, 3, solve_1_3);
+Registrar reg_1_3(PIT_F32, 1, 3, 0, solve_1_3);
 }  // namespace
 }  // namespace pit

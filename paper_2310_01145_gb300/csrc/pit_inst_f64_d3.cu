@@ -7,10 +7,14 @@ namespace {
 int solve_3_1(const SolveArgs& a, size_t* w, bool e) {
   return SolverImpl<double, 3, 2, 8, 1>::run(a, w, e);
 }
-Registrar reg_3_1(PIT_F64, 3, 1, solve_3_1);
+Registrar reg_3_1(PIT_F64, 3, 1, 0, solve_3_1);
+int solve_3_1_v1(const SolveArgs& a, size_t* w, bool e) {
+  return SolverImpl<double, 3, 2, 4, 2, 8, 1>::run(a, w, e);
+}
+Registrar reg_3_1_v1(PIT_F64, 3, 1, 1, solve_3_1_v1);
 int solve_3_2(const SolveArgs& a, size_t* w, bool e) {
   return SolverImpl<double, 3, 3, 16, 1>::run(a, w, e);
 }
-Registrar reg_3_2(PIT_F64, 3, 2, solve_3_2);
+Registrar reg_3_2(PIT_F64, 3, 2, 0, solve_3_2);
 }  // namespace
 }  // namespace pit

@@ -85,13 +85,13 @@ int taylor_init(const Problem& pb, double* mu0);
 using SolveFn = int (*)(const SolveArgs&, size_t* ws_query, bool eks);
 using ScanFn = int (*)(const ScanArgs&, size_t* ws_query);
 
-SolveFn find_solver(int dtype, int d, int q);
+SolveFn find_solver(int dtype, int d, int q, int variant);
 ScanFn find_filter_scan(int dtype, int D);
 ScanFn find_smooth_scan(int dtype, int D);
 
 // Registration (each instantiation file registers its functions at static-init time).
 struct Registrar {
-  Registrar(int dtype, int d, int q, SolveFn fn);
+  Registrar(int dtype, int d, int q, int variant, SolveFn fn);
 };
 struct ScanRegistrar {
   ScanRegistrar(int dtype, int D, ScanFn filter_fn, ScanFn smooth_fn);

@@ -230,10 +230,10 @@ k_gen_smooth(int64_t N, int L, int64_t P, typename C::Tp* E, typename C::Tp* gv,
 }
 
 // ---- tree driver -----------------------------------------------------------------------------
-template <class C, bool FILTER, bool WITH_L, bool REVERSE>
+template <class C, bool FILTER, bool WITH_L, bool REVERSE, bool VALUES_DOWN = false>
 struct Tree {
   using T = typename C::Tp;
-  using OPS = TreeOps<C, FILTER, WITH_L>;
+  using OPS = TreeOps<C, FILTER, WITH_L, VALUES_DOWN>;
   static constexpr int SZ = OPS::SZ;
   static constexpr int NG = kThreads / C::G;
   static int block_items() {
@@ -302,9 +302,11 @@ struct Tree {
 };
 
 // ---- the solver ------------------------------------------------------------------------------
-template <typename T, int DD, int Q1, int G, int RL>
+// C: layout of the chain kernels; CT: layout of the tree kernels (items are layout-free).
+template <typename T, int DD, int Q1, int G, int RL, int GT = G, int RLT = RL>
 struct SolverImpl {
   using C = Cfg<T, DD, Q1, G, RL>;
+  using CT = Cfg<T, DD, Q1, GT, RLT>;
   using V = typename TrajType<T>::type;
   static constexpr int D = C::D;
   static constexpr int NG = kThreads / G;
@@ -379,10 +381,10 @@ struct SolverImpl {
     b.gs = cv.take<T>(N1 * D);
     b.Ls = want_cov ? cv.take<T>(N1 * D * D) : nullptr;
     b.fagg = cv.take<T>(p.P * C::FA);
-    b.fup = cv.take<T>(Tree<C, true, false, false>::upper_bytes(p.P) / sizeof(T) + 1);
+    b.fup = cv.take<T>(Tree<CT, true, false, false, true>::upper_bytes(p.P) / sizeof(T) + 1);
     b.sagg = cv.take<T>(p.P * C::SA);
-    const size_t sup_bytes = std::max(Tree<C, false, false, true>::upper_bytes(p.P),
-                                      Tree<C, false, true, true>::upper_bytes(p.P));
+    const size_t sup_bytes = std::max(Tree<CT, false, false, true>::upper_bytes(p.P),
+                                      Tree<CT, false, true, true>::upper_bytes(p.P));
     b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
     b.scal = cv.take<SolveScalars>(1);
     return cv.used();
@@ -412,12 +414,12 @@ struct SolverImpl {
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
     PIT_LAUNCH(KC_FILTER_REDUCE, s, 
                k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg););
-    int st = Tree<C, true, false, false>::run(b.fagg, p.P, b.fup, false, s);
+    int st = Tree<CT, true, false, false, true>::run(b.fagg, p.P, b.fup, false, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_FILTER_DOWN, s, 
                k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg,
                                                                b.Es, b.gs, b.Ls, b.sagg, b.scal););
-    st = Tree<C, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
+    st = Tree<CT, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_SMOOTH_DOWN, s, 
                k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
