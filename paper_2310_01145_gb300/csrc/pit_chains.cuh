@@ -1,6 +1,8 @@
 // Chain kernels of one IEKS iteration and the block-level/grid-level tree scans.
 #pragma once
 
+#include <type_traits>
+
 #include "pit_kernels.cuh"
 
 namespace pit {
@@ -48,6 +50,35 @@ __device__ __forceinline__ void load_forcing(const typename C::GR& g,
   for (int l = 0; l < C::RL; ++l) uf[l] = g.valid(l) ? U[n * C::D + g.row(l)] : typename C::Tp(0);
 }
 
+// Raw per-step inputs (loaded one step ahead to hide their latency).
+template <class C>
+struct StepIn {
+  using T = typename C::Tp;
+  T y[C::DD];  // solution components of lin_n (original coordinates, for the Jacobian)
+  T r[C::DD];  // residual r_n
+  T u[C::RL];  // forcing u_{n-1}, this lane's rows
+  __device__ __forceinline__ void load(const typename C::GR& g, const T* __restrict__ Yv,
+                                       const T* __restrict__ R, const T* __restrict__ U,
+                                       int64_t n) {
+#pragma unroll
+    for (int k = 0; k < C::DD; ++k) {
+      y[k] = Yv[n * C::DD + k];
+      r[k] = R[n * C::DD + k];
+    }
+    load_forcing<C>(g, U, n - 1, u);
+  }
+  __device__ __forceinline__ void jacobian(const IeksParams<T>& p, T (&Ft)[C::DD][C::DD]) const {
+    T f[C::DD], F[C::DD][C::DD];
+    ode_eval<T, C::DD>(p.ode, y, f, F);
+#pragma unroll
+    for (int k = 0; k < C::DD; ++k)
+#pragma unroll
+      for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * p.hq;
+  }
+};
+
+constexpr int kJBatch = 4;  // leaves whose information rows are folded into sqrtJ at once
+
 // ---------------------------------------------------------------------------------------------
 // Filter reduce: chain c folds its leaves n = cL+1 .. min(cL+L, N) into the aggregate
 // a_{cL+1} (x)_f ... (x)_f a_{end}; chain 0 starts from the initial state (A = 0, b = delta_0,
@@ -87,12 +118,25 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     b[l] = (chain == 0 && r < D) ? d0[r] : T(0);
     eta[l] = T(0);
   }
+  // information rows G^T of the last kJBatch leaves, folded into sqrtJ by one structured LQ
+  T Gbuf[1][RL][kJBatch * DD];
+#pragma unroll
+  for (int l = 0; l < RL; ++l)
+#pragma unroll
+    for (int j = 0; j < kJBatch * DD; ++j) Gbuf[0][l][j] = T(0);
+  int nbuf = 0;
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
+  StepIn<C> cur, nxt;
+  if (n0 <= n1) cur.load(g, Yv, R, U, n0);
   for (int64_t n = n0; n <= n1; ++n) {
+    if (n + 1 <= n1) nxt.load(g, Yv, R, U, n + 1);
     T Ft[DD][DD], rr[DD], uf[RL];
-    step_inputs<C>(p, Yv, R, n, Ft, rr);
-    load_forcing<C>(g, U, n - 1, uf);
+    cur.jacobian(p, Ft);
+#pragma unroll
+    for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) uf[l] = cur.u[l];
     // predict the conditional filter: A' = Phi A, b' = Phi b + u, C- = tria([sqrtQ | Phi sqrtC])
     publish<GR, D, LDM>(g, A, scr + C::MAT0);
     publish<GR, W, LDM>(g, sC, scr + C::MAT1);
@@ -159,7 +203,23 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
       }
       eta[l] = acc;
     }
-    lq_tri_ext<GR, 1, DD>(g, sJ, Gt, scr + C::PIV);
+    // shift the batch left by one leaf and append this leaf's rows
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+#pragma unroll
+      for (int j = 0; j < (kJBatch - 1) * DD; ++j) Gbuf[0][l][j] = Gbuf[0][l][j + DD];
+#pragma unroll
+      for (int kk = 0; kk < DD; ++kk) Gbuf[0][l][(kJBatch - 1) * DD + kk] = Gt[0][l][kk];
+    }
+    if (++nbuf == kJBatch || n == n1) {
+      lq_tri_ext<GR, 1, kJBatch * DD>(g, sJ, Gbuf, scr + C::PIV);
+#pragma unroll
+      for (int l = 0; l < RL; ++l)
+#pragma unroll
+        for (int j = 0; j < kJBatch * DD; ++j) Gbuf[0][l][j] = T(0);
+      nbuf = 0;
+    }
+    cur = nxt;
   }
   // triangularise sqrtC (D x W -> D x D lower) and write the chain item
   T Cfull[1][RL][D];
@@ -296,51 +356,63 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
-  for (int64_t n = n0; n <= n1; ++n) {
+  StepIn<C> cur, nxt;
+  if (!LOCAL_LIN && n0 <= n1) cur.load(g, Yv, R, U, n0);
+  // One Kalman step n.  NE = number of columns of sqrtP in use: D for a prefix that comes from
+  // the tree (a full triangular factor), W = D - d after any update (rank D - d).
+  auto step = [&](auto ne_tag, int64_t n) {
+    constexpr int NE = decltype(ne_tag)::value;
+    if constexpr (!LOCAL_LIN) {
+      if (n + 1 <= n1) nxt.load(g, Yv, R, U, n + 1);
+    }
     T Ft[DD][DD], rr[DD], uf[RL];
     if constexpr (!LOCAL_LIN) {
-      step_inputs<C>(p, Yv, R, n, Ft, rr);
-      load_forcing<C>(g, U, n - 1, uf);
+      cur.jacobian(p, Ft);
+#pragma unroll
+      for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
+#pragma unroll
+      for (int l = 0; l < RL; ++l) uf[l] = cur.u[l];
     } else {
 #pragma unroll
       for (int l = 0; l < RL; ++l) uf[l] = T(0);
     }
-    publish<GR, D, LDM>(g, sP, scr + C::MAT0);
+    publish_cols<GR, NE, LDM>(g, sP, scr + C::MAT0);
     publish_vec(g, m, scr + C::VEC0);
     g.sync();
     // Pi input: top rows [sqrtQ | Phi sqrtP], bottom rows [0 | sqrtP]
-    T tri[2][RL][D], ext[2][RL][D], mp[RL];
-    phi_rows<C, D>(lc, scr + C::MAT0, ext[0]);
+    T tri[2][RL][D], ext[2][RL][NE], mp[RL];
+    phi_rows<C, NE>(lc, scr + C::MAT0, ext[0]);
     phi_vec<C>(lc, scr + C::VEC0, mp);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       mp[l] += uf[l];
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        tri[0][l][c] = lc.sqrow[l][c];
-        tri[1][l][c] = T(0);
-        ext[1][l][c] = sP[l][c];
+      for (int cc = 0; cc < D; ++cc) {
+        tri[0][l][cc] = lc.sqrow[l][cc];
+        tri[1][l][cc] = T(0);
       }
+#pragma unroll
+      for (int cc = 0; cc < NE; ++cc) ext[1][l][cc] = sP[l][cc];
     }
     g.sync();
-    lq_tri_ext<GR, 2, D>(g, tri, ext, scr + C::PIV);
+    lq_tri_ext<GR, 2, NE>(g, tri, ext, scr + C::PIV);
     // Pi11 = tri[0] (= predicted factor of step n), Pi21 = tri[1], remainder ext[1]
     publish<GR, D, LDM>(g, tri[0], scr + C::MAT0);
     publish_vec(g, mp, scr + C::VEC0);
     g.sync();
     // smoothing element n-1: E = Pi21 Pi11^-1, g = m^f - E m-
     T e[RL][D], gg[RL], lrow[RL][D];
+    T rinv[D];
+    inv_diag<D, LDM>(scr + C::MAT0, rinv);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
-      solve_xL<D, LDM>(scr + C::MAT0, tri[1][l], e[l]);
-      T acc = m[l];
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc -= e[l][c] * scr[C::VEC0 + c];
+      solve_xL<D, LDM>(scr + C::MAT0, rinv, tri[1][l], e[l]);
+      const T acc = m[l] - sum4<T, D>([&](int cc) { return e[l][cc] * scr[C::VEC0 + cc]; });
       gg[l] = g.valid(l) ? acc : T(0);
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        if (!g.valid(l)) e[l][c] = T(0);
-        lrow[l][c] = T(0);
+      for (int cc = 0; cc < D; ++cc) {
+        if (!g.valid(l)) e[l][cc] = T(0);
+        lrow[l][cc] = T(0);
       }
     }
     if constexpr (WITH_L) {
@@ -349,12 +421,12 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 #pragma unroll
       for (int l = 0; l < RL; ++l)
 #pragma unroll
-        for (int c = 0; c < D; ++c) Rm[0][l][c] = ext[1][l][c];
+        for (int cc = 0; cc < D; ++cc) Rm[0][l][cc] = (cc < NE) ? ext[1][l][cc < NE ? cc : 0] : T(0);
       lq_dense<GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
 #pragma unroll
       for (int l = 0; l < RL; ++l)
 #pragma unroll
-        for (int c = 0; c < D; ++c) lrow[l][c] = Rm[0][l][c];
+        for (int cc = 0; cc < D; ++cc) lrow[l][cc] = Rm[0][l][cc];
     }
     emit(n - 1, e, gg, lrow);
     if constexpr (LOCAL_LIN) {
@@ -375,7 +447,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       for (int kk = 0; kk < DD; ++kk) acc += u.K[l][kk] * u.nu[kk];
       m[l] = acc;
 #pragma unroll
-      for (int c = 0; c < D; ++c) sP[l][c] = (c < W) ? sPn[l][c] : T(0);
+      for (int cc = 0; cc < D; ++cc) sP[l][cc] = (cc < W) ? sPn[l][cc < W ? cc : 0] : T(0);
     }
     if (g.gl == 0) {
       T z[DD];
@@ -385,7 +457,14 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       for (int kk = 0; kk < DD; ++kk) s += static_cast<double>(z[kk]) * static_cast<double>(z[kk]);
       s2acc += s;
     }
+    if constexpr (!LOCAL_LIN) cur = nxt;
+  };
+  int64_t n = n0;
+  if (chain != 0 && n <= n1) {
+    step(std::integral_constant<int, D>{}, n);
+    ++n;
   }
+  for (; n <= n1; ++n) step(std::integral_constant<int, W>{}, n);
   // the chain owning n = N emits b_N = (E = 0, g = m^f_N, sqrtL = tria(sqrtP^f_N))
   if (chain == p.N / p.L) {
     T e[RL][D], lrow[RL][D];
@@ -480,7 +559,25 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       (WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD)) : 1.0);
   const int64_t s0 = chain * p.L;
   const int64_t s1 = min(chain * p.L + p.L - 1, p.N);
+  // E row, g entry and trajectory entry of step n for this lane's rows (prefetched one step
+  // ahead: the walk is a dependent chain, the loads are not)
+  auto load = [&](int64_t n, T (&E_)[RL][D], T (&g_)[RL], V (&l_)[RL]) {
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+      const T* Er = Es + n * D * D + rr[l] * D;
+#pragma unroll
+      for (int k = 0; k < D; ++k) E_[l][k] = Er[k];
+      g_[l] = gs[n * D + rr[l]];
+      l_[l] = lin ? lin[n * D + rr[l]] : v_from_zero<V>();
+    }
+  };
+  T Ec[RL][D], gc[RL];
+  V lc[RL];
+  if (s1 >= s0) load(s1, Ec, gc, lc);
   for (int64_t n = s1; n >= s0; --n) {
+    T En[RL][D], gn[RL];
+    V ln_[RL];
+    if (n - 1 >= s0) load(n - 1, En, gn, ln_);
     publish_vec(g, m, scr + C::VEC0);
     if constexpr (WITH_L) publish<GR, D, LDM>(g, sPs, scr + C::MAT0);
     g.sync();
@@ -488,18 +585,13 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     T tri[1][RL][D], ext[1][RL][D];
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
-      const T* Er = Es + n * D * D + rr[l] * D;
-      T acc = gs[n * D + rr[l]];
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc += Er[k] * scr[C::VEC0 + k];
+      const T acc = gc[l] + sum4<T, D>([&](int k) { return Ec[l][k] * scr[C::VEC0 + k]; });
       mn[l] = vv[l] ? acc : T(0);
       if constexpr (WITH_L) {
         const T* Lr = Ls + n * D * D + rr[l] * D;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          T a2 = T(0);
-#pragma unroll
-          for (int k = 0; k < D; ++k) a2 += Er[k] * scr[C::MAT0 + k * LDM + c];
+          const T a2 = sum4<T, D>([&](int k) { return Ec[l][k] * scr[C::MAT0 + k * LDM + c]; });
           ext[0][l][c] = vv[l] ? a2 : T(0);
           tri[0][l][c] = vv[l] ? Lr[c] : T(0);
         }
@@ -518,21 +610,27 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       m[l] = mn[l];
       if (!vv[l]) continue;
       const int r = rr[l];
-      const V lv = lin ? lin[n * D + r] : v_from_zero<V>();
-      const V ln = v_add_small(lv, mn[l]);
+      const V lnew = v_add_small(lc[l], mn[l]);
       if constexpr (WITH_L) {
-        mean_out[n * D + r] = Trow[l] * v_to_T<T>(ln);
+        mean_out[n * D + r] = Trow[l] * v_to_T<T>(lnew);
 #pragma unroll
         for (int c = 0; c < D; ++c) cov_out[n * D * D + r * D + c] = sigma * Trow[l] * sPs[l][c];
       } else {
-        lin_new[n * D + r] = ln;
+        lin_new[n * D + r] = lnew;
         if (r % C::Q1 == 0) {
           const T dd = fabs(p.T0 * mn[l]);
           bad = bad || !(dd == dd);
           dmax = fmax(dmax, dd);
-          ymax = fmax(ymax, fabs(p.T0 * v_to_T<T>(ln)));
+          ymax = fmax(ymax, fabs(p.T0 * v_to_T<T>(lnew)));
         }
       }
+    }
+#pragma unroll
+    for (int l = 0; l < RL; ++l) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) Ec[l][k] = En[l][k];
+      gc[l] = gn[l];
+      lc[l] = ln_[l];
     }
   }
   if constexpr (!WITH_L) {

@@ -84,6 +84,18 @@ __device__ __forceinline__ void publish(const GR& g, const T (&x)[GR::RL][NC], T
   }
 }
 
+// Publish the first NC columns of RL rows stored with NX >= NC columns.
+template <class GR, int NC, int LD, int NX, typename T>
+__device__ __forceinline__ void publish_cols(const GR& g, const T (&x)[GR::RL][NX], T* buf) {
+  static_assert(NC <= NX, "too many columns");
+#pragma unroll
+  for (int l = 0; l < GR::RL; ++l) {
+    const int r = g.row(l);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) buf[r * LD + c] = x[l][c];
+  }
+}
+
 template <class GR, typename T>
 __device__ __forceinline__ void publish_vec(const GR& g, const T (&x)[GR::RL], T* buf) {
 #pragma unroll
@@ -255,29 +267,35 @@ __device__ __forceinline__ void lq_dense(const GR& g, T (&rows)[NS][GR::RL][NC],
 }
 
 // ---- small helpers -------------------------------------------------------------------------
+// Reciprocals of the diagonal of a D x D matrix in scratch (ld LD); computed once so that the
+// substitutions below run on multiply-adds only.
+template <int D, int LD, typename T>
+__device__ __forceinline__ void inv_diag(const T* Lm, T (&rinv)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) rinv[c] = T(1) / Lm[c * LD + c];
+}
+
 // Solve x * L^T = y for x (row vector), L lower-triangular D x D in scratch (ld LD):
 //   x[c] = (y[c] - sum_{k<c} x[k] L[c][k]) / L[c][c]     (forward substitution)
 template <int D, int LD, typename T>
-__device__ __forceinline__ void solve_xLt(const T* Lm, const T (&y)[D], T (&x)[D]) {
+__device__ __forceinline__ void solve_xLt(const T* Lm, const T (&rinv)[D], const T (&y)[D],
+                                          T (&x)[D]) {
 #pragma unroll
   for (int c = 0; c < D; ++c) {
-    T acc = y[c];
-#pragma unroll
-    for (int k = 0; k < c; ++k) acc -= x[k] * Lm[c * LD + k];
-    x[c] = acc / Lm[c * LD + c];
+    const T acc = y[c] - sum4<T, D>([&](int k) { return (k < c) ? x[k] * Lm[c * LD + k] : T(0); });
+    x[c] = acc * rinv[c];
   }
 }
 
 // Solve x * L = y for x (row vector), L lower-triangular:
 //   x[c] = (y[c] - sum_{k>c} x[k] L[k][c]) / L[c][c]      (backward substitution)
 template <int D, int LD, typename T>
-__device__ __forceinline__ void solve_xL(const T* Lm, const T (&y)[D], T (&x)[D]) {
+__device__ __forceinline__ void solve_xL(const T* Lm, const T (&rinv)[D], const T (&y)[D],
+                                         T (&x)[D]) {
 #pragma unroll
   for (int c = D - 1; c >= 0; --c) {
-    T acc = y[c];
-#pragma unroll
-    for (int k = c + 1; k < D; ++k) acc -= x[k] * Lm[k * LD + c];
-    x[c] = acc / Lm[c * LD + c];
+    const T acc = y[c] - sum4<T, D>([&](int k) { return (k > c) ? x[k] * Lm[k * LD + c] : T(0); });
+    x[c] = acc * rinv[c];
   }
 }
 

@@ -101,7 +101,8 @@ struct Cfg {
   static constexpr int VEC3 = VEC2 + RP;
   static constexpr int SV = VEC3 + RP;
   static constexpr int PIV = SV + RoundUp<(DD_ * DD_ > 1 ? DD_ * DD_ : 1), 2>::value;
-  static constexpr int SCR = RoundUp<PIV + 2 * (2 * D + 1), 4>::value;
+  static constexpr int SCR =
+      RoundUp<PIV + 2 * ((2 * D > 4 * DD_ ? 2 * D : 4 * DD_) + 1), 4>::value;
   // item sizes
   static constexpr int FA = 3 * D * D + 2 * D;   // filter element (A, b, C, eta, J)
   static constexpr int SA = 2 * D * D + D;       // smoothing element (E, g, L)
@@ -333,46 +334,58 @@ __device__ void combine_f(const typename C::GR& g, const typename C::Tp* al,
   int rr[RL];
 #pragma unroll
   for (int l = 0; l < RL; ++l) rr[l] = g.valid(l) ? g.row(l) : 0;
-  // 1. Xi input: top rows [Ci^T Jj | I], bottom rows [Jj | 0]; 2D columns.
-  T X[2][RL][2 * D];
+  // 1. Xi = tria([[Ci^T Jj, I], [Jj, 0]]).  tria is invariant under a permutation of the
+  // columns, so the rows are taken as top [I | Ci^T Jj], bottom [0 | Jj]: a lower-triangular
+  // block plus a dense block, which the structured LQ reduces with D reflections.  Afterwards
+  // top = [Xi11 | 0], bottom = [Xi21 | R] with Xi22 = tria(R).
+  T tri[2][RL][D], ext[2][RL][D];
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     const int r = rr[l];
     const bool v = g.valid(l);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k < D; ++k) acc += Ci[k * D + r] * Jj[k * D + c];
-      X[0][l][c] = v ? acc : T(0);
-      X[0][l][D + c] = (v && c == r) ? T(1) : T(0);
-      X[1][l][c] = v ? Jj[r * D + c] : T(0);
-      X[1][l][D + c] = T(0);
+      const T w = sum4<T, D>([&](int kk) { return Ci[kk * D + r] * Jj[kk * D + c]; });
+      tri[0][l][c] = (v && c == r) ? T(1) : T(0);
+      ext[0][l][c] = v ? w : T(0);
+      tri[1][l][c] = T(0);
+      ext[1][l][c] = v ? Jj[r * D + c] : T(0);
     }
   }
-  lq_dense<typename C::GR, 2, 2 * D, 0, D, 0>(g, X, scr + C::PIV);
-  lq_dense<typename C::GR, 2, 2 * D, 1, D, D>(g, X, scr + C::PIV);
-  // Xi11 = X[0][.][0..D-1], Xi21 = X[1][.][0..D-1], Xi22 = X[1][.][D..2D-1]
+  lq_tri_ext<typename C::GR, 2, D>(g, tri, ext, scr + C::PIV);
   T X11r[RL][D], X21r[RL][D], X22r[RL][D];
 #pragma unroll
   for (int l = 0; l < RL; ++l)
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      X11r[l][c] = X[0][l][c];
-      X21r[l][c] = X[1][l][c];
-      X22r[l][c] = X[1][l][D + c];
+      X11r[l][c] = tri[0][l][c];
+      X21r[l][c] = tri[1][l][c];
     }
+  if constexpr (!VALUES_ONLY) {
+    T Rm[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) Rm[0][l][c] = ext[1][l][c];
+    lq_dense<typename C::GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) X22r[l][c] = Rm[0][l][c];
+  }
   publish<typename C::GR, D, LDM>(g, X11r, scr + C::MAT0);
   publish<typename C::GR, D, LDM>(g, X21r, scr + C::MAT1);
   g.sync();
   // 2. M = Ci Xi11^-T (row r: solve M_r Xi11^T = Ci_r); Y = I - M Xi21^T
   T Mr[RL][D], Yr[RL][D];
+  T rinv[D];
+  inv_diag<D, LDM>(scr + C::MAT0, rinv);
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     T y[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) y[c] = Ci[rr[l] * D + c];
-    solve_xLt<D, LDM>(scr + C::MAT0, y, Mr[l]);
+    solve_xLt<D, LDM>(scr + C::MAT0, rinv, y, Mr[l]);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       T acc = T(0);
