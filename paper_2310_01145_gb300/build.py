@@ -22,6 +22,8 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
+# extra nvcc flags (space-separated), e.g. "-Xptxas -v" to print register use
+FLAGS += os.environ.get("PIT_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
