@@ -49,6 +49,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
+    ap.add_argument("--workload", choices=("fhn", "lv_batch"), default="fhn",
+                    help="fhn: the single-problem FitzHugh-Nagumo solve (default); lv_batch: "
+                         "4096 Lotka-Volterra instances in one batched solve")
+    ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--no-eks", action="store_true", help="skip the sequential-EKS comparison")
     return ap.parse_args(argv)
 
 
@@ -294,6 +299,26 @@ def run_pit(args):
     kernel_shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                          "share": v[0] / total_ms} for k, v in shares.items()}
 
+    # ---- the sequential-in-time EKS on the same GPU (Sections 2.3 and 4.3), one solve ----
+    eks = None
+    if rank == 0 and not args.no_eks:
+        eopts = pit.make_opts(dtype=tdt, want_cov=True)
+        pit.pit_eks_sequential(ode, prob.y0, prob.t0, prob.t1, min(prob.N, 4096), prob.q, eopts)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pit.pit_eks_sequential(ode, prob.y0, prob.t0, prob.t1, prob.N, prob.q, eopts,
+                               out=(mean, cov), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eks_ms = e0.elapsed_time(e1)
+        eks = {"value": prob.N / (eks_ms / 1e3), "unit": "steps/s", "ms_per_solve": eks_ms,
+               "what": "sequential EKS (local linearisation, one forward and one backward pass "
+                       "strictly in time order) on the same GPU, same grid and dtype",
+               "parallel_ms_per_solve": ms_local / args.steps,
+               "speedup_time_to_solution": eks_ms / (ms_local / args.steps)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -325,6 +350,118 @@ def run_pit(args):
         "kernel_shares": kernel_shares,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "sequential_eks_gpu": eks,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---- batched Lotka-Volterra (segmented scans over 4096 instances) ------------------------------
+def run_lv_batch(args):
+    import numpy as np
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+    import workloads as W
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    probs = W.lotka_volterra_batch(count=args.instances, seed=rank)
+    Ns = np.array([p.N for p in probs])
+    opts = pit.make_opts(dtype=torch.float32, max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
+                         want_cov=False, calibrate=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return pit.solve_problems_batched(probs, opts=opts, stream=stream,
+                                          allow_diverged=True)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+    pit.pit_profile_reset()
+    pit.pit_profile_enable(True)
+    launches0 = pit.pit_launch_count()
+    work = 0.0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            work += float(np.sum(Ns * r.iterations))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = pit.pit_launch_count() - launches0
+    pit.pit_profile_enable(False)
+    prof = pit.pit_profile_read()
+    ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    value = reduce_sum(work, world, dev) / (ms / 1e3)
+    clocks = clk.summary()
+    # end to end: means copied back to pinned host memory every step
+    host = torch.empty(r.mean.shape, dtype=torch.float32, pin_memory=True)
+    t0 = time.perf_counter()
+    work_e2e = 0.0
+    for _ in range(args.steps):
+        r = step()
+        host.copy_(r.mean, non_blocking=True)
+        torch.cuda.synchronize()
+        work_e2e += float(np.sum(Ns * r.iterations))
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = reduce_sum(work_e2e, world, dev) / t_e2e
+    # the same instances one at a time through the single-problem FP64 solver (first 32)
+    single = None
+    if rank == 0:
+        sub = probs[:32]
+        o64 = pit.make_opts(dtype=torch.float64, max_iter=20, atol_delta=1e-10, want_cov=False)
+        for p in sub[:2]:
+            pit.solve_problem(p, opts=o64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        w = 0
+        for p in sub:
+            rr = pit.solve_problem(p, opts=o64)
+            w += p.N * rr.iterations
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        single = {"value": w / el, "unit": UNIT, "what": "single-instance FP64 parallel solves, "
+                  "one after another, of the first 32 instances (same stop rule in FP64: "
+                  "max|dy| <= 1e-10 or 20 iterations)"}
+    shares = {k: v for k, v in prof.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in shares.values())
+    out = {
+        "metric": "IEKS steps*iterations/s, batched Lotka-Volterra (FP32, IWP(2))", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched Lotka-Volterra: {args.instances} instances, (al,be,ga,de)"
+                               f"=(1.5,1,3,1)*U[0.8,1.2], y0~U[0.5,2]^2, t in [0,10], N "
+                               f"log-uniform in [256,16384] (sum N = {int(Ns.sum())}), IWP(2), "
+                               f"one batched solve per step, stop per instance at max|dy|<="
+                               f"1e-10+1e-6 max|y| or 20 iterations, means + sigma^2",
+                   "iterations_mean": float(np.mean(r.iterations)),
+                   "converged_fraction": float(np.mean(r.converged)),
+                   "diverged": int(np.sum(r.status == 6)),
+                   "diverged_examples": [int(i) for i in np.nonzero(r.status == 6)[0][:8]],
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(args.instances * 8 * 9),
+                "d2h_bytes_per_step": int(host.numel() * 4)},
+        "gpu_launches": launches,
+        "kernel_shares": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                              "share": v[0] / total_ms} for k, v in shares.items()},
+        "clocks": clocks,
+        "single_instance_f64": single,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -373,6 +510,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "lv_batch":
+        run_lv_batch(args)
     else:
         run_pit(args)
 

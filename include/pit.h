@@ -257,6 +257,54 @@ int32_t pit_eks_sequential(const pit_ode* ode, const pit_grid* grid, int32_t q,
                            pit_solve_info* info, void* workspace, size_t ws_bytes,
                            void* stream);
 
+/* ---- batched (segmented) solves ------------------------------------------------------- */
+
+/* Per-instance report of a batched solve (host memory). */
+typedef struct {
+  int32_t iterations;   /* IEKS iterations this instance took part in                      */
+  int32_t converged;    /* 1 if its stopping rule was met (or fixed_iters was requested)    */
+  int32_t status;       /* PIT_OK, PIT_ENOCONV, or PIT_ENONFINITE (diverged, see below)     */
+  int32_t pad;
+  double last_delta;    /* max |change of E0 mean| of its last iteration                    */
+  double sigma2;        /* its quasi-MLE diffusion sigma^2 (1 when calibrate == 0)          */
+} pit_batch_info;
+
+/* ParaIEKS (Algorithm 2) on B independent initial value problems of one ODE family, dimension
+ * d and prior order q, each with its own parameters, initial value and uniform grid (any N).
+ * No counterpart in the paper, which solves one problem at a time: the instances are laid end
+ * to end on one time axis and solved by the same associative scans (Algorithm 1) in the same
+ * kernel launches.  Each instance's first point enters the filtering scan as an element with
+ * A = 0, sqrtC = 0, eta = 0, sqrtJ = 0 and its last point the smoothing scan as an element with
+ * E = 0 (the boundary elements of Section 3.1.3, Eqs. filtering-elements and
+ * smoothing-elements), so no value of one instance depends on another's and every instance gets
+ * the result a single solve would give, up to the rounding of a different chain partition.
+ * Each instance stops on its own rule (as pit_solve) and then leaves the active set; later
+ * iterations run on the remaining instances only.
+ *   B                  number of instances (>= 1)
+ *   odes               host, B entries; all of the same kind and d (parameters may differ)
+ *   grids              host, B entries (t0 < t1, N >= 1 each)
+ *   q                  prior order, shared
+ *   y0                 host, B x d initial values
+ *   opts               host, NULL = defaults (as pit_solve; init_traj is not supported)
+ *   mean               device, sum_i (N_i + 1) rows of D values, `dtype`: instance i's
+ *                      smoothing means start at row sum_{j<i} (N_j + 1); original coordinates
+ *   sqrtcov            device, the same rows of D x D values, or NULL when want_cov = 0
+ *   info               host, B entries, may be NULL
+ *   workspace          device, >= pit_solve_batched_workspace_size bytes, 256-byte aligned
+ * The call synchronises `stream` once per iteration (to read the per-instance change
+ * statistics) and returns when the outputs are complete.  An instance whose change exceeds
+ * 1e12 or turns non-finite is stopped with status PIT_ENONFINITE (its outputs hold its last
+ * finite iterate); an overflow inside a pass can make the values of instances that share a
+ * chain or tree node with it non-finite in that pass, which are then reported the same way.
+ * Returns PIT_ENONFINITE if any instance diverged, else PIT_ENOCONV if any instance hit
+ * max_iter, else PIT_OK; PIT_EINVAL (arguments, mixed kinds), PIT_EUNSUPPORTED, PIT_ENOMEM,
+ * PIT_ECUDA as pit_solve. */
+int32_t pit_solve_batched_workspace_size(int32_t B, const pit_ode* odes, const pit_grid* grids,
+                                         int32_t q, const pit_opts* opts, size_t* bytes);
+int32_t pit_solve_batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q,
+                          const double* y0, const pit_opts* opts, void* mean, void* sqrtcov,
+                          pit_batch_info* info, void* workspace, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,12 @@ class _Info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("deltas", ctypes.c_double * 64)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double)]
+
+
 _lib = None
 
 # exported symbols and their signatures (declared in include/pit.h)
@@ -85,6 +91,12 @@ SIGNATURES = {
     "pit_eks_sequential": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                                   ctypes.POINTER(_Opts), _P, _P, ctypes.POINTER(_Info), _P, _SZ,
                                   _P]),
+    "pit_solve_batched_workspace_size": (_I32, [_I32, ctypes.POINTER(_Ode),
+                                                ctypes.POINTER(_Grid), _I32,
+                                                ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
+    "pit_solve_batched": (_I32, [_I32, ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
+                                 ctypes.POINTER(_Opts), _P, _P, ctypes.POINTER(_BatchInfo), _P,
+                                 _SZ, _P]),
 }
 
 
@@ -344,3 +356,75 @@ def solve_problem(problem, **kw) -> SolveResult:
                                                          "want_cov", "chain_len")})
     return pit_solve(ode_from_problem(problem), problem.y0, problem.t0, problem.t1, problem.N,
                      problem.q, opts, **kw)
+
+
+@dataclasses.dataclass
+class BatchResult:
+    mean: "object"          # torch tensor (sum_i (N_i + 1), D)
+    sqrtcov: "object"       # torch tensor (sum_i (N_i + 1), D, D) or None
+    rows: np.ndarray        # first row of each instance
+    iterations: np.ndarray
+    converged: np.ndarray
+    status: np.ndarray      # per-instance pit_status
+    last_delta: np.ndarray
+    sigma2: np.ndarray
+    call_status: int
+
+    def instance(self, i: int):
+        """(mean, sqrtcov) views of instance i."""
+        a, b = int(self.rows[i]), int(self.rows[i + 1])
+        return self.mean[a:b], (self.sqrtcov[a:b] if self.sqrtcov is not None else None)
+
+
+def pit_solve_batched(odes: Sequence[Ode], y0s, grids: Sequence[tuple], q: int,
+                      opts: Optional[_Opts] = None, device=None, stream=None, workspace=None,
+                      allow_noconv=True, allow_diverged=False) -> BatchResult:
+    """Batched ParaIEKS over instances of one ODE family (see pit_solve_batched in pit.h).
+    grids: (t0, t1, N) per instance; y0s: (B, d)."""
+    import torch
+    lib = load()
+    opts = opts or make_opts()
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    B = len(odes)
+    cs = (_Ode * B)(*[o.c() for o in odes])
+    keep = [o._p for o in odes]  # parameter arrays referenced by cs
+    gs = (_Grid * B)(*[_Grid(float(t0), float(t1), int(N)) for (t0, t1, N) in grids])
+    sz = ctypes.c_size_t(0)
+    _check(lib.pit_solve_batched_workspace_size(B, cs, gs, int(q), ctypes.byref(opts),
+                                                ctypes.byref(sz)), "batched workspace_size")
+    if workspace is None or workspace.numel() < sz.value:
+        workspace = _workspace(sz.value, device)
+    d = odes[0].d
+    D = d * (q + 1)
+    Ns = np.array([int(g[2]) for g in grids], dtype=np.int64)
+    rows = np.concatenate([[0], np.cumsum(Ns + 1)])
+    M = int(rows[-1])
+    tdt = _torch_dtype(opts.dtype)
+    mean = torch.empty((M, D), dtype=tdt, device=device)
+    cov = torch.empty((M, D, D), dtype=tdt, device=device) if opts.want_cov else None
+    y = np.ascontiguousarray(np.asarray(y0s, dtype=np.float64).reshape(B, d))
+    info = (_BatchInfo * B)()
+    st = lib.pit_solve_batched(B, cs, gs, int(q), _dptr(y), ctypes.byref(opts), _tptr(mean),
+                               _tptr(cov), info, _tptr(workspace), workspace.numel(),
+                               _stream_ptr(stream))
+    del keep
+    if not (st == 0 or (st == 4 and allow_noconv) or (st == 6 and allow_diverged)):
+        _check(st, "pit_solve_batched")
+    return BatchResult(mean, cov, rows,
+                       np.array([info[i].iterations for i in range(B)]),
+                       np.array([bool(info[i].converged) for i in range(B)]),
+                       np.array([info[i].status for i in range(B)]),
+                       np.array([info[i].last_delta for i in range(B)]),
+                       np.array([info[i].sigma2 for i in range(B)]), int(st))
+
+
+def solve_problems_batched(problems, **kw) -> BatchResult:
+    """Batched solve of workloads.Problem instances (same family, d and q)."""
+    opts = kw.pop("opts", None) or make_opts(**{k: kw.pop(k) for k in list(kw)
+                                                if k in ("dtype", "max_iter", "fixed_iters",
+                                                         "atol_delta", "rtol_delta", "calibrate",
+                                                         "want_cov", "chain_len")})
+    q = problems[0].q
+    return pit_solve_batched([ode_from_problem(p) for p in problems],
+                             np.stack([np.asarray(p.y0, dtype=np.float64) for p in problems]),
+                             [(p.t0, p.t1, p.N) for p in problems], q, opts, **kw)

@@ -304,8 +304,7 @@ static int expected_d(int kind, int d) {
   }
 }
 
-static int fill_problem(const pit_ode* ode, int q, const double* y0, Problem& pb,
-                        bool need_y0 = true) {
+int fill_problem(const pit_ode* ode, int q, const double* y0, Problem& pb, bool need_y0) {
   if (!ode) {
     set_error("ode is NULL");
     return PIT_EINVAL;
@@ -351,7 +350,7 @@ static int fill_problem(const pit_ode* ode, int q, const double* y0, Problem& pb
   return PIT_OK;
 }
 
-static int fill_grid(const pit_grid* grid, Problem& pb) {
+int fill_grid(const pit_grid* grid, Problem& pb) {
   if (!grid) {
     set_error("grid is NULL");
     return PIT_EINVAL;
@@ -370,7 +369,7 @@ static int fill_grid(const pit_grid* grid, Problem& pb) {
   return PIT_OK;
 }
 
-static int check_opts(const pit_opts* in, pit_opts& o) {
+int check_opts(const pit_opts* in, pit_opts& o) {
   pit_opts_default(&o);
   if (in) o = *in;
   if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||

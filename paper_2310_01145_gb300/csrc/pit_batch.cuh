@@ -1,0 +1,385 @@
+// Segmented (batched) IEKS: many instances of one ODE family, of any lengths, solved by the same
+// scans over one global time axis (Section 3.1's operators, unchanged).  Instance i occupies
+// global points off_i .. off_i + N_i; its n = 0 point enters the filter scan as a reset element
+// (A = 0, b = delta_0, C = 0, eta = 0, J = 0) and its n = N point leaves the smoothing scan as an
+// element with E = 0, so every prefix value (filtering means and factors) and every smoothing
+// value of an instance depends on that instance's data only.  Included by the pit_batch_*.cu
+// instantiation files.
+#pragma once
+
+#include <cstddef>
+#include <vector>
+
+#include "pit_solve_impl.cuh"
+
+namespace pit {
+
+static_assert(sizeof(InstAcc) == sizeof(SegResult), "InstAcc and SegResult must match");
+static_assert(offsetof(InstAcc, delta_max) == offsetof(SegResult, delta_max), "layout");
+static_assert(offsetof(InstAcc, flags) == offsetof(SegResult, flags), "layout");
+
+// Layout of one pass: per slot, the instance's offset and current trajectory; per global point,
+// the instance code (id, or ~id at n = 0).
+template <typename T>
+__global__ void k_seg_layout(const SegSlot* __restrict__ slots, InstDesc<T>* __restrict__ desc,
+                             int* __restrict__ inst_of) {
+  const SegSlot sl = slots[blockIdx.x];
+  InstDesc<T>& d = desc[sl.id];
+  if (threadIdx.x == 0) {
+    d.off = sl.off;
+    d.cur = sl.cur;
+  }
+  const int64_t npts = d.N + 1;
+  for (int64_t n = threadIdx.x; n < npts; n += blockDim.x)
+    inst_of[sl.off + n] = (n == 0) ? ~sl.id : sl.id;
+}
+
+// lin[cur] <- mu0 (preconditioned) at every point, for every slot (blockIdx.y).
+template <class C>
+__global__ void k_seg_init(const SegSlot* __restrict__ slots,
+                           const InstDesc<typename C::Tp>* __restrict__ desc) {
+  using V = typename TrajType<typename C::Tp>::type;
+  const SegSlot sl = slots[blockIdx.y];
+  const InstDesc<typename C::Tp>& d = desc[sl.id];
+  V* lin = static_cast<V*>(d.lin[sl.cur]);
+  const int64_t total = (d.N + 1) * C::D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x)
+    lin[i] = v_from_double<V>(d.mu0d[i % C::D]);
+}
+
+// mean <- T lin[1 - cur] (original coordinates), for every slot (blockIdx.y).
+template <class C>
+__global__ void k_seg_export(const SegSlot* __restrict__ slots,
+                             const InstDesc<typename C::Tp>* __restrict__ desc) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  const SegSlot sl = slots[blockIdx.y];
+  const InstDesc<T>& d = desc[sl.id];
+  const V* lin = static_cast<const V*>(d.lin[1 - sl.cur]);
+  const int64_t total = (d.N + 1) * C::D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = static_cast<int>(i % C::D);
+    d.mean[i] = d.Tdiag[r % C::Q1] * v_to_T<T>(lin[i]);
+  }
+}
+
+// Inputs of the increment model (as k_residuals) for every global point of the layout, with the
+// instance's own constants: u_n = Phibar lin_n - lin_{n+1} (n < N_i; 0 at n = N_i), r_n, y_n, and
+// delta_0 = mu0 - lin_0 of instance i at d0[i D ..].
+template <class C>
+__global__ void __launch_bounds__(256)
+k_seg_residuals(const IeksParams<typename C::Tp> p, typename C::Tp* __restrict__ U,
+                typename C::Tp* __restrict__ R, typename C::Tp* __restrict__ Yv,
+                typename C::Tp* __restrict__ d0) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp <= p.N;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    const int id = seg_id(p.seg.inst_of[gp]);
+    const InstDesc<T>& d = p.seg.desc[id];
+    const int64_t n = gp - d.off;
+    const V* lin = static_cast<const V*>(d.lin[d.cur]);
+    V x[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[r] = lin[n * D + r];
+    if (n < d.N) {
+#pragma unroll
+      for (int k = 0; k < DD; ++k) {
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+          V acc = x[k * Q1 + i];
+#pragma unroll
+          for (int j = i + 1; j < Q1; ++j)
+            acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+          acc = acc - lin[(n + 1) * D + k * Q1 + i];
+          U[gp * D + k * Q1 + i] = v_to_T<T>(acc);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < D; ++r) U[gp * D + r] = T(0);
+    }
+    OdeConstsV<V> oc;
+    ode_consts_v<V, T, DD>(p.ode, d.pd, oc);
+    const V T0v = v_from_double<V>(d.T0d);
+    const V T1iv = v_from_double<V>(d.T1invd);
+    V y[DD], f[DD];
+#pragma unroll
+    for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
+    ode_f_v<V, DD>(oc, y, f);
+#pragma unroll
+    for (int k = 0; k < DD; ++k) {
+      Yv[gp * DD + k] = v_to_T<T>(y[k]);
+      R[gp * DD + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
+    }
+    if (n == 0) {
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+        d0[static_cast<int64_t>(id) * D + r] = v_to_T<T>(v_from_double<V>(d.mu0d[r]) - x[r]);
+    }
+  }
+}
+
+template <typename T, int DD, int Q1, int G, int RL>
+class SegEngineImpl final : public SegEngine {
+ public:
+  using C = Cfg<T, DD, Q1, G, RL>;
+  using V = typename TrajType<T>::type;
+  using Base = SolverImpl<T, DD, Q1, G, RL>;
+  static constexpr int D = C::D;
+  static constexpr int NG = kThreads / G;
+
+  int state_dim() const override { return D; }
+  size_t traj_bytes(int64_t N) const override {
+    return static_cast<size_t>(N + 1) * D * sizeof(V);
+  }
+
+  static int64_t max_chains(int64_t max_points, int chain_len) {
+    if (chain_len > 0) return (max_points - 1) / chain_len + 1;
+    // default chain length (SolverImpl::default_chain_len) gives at most target + 1 chains, or
+    // max_points / 512 + 1 when the length is clamped at 512
+    const int64_t target = 152LL * 8 * NG;
+    return std::max<int64_t>(target + 2, max_points / 512 + 2);
+  }
+
+  struct Bufs {
+    T *U, *R, *Yv, *d0, *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
+    SolveScalars* scal;
+    InstDesc<T>* desc;
+    InstAcc* acc;
+    int* inst_of;
+    SegSlot* slots;
+  };
+
+  size_t carve(void* ws, size_t bytes, int64_t max_points, int max_inst, bool want_cov,
+               int chain_len, Bufs& b) const {
+    Carver cv(ws, bytes);
+    const int64_t M = max_points;
+    const int64_t P = max_chains(max_points, chain_len);
+    b.U = cv.take<T>(M * D);
+    b.R = cv.take<T>(M * DD);
+    b.Yv = cv.take<T>(M * DD);
+    b.d0 = cv.take<T>(static_cast<int64_t>(max_inst) * D);
+    b.Es = cv.take<T>(M * D * D);
+    b.gs = cv.take<T>(M * D);
+    b.Ls = want_cov ? cv.take<T>(M * D * D) : nullptr;
+    b.fagg = cv.take<T>(P * C::FA);
+    b.fup = cv.take<T>(Tree<C, true, false, false, true>::upper_bytes(P) / sizeof(T) + 1);
+    b.sagg = cv.take<T>(P * C::SA);
+    const size_t sup_bytes = std::max(Tree<C, false, false, true>::upper_bytes(P),
+                                      Tree<C, false, true, true>::upper_bytes(P));
+    b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
+    b.scal = cv.take<SolveScalars>(1);
+    b.desc = cv.take<InstDesc<T>>(max_inst);
+    b.acc = cv.take<InstAcc>(max_inst);
+    b.inst_of = cv.take<int>(M);
+    b.slots = cv.take<SegSlot>(max_inst);
+    return cv.used();
+  }
+
+  size_t workspace_bytes(int64_t max_points, int max_inst, bool want_cov,
+                         int chain_len) const override {
+    Bufs b;
+    return carve(nullptr, 0, max_points, max_inst, want_cov, chain_len, b);
+  }
+
+  int bind(void* ws, size_t bytes, int64_t max_points, int max_inst, bool want_cov,
+           int chain_len) override {
+    const size_t need = carve(ws, bytes, max_points, max_inst, want_cov, chain_len, b_);
+    if (bytes < need || !ws) {
+      set_error("segmented workspace too small: need " + std::to_string(need) + " bytes");
+      return PIT_ENOMEM;
+    }
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+      set_error("workspace must be 256-byte aligned");
+      return PIT_EINVAL;
+    }
+    max_points_ = max_points;
+    max_inst_ = max_inst;
+    want_cov_ = want_cov;
+    chain_len_ = chain_len;
+    h_desc_.assign(max_inst, InstDesc<T>{});
+    h_acc_.assign(max_inst, InstAcc{});
+    kind_ = -1;
+    return Base::set_smem_attrs_seg();
+  }
+
+  int set_instance(int id, const Problem& pb, void* lin0, void* lin1, void* mean, void* cov,
+                   cudaStream_t s) override {
+    if (id < 0 || id >= max_inst_) {
+      set_error("instance id out of range");
+      return PIT_EINVAL;
+    }
+    if (kind_ < 0) {
+      // constants shared by all instances: family, Phibar, sqrt(Qbar) (step-size free)
+      SolveArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.pb = pb;
+      pit_opts_default(&a.opts);
+      int st = Base::fill_params(a, shared_, 0);
+      if (st != PIT_OK) return st;
+      kind_ = pb.kind;
+    } else if (pb.kind != kind_) {
+      set_error("all instances of a segmented solve must share the ODE family");
+      return PIT_EINVAL;
+    }
+    if (pb.n_params > kMaxInstParams) {
+      set_error("too many ODE parameters for a segmented solve");
+      return PIT_EINVAL;
+    }
+    SolveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pb = pb;
+    pit_opts_default(&a.opts);
+    IeksParams<T> pi;
+    int st = Base::fill_params(a, pi, 0);
+    if (st != PIT_OK) return st;
+    InstDesc<T>& d = h_desc_[id];
+    std::memset(&d, 0, sizeof(d));
+    d.off = 0;
+    d.N = pb.N;
+    d.lin[0] = lin0;
+    d.lin[1] = lin1;
+    d.cur = 0;
+    d.mean = static_cast<T*>(mean);
+    d.cov = static_cast<T*>(cov);
+    for (int j = 0; j < pb.n_params; ++j) {
+      d.pd[j] = pb.params[j];
+      d.p[j] = static_cast<T>(pb.params[j]);
+    }
+    for (int r = 0; r < D; ++r) d.mu0d[r] = pi.mu0d[r];
+    d.T0d = pi.T0d;
+    d.T1invd = pi.T1invd;
+    for (int i = 0; i < Q1; ++i) {
+      d.Tdiagd[i] = pi.Tdiagd[i];
+      d.Tdiag[i] = pi.Tdiag[i];
+    }
+    d.T0 = pi.T0;
+    d.T1inv = pi.T1inv;
+    d.hq = pi.hq;
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.desc + id, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    return PIT_OK;
+  }
+
+  int upload_slots(const SegSlot* slots, int n, cudaStream_t s) {
+    if (n < 1 || n > max_inst_) {
+      set_error("slot count out of range");
+      return PIT_EINVAL;
+    }
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.slots, slots, sizeof(SegSlot) * n, cudaMemcpyHostToDevice, s));
+    return PIT_OK;
+  }
+
+  static unsigned per_slot_grid(const SegSlot* slots, int n, const std::vector<InstDesc<T>>& hd) {
+    int64_t mx = 1;
+    for (int i = 0; i < n; ++i) mx = std::max<int64_t>(mx, (hd[slots[i].id].N + 1) * D);
+    return static_cast<unsigned>(std::min<int64_t>((mx + 255) / 256, 64));
+  }
+
+  int init_traj(const SegSlot* slots, int n, cudaStream_t s) override {
+    int st = upload_slots(slots, n, s);
+    if (st != PIT_OK) return st;
+    dim3 grid(per_slot_grid(slots, n, h_desc_), static_cast<unsigned>(n));
+    PIT_LAUNCH(KC_INIT, s, k_seg_init<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc););
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  int export_means(const SegSlot* slots, int n, cudaStream_t s) override {
+    int st = upload_slots(slots, n, s);
+    if (st != PIT_OK) return st;
+    dim3 grid(per_slot_grid(slots, n, h_desc_), static_cast<unsigned>(n));
+    PIT_LAUNCH(KC_EXPORT, s, k_seg_export<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc););
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  template <bool WITH_L>
+  int pass_t(int64_t M, int calibrate, cudaStream_t s) {
+    IeksParams<T> p = shared_;
+    p.N = M - 1;
+    p.L = chain_len_ > 0 ? chain_len_ : Base::default_chain_len(p.N);
+    p.P = p.N / p.L + 1;
+    p.want_cov = WITH_L ? 1 : 0;
+    p.calibrate = calibrate;
+    p.seg.desc = b_.desc;
+    p.seg.inst_of = b_.inst_of;
+    p.seg.acc = b_.acc;
+    if (p.P > max_chains(max_points_, chain_len_)) {
+      set_error("internal: chain count exceeds the bound");
+      return PIT_EINTERNAL;
+    }
+    const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
+    const size_t sm = Base::chain_smem();
+    PIT_LAUNCH(KC_RESIDUALS, s,
+               k_seg_residuals<C><<<Base::elem_grid(M, 256), 256, 0, s>>>(p, b_.U, b_.R, b_.Yv,
+                                                                         b_.d0););
+    PIT_LAUNCH(KC_FILTER_REDUCE, s,
+               k_filter_reduce<C, true><<<grid, kThreads, sm, s>>>(p, b_.U, b_.R, b_.Yv, b_.d0,
+                                                                  b_.fagg););
+    int st = Tree<C, true, false, false, true>::run(b_.fagg, p.P, b_.fup, false, s);
+    if (st != PIT_OK) return st;
+    PIT_LAUNCH(KC_FILTER_DOWN, s,
+               k_filter_down<C, WITH_L, false, true><<<grid, kThreads, sm, s>>>(
+                   p, b_.U, b_.R, b_.Yv, b_.d0, b_.fagg, b_.Es, b_.gs, b_.Ls, b_.sagg, b_.scal););
+    st = Tree<C, false, WITH_L, true>::run(b_.sagg, p.P, b_.sup, true, s);
+    if (st != PIT_OK) return st;
+    PIT_LAUNCH(KC_SMOOTH_DOWN, s,
+               k_smooth_down<C, WITH_L, true><<<grid, kThreads, sm, s>>>(
+                   p, b_.Es, b_.gs, b_.Ls, b_.sagg, nullptr, nullptr, nullptr, nullptr, b_.scal););
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  int pass(const SegSlot* slots, int n, bool with_L, int calibrate, SegResult* res,
+           cudaStream_t s) override {
+    if (with_L && !want_cov_) {
+      set_error("covariance pass on an engine bound without covariance buffers");
+      return PIT_EINVAL;
+    }
+    int64_t M = 0;
+    for (int i = 0; i < n; ++i) {
+      if (slots[i].off != M) {
+        set_error("internal: slots must tile the global points in order");
+        return PIT_EINTERNAL;
+      }
+      M += h_desc_[slots[i].id].N + 1;
+    }
+    if (M > max_points_ || M < 2) {
+      set_error("layout exceeds the engine's point capacity");
+      return PIT_EINVAL;
+    }
+    int st = upload_slots(slots, n, s);
+    if (st != PIT_OK) return st;
+    PIT_LAUNCH(KC_INIT, s,
+               k_seg_layout<T><<<static_cast<unsigned>(n), 256, 0, s>>>(b_.slots, b_.desc,
+                                                                       b_.inst_of););
+    PIT_CUDA_TRY(cudaMemsetAsync(b_.acc, 0, sizeof(InstAcc) * max_inst_, s));
+    st = with_L ? pass_t<true>(M, calibrate, s) : pass_t<false>(M, calibrate, s);
+    if (st != PIT_OK) return st;
+    // pageable destination: returns once the copy (and everything before it) has completed
+    PIT_CUDA_TRY(cudaMemcpyAsync(h_acc_.data(), b_.acc, sizeof(InstAcc) * max_inst_,
+                                 cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i) std::memcpy(&res[i], &h_acc_[slots[i].id], sizeof(SegResult));
+    return PIT_OK;
+  }
+
+  static SegEngine* make() { return new SegEngineImpl(); }
+
+ private:
+  Bufs b_{};
+  int64_t max_points_ = 0;
+  int max_inst_ = 0;
+  bool want_cov_ = false;
+  int chain_len_ = 0;
+  int kind_ = -1;
+  IeksParams<T> shared_{};
+  std::vector<InstDesc<T>> h_desc_;
+  std::vector<InstAcc> h_acc_;
+};
+
+}  // namespace pit

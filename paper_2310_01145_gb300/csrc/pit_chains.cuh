@@ -57,32 +57,72 @@ __device__ __forceinline__ void load_forcing(const typename C::GR& g,
   for (int l = 0; l < C::RL; ++l) uf[l] = g.valid(l) ? U[n * C::D + g.row(l)] : typename C::Tp(0);
 }
 
-// Raw per-step inputs (loaded one step ahead to hide their latency).
-template <class C>
+// Raw per-step inputs (loaded one step ahead to hide their latency).  SEG: also the point's
+// instance code (instance id, or ~id at the instance's n = 0).
+template <class C, bool SEG = false>
 struct StepIn {
   using T = typename C::Tp;
   T y[C::DD];  // solution components of lin_n (original coordinates, for the Jacobian)
   T r[C::DD];  // residual r_n
   T u[C::RL];  // forcing u_{n-1}, this lane's rows
-  __device__ __forceinline__ void load(const typename C::GR& g, const T* __restrict__ Yv,
-                                       const T* __restrict__ R, const T* __restrict__ U,
-                                       int64_t n) {
+  int code;
+  __device__ __forceinline__ void load(const typename C::GR& g, const IeksParams<T>& p,
+                                       const T* __restrict__ Yv, const T* __restrict__ R,
+                                       const T* __restrict__ U, int64_t n) {
 #pragma unroll
     for (int k = 0; k < C::DD; ++k) {
       y[k] = Yv[n * C::DD + k];
       r[k] = R[n * C::DD + k];
     }
     load_forcing<C>(g, U, n - 1, u);
+    code = SEG ? p.seg.inst_of[n] : 0;
   }
-  __device__ __forceinline__ void jacobian(const IeksParams<T>& p, T (&Ft)[C::DD][C::DD]) const {
+  __device__ __forceinline__ void jacobian(const OdeParams<T>& ode, T hq,
+                                           T (&Ft)[C::DD][C::DD]) const {
     T f[C::DD], F[C::DD][C::DD];
-    ode_eval<T, C::DD>(p.ode, y, f, F);
+    ode_eval<T, C::DD>(ode, y, f, F);
 #pragma unroll
     for (int k = 0; k < C::DD; ++k)
 #pragma unroll
-      for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * p.hq;
+      for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * hq;
   }
 };
+
+// ODE parameters of the instance that owns the current step (segmented solves switch them at
+// instance boundaries; single solves use the kernel parameters).
+template <class C, bool SEG>
+struct StepModel {
+  using T = typename C::Tp;
+  OdeParams<T> ode;
+  T hq;
+  int id = -1;
+  __device__ __forceinline__ const OdeParams<T>& params(const IeksParams<T>& p) const {
+    if constexpr (SEG) return ode; else return p.ode;
+  }
+  __device__ __forceinline__ T scale(const IeksParams<T>& p) const {
+    if constexpr (SEG) return hq; else return p.hq;
+  }
+  // SEG: make instance `nid` current; returns the previous id (or -1)
+  __device__ __forceinline__ void select(const IeksParams<T>& p, int nid) {
+    if constexpr (SEG) {
+      const InstDesc<T>& d = p.seg.desc[nid];
+      ode.kind = p.ode.kind;
+      ode.d = p.ode.d;
+#pragma unroll
+      for (int j = 0; j < kMaxInstParams; ++j) ode.p[j] = d.p[j];
+      hq = d.hq;
+      id = nid;
+    }
+  }
+};
+
+// Initial increment delta_0 of the instance that starts at global point 0.
+template <class C, bool SEG>
+__device__ __forceinline__ const typename C::Tp* first_d0(const IeksParams<typename C::Tp>& p,
+                                                          const typename C::Tp* d0) {
+  if constexpr (SEG) return d0 + static_cast<int64_t>(seg_id(p.seg.inst_of[0])) * C::D;
+  else return d0;
+}
 
 constexpr int kJBatch = 4;  // leaves whose information rows are folded into sqrtJ at once
 
@@ -92,7 +132,7 @@ constexpr int kJBatch = 4;  // leaves whose information rows are folded into sqr
 // C = 0), the others from the neutral element.  Output: one filter item per chain, with C and J
 // lower-triangular.
 // ---------------------------------------------------------------------------------------------
-template <class C>
+template <class C, bool SEG = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
                 const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
@@ -112,6 +152,7 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
   lc.init(g, p);
 
   T A[RL][D], b[RL], sC[RL][W], eta[RL], sJ[1][RL][D];
+  const T* d0c = first_d0<C, SEG>(p, d0);
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     const int r = g.row(l);
@@ -122,9 +163,10 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     }
 #pragma unroll
     for (int c = 0; c < W; ++c) sC[l][c] = T(0);
-    b[l] = (chain == 0 && r < D) ? d0[r] : T(0);
+    b[l] = (chain == 0 && r < D) ? d0c[r] : T(0);
     eta[l] = T(0);
   }
+  StepModel<C, SEG> mdl;
   // information rows G^T of the last kJBatch leaves, folded into sqrtJ by one structured LQ
   T Gbuf[1][RL][kJBatch * DD];
 #pragma unroll
@@ -134,12 +176,38 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
   int nbuf = 0;
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
-  StepIn<C> cur, nxt;
-  if (n0 <= n1) cur.load(g, Yv, R, U, n0);
+  StepIn<C, SEG> cur, nxt;
+  if (n0 <= n1) cur.load(g, p, Yv, R, U, n0);
   for (int64_t n = n0; n <= n1; ++n) {
-    if (n + 1 <= n1) nxt.load(g, Yv, R, U, n + 1);
+    if (n + 1 <= n1) nxt.load(g, p, Yv, R, U, n + 1);
+    if constexpr (SEG) {
+      if (cur.code < 0) {
+        // first point of an instance: the reset element (A = 0, b = delta_0, C = 0); the
+        // information part is dropped too, since no later value depends on it
+        const T* d0i = d0 + static_cast<int64_t>(~cur.code) * D;
+#pragma unroll
+        for (int l = 0; l < RL; ++l) {
+          const int r = g.row(l);
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            A[l][c] = T(0);
+            sJ[0][l][c] = T(0);
+          }
+#pragma unroll
+          for (int c = 0; c < W; ++c) sC[l][c] = T(0);
+#pragma unroll
+          for (int j = 0; j < kJBatch * DD; ++j) Gbuf[0][l][j] = T(0);
+          b[l] = (r < D) ? d0i[r] : T(0);
+          eta[l] = T(0);
+        }
+        nbuf = 0;
+        cur = nxt;
+        continue;
+      }
+      if (cur.code != mdl.id) mdl.select(p, cur.code);
+    }
     T Ft[DD][DD], rr[DD], uf[RL];
-    cur.jacobian(p, Ft);
+    cur.jacobian(mdl.params(p), mdl.scale(p), Ft);
 #pragma unroll
     for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll
@@ -260,7 +328,7 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
 // Accumulates the calibration sum sum_n ||sqrtS_n^-1 nu_n||^2 in FP64.
 // LOCAL_LIN: the sequential EKS; linearise at the predicted mean (plain model, no increment).
 // ---------------------------------------------------------------------------------------------
-template <class C, bool WITH_L, bool LOCAL_LIN>
+template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
               const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
@@ -286,12 +354,13 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   T m[RL], sP[RL][D];
   {
     const T* pre = fprefix + chain * C::FA;
+    const T* d0c = first_d0<C, SEG>(p, d0);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       const int r = g.valid(l) ? g.row(l) : 0;
       const bool v = g.valid(l);
       if (chain == 0) {
-        m[l] = v ? (LOCAL_LIN ? p.mu0[r] : d0[r]) : T(0);
+        m[l] = v ? (LOCAL_LIN ? p.mu0[r] : d0c[r]) : T(0);
 #pragma unroll
         for (int c = 0; c < D; ++c) sP[l][c] = T(0);
       } else {
@@ -314,6 +383,16 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     xa[l] = T(0);
   }
   double s2acc = 0.0;
+  bool closed = false;  // the smoothing aggregate holds a segment's last element (E = 0)
+  StepModel<C, SEG> mdl;
+  // calibration sum of the current instance (segmented) or of the solve
+  auto flush_s2 = [&]() {
+    if (g.gl == 0 && s2acc != 0.0) {
+      if constexpr (SEG) atomicAdd(&p.seg.acc[mdl.id].sigma2_sum, s2acc);
+      else atomicAdd(&scal->sigma2_sum, s2acc);
+    }
+    s2acc = 0.0;
+  };
 
   // fold one smoothing element (rows e, entry gg, rows lrow) into the chain aggregate and store it
   auto emit = [&](int64_t idx, const T (&e)[RL][D], const T (&gg)[RL], const T (&lrow)[RL][D]) {
@@ -329,6 +408,9 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
         for (int c = 0; c < D; ++c) Ls[idx * D * D + r * D + c] = lrow[l][c];
       }
     }
+    // after a segment's last element the aggregate is final (its E is 0): later elements,
+    // which belong to the next segment, are not folded in
+    if (closed) return;
     g.sync();
     publish<GR, D, LDM>(g, e, scr + C::MAT2);
     publish_vec(g, gg, scr + C::VEC2);
@@ -361,20 +443,63 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       for (int c = 0; c < D; ++c) Ea[l][c] = Enew[l][c];
   };
 
+  // the last smoothing element of a segment: b_N = (E = 0, g = m^f_N, sqrtL = tria(sqrtP^f_N))
+  auto emit_end = [&](int64_t idx) {
+    T e[RL][D], lrow[RL][D];
+    T Rm[1][RL][D];
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        e[l][c] = T(0);
+        Rm[0][l][c] = sP[l][c];
+      }
+    if constexpr (WITH_L) lq_dense<GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) lrow[l][c] = WITH_L ? Rm[0][l][c] : T(0);
+    T gg[RL];
+#pragma unroll
+    for (int l = 0; l < RL; ++l) gg[l] = g.valid(l) ? m[l] : T(0);
+    emit(idx, e, gg, lrow);
+    closed = true;
+  };
+
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
-  StepIn<C> cur, nxt;
-  if (!LOCAL_LIN && n0 <= n1) cur.load(g, Yv, R, U, n0);
+  StepIn<C, SEG> cur, nxt;
+  if (!LOCAL_LIN && n0 <= n1) cur.load(g, p, Yv, R, U, n0);
   // One Kalman step n.  NE = number of columns of sqrtP in use: D for a prefix that comes from
   // the tree (a full triangular factor), W = D - d after any update (rank D - d).
   auto step = [&](auto ne_tag, int64_t n) {
     constexpr int NE = decltype(ne_tag)::value;
     if constexpr (!LOCAL_LIN) {
-      if (n + 1 <= n1) nxt.load(g, Yv, R, U, n + 1);
+      if (n + 1 <= n1) nxt.load(g, p, Yv, R, U, n + 1);
+    }
+    if constexpr (SEG) {
+      if (cur.code < 0) {
+        // first point of an instance: close the previous instance with its last smoothing
+        // element and restart the filter from the reset element (delta_0, zero covariance)
+        emit_end(n - 1);
+        const T* d0i = d0 + static_cast<int64_t>(~cur.code) * D;
+#pragma unroll
+        for (int l = 0; l < RL; ++l) {
+          m[l] = g.valid(l) ? d0i[g.row(l)] : T(0);
+#pragma unroll
+          for (int cc = 0; cc < D; ++cc) sP[l][cc] = T(0);
+        }
+        cur = nxt;
+        return;
+      }
+      if (cur.code != mdl.id) {
+        flush_s2();
+        mdl.select(p, cur.code);
+      }
     }
     T Ft[DD][DD], rr[DD], uf[RL];
     if constexpr (!LOCAL_LIN) {
-      cur.jacobian(p, Ft);
+      cur.jacobian(mdl.params(p), mdl.scale(p), Ft);
 #pragma unroll
       for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll
@@ -472,27 +597,8 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     ++n;
   }
   for (; n <= n1; ++n) step(std::integral_constant<int, W>{}, n);
-  // the chain owning n = N emits b_N = (E = 0, g = m^f_N, sqrtL = tria(sqrtP^f_N))
-  if (chain == p.N / p.L) {
-    T e[RL][D], lrow[RL][D];
-    T Rm[1][RL][D];
-#pragma unroll
-    for (int l = 0; l < RL; ++l)
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        e[l][c] = T(0);
-        Rm[0][l][c] = sP[l][c];
-      }
-    if constexpr (WITH_L) lq_dense<GR, 1, D, 0, D, 0>(g, Rm, scr + C::PIV);
-#pragma unroll
-    for (int l = 0; l < RL; ++l)
-#pragma unroll
-      for (int c = 0; c < D; ++c) lrow[l][c] = WITH_L ? Rm[0][l][c] : T(0);
-    T gg[RL];
-#pragma unroll
-    for (int l = 0; l < RL; ++l) gg[l] = g.valid(l) ? m[l] : T(0);
-    emit(p.N, e, gg, lrow);
-  }
+  // the chain owning n = N emits b_N
+  if (chain == p.N / p.L) emit_end(p.N);
   // write the chain's smoothing aggregate
   T* out = sagg + chain * C::SA;
 #pragma unroll
@@ -506,7 +612,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     }
     out[C::S_G + r] = xa[l];
   }
-  if (g.gl == 0 && s2acc != 0.0) atomicAdd(&scal->sigma2_sum, s2acc);
+  flush_s2();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -517,7 +623,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 // the covariance pass writes the outputs in original coordinates.  lin == nullptr means a zero
 // trajectory (the sequential EKS).
 // ---------------------------------------------------------------------------------------------
-template <class C, bool WITH_L>
+template <class C, bool WITH_L, bool SEG = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
               const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
@@ -562,29 +668,109 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   T dmax = T(0), ymax = T(0);
   bool bad = false;
   // quasi-MLE diffusion of this (final) pass: sigma^2 = sum / (N d)
-  const T sigma = static_cast<T>(
-      (WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD)) : 1.0);
+  T sigma = static_cast<T>(
+      (!SEG && WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD))
+                                      : 1.0);
+  T T0 = p.T0;
+  // segmented: the instance being written (outputs, scalings, reductions) ...
+  int sid = -1;
+  int64_t soff = 0;
+  V* snew = lin_new;
+  T* smean = mean_out;
+  T* scov = cov_out;
+  // ... and the instance being loaded (one step ahead)
+  int lid = -1;
+  int64_t loff = 0;
+  const V* lbase = lin;
+  // reduce the change statistics over the group: one atomic per group and instance
+  auto flush = [&]() {
+    if constexpr (!WITH_L) {
+#pragma unroll
+      for (int o = C::G / 2; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(g.mask, dmax, o));
+        ymax = fmax(ymax, __shfl_xor_sync(g.mask, ymax, o));
+      }
+      const unsigned anybad = __any_sync(g.mask, bad);
+      if (g.gl == 0) {
+        double* dm = SEG ? &p.seg.acc[sid].delta_max : &scal->delta_max;
+        double* ym = SEG ? &p.seg.acc[sid].y_max : &scal->y_max;
+        unsigned* fl = SEG ? &p.seg.acc[sid].flags : &scal->flags;
+        if (anybad) atomicOr(fl, 1u);
+        atomic_max_nonneg(dm, static_cast<double>(dmax));
+        atomic_max_nonneg(ym, static_cast<double>(ymax));
+      }
+      dmax = T(0);
+      ymax = T(0);
+      bad = false;
+    }
+  };
   const int64_t s0 = chain * p.L;
   const int64_t s1 = min(chain * p.L + p.L - 1, p.N);
   // E row, g entry and trajectory entry of step n for this lane's rows (prefetched one step
   // ahead: the walk is a dependent chain, the loads are not)
-  auto load = [&](int64_t n, T (&E_)[RL][D], T (&g_)[RL], V (&l_)[RL]) {
+  auto load = [&](int64_t n, T (&E_)[RL][D], T (&g_)[RL], V (&l_)[RL], int& id_, int& code_) {
+    int64_t ln = n;
+    if constexpr (SEG) {
+      code_ = p.seg.inst_of[n];
+      id_ = seg_id(code_);
+      if (id_ != lid) {
+        const InstDesc<T>& d = p.seg.desc[id_];
+        lid = id_;
+        loff = d.off;
+        lbase = static_cast<const V*>(d.lin[d.cur]);
+      }
+      ln = n - loff;
+    }
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       const T* Er = Es + n * D * D + rr[l] * D;
 #pragma unroll
       for (int k = 0; k < D; ++k) E_[l][k] = Er[k];
       g_[l] = gs[n * D + rr[l]];
-      l_[l] = lin ? lin[n * D + rr[l]] : v_from_zero<V>();
+      l_[l] = lbase ? lbase[ln * D + rr[l]] : v_from_zero<V>();
     }
   };
   T Ec[RL][D], gc[RL];
   V lc[RL];
-  if (s1 >= s0) load(s1, Ec, gc, lc);
+  int ic = 0, cc_ = 0;
+  if (s1 >= s0) load(s1, Ec, gc, lc, ic, cc_);
+  // segmented: the point after n starts another instance (or n = N), so n is a segment's last
+  // point with E_n = 0; its successor state is taken as exactly zero (E_n m = 0 for finite m,
+  // and another instance's non-finite values stay out)
+  bool succ_start = SEG && (s1 == p.N || p.seg.inst_of[s1 + 1 <= p.N ? s1 + 1 : s1] < 0);
   for (int64_t n = s1; n >= s0; --n) {
     T En[RL][D], gn[RL];
     V ln_[RL];
-    if (n - 1 >= s0) load(n - 1, En, gn, ln_);
+    int in_ = 0, cn_ = 0;
+    if (n - 1 >= s0) load(n - 1, En, gn, ln_, in_, cn_);
+    if constexpr (SEG) {
+      if (succ_start) {
+#pragma unroll
+        for (int l = 0; l < RL; ++l) {
+          m[l] = T(0);
+#pragma unroll
+          for (int c = 0; c < D; ++c) sPs[l][c] = T(0);
+        }
+      }
+      succ_start = cc_ < 0;
+      if (ic != sid) {
+        if (sid >= 0) flush();
+        const InstDesc<T>& d = p.seg.desc[ic];
+        sid = ic;
+        soff = d.off;
+        snew = static_cast<V*>(d.lin[1 - d.cur]);
+        smean = d.mean;
+        scov = d.cov;
+        T0 = d.T0;
+#pragma unroll
+        for (int l = 0; l < RL; ++l) Trow[l] = d.Tdiag[rr[l] % C::Q1];
+        if constexpr (WITH_L)
+          sigma = static_cast<T>(p.calibrate ? sqrt(p.seg.acc[ic].sigma2_sum /
+                                                    (static_cast<double>(d.N) * C::DD))
+                                             : 1.0);
+      }
+    }
+    const int64_t on = SEG ? n - soff : n;  // index within the output arrays
     publish_vec(g, m, scr + C::VEC0);
     if constexpr (WITH_L) publish<GR, D, LDM>(g, sPs, scr + C::MAT0);
     g.sync();
@@ -619,16 +805,16 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       const int r = rr[l];
       const V lnew = v_add_small(lc[l], mn[l]);
       if constexpr (WITH_L) {
-        mean_out[n * D + r] = Trow[l] * v_to_T<T>(lnew);
+        smean[on * D + r] = Trow[l] * v_to_T<T>(lnew);
 #pragma unroll
-        for (int c = 0; c < D; ++c) cov_out[n * D * D + r * D + c] = sigma * Trow[l] * sPs[l][c];
+        for (int c = 0; c < D; ++c) scov[on * D * D + r * D + c] = sigma * Trow[l] * sPs[l][c];
       } else {
-        lin_new[n * D + r] = lnew;
+        snew[on * D + r] = lnew;
         if (r % C::Q1 == 0) {
-          const T dd = fabs(p.T0 * mn[l]);
+          const T dd = fabs(T0 * mn[l]);
           bad = bad || !(dd == dd);
           dmax = fmax(dmax, dd);
-          ymax = fmax(ymax, fabs(p.T0 * v_to_T<T>(lnew)));
+          ymax = fmax(ymax, fabs(T0 * v_to_T<T>(lnew)));
         }
       }
     }
@@ -639,21 +825,11 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       gc[l] = gn[l];
       lc[l] = ln_[l];
     }
+    ic = in_;
+    cc_ = cn_;
   }
-  if constexpr (!WITH_L) {
-    // reduce over the group (groups past the last chain have returned), one atomic per group
-#pragma unroll
-    for (int o = C::G / 2; o > 0; o >>= 1) {
-      dmax = fmax(dmax, __shfl_xor_sync(g.mask, dmax, o));
-      ymax = fmax(ymax, __shfl_xor_sync(g.mask, ymax, o));
-    }
-    const unsigned anybad = __any_sync(g.mask, bad);
-    if (g.gl == 0) {
-      if (anybad) atomicOr(&scal->flags, 1u);
-      atomic_max_nonneg(&scal->delta_max, static_cast<double>(dmax));
-      atomic_max_nonneg(&scal->y_max, static_cast<double>(ymax));
-    }
-  }
+  // groups past the last chain have returned; every lane of a live group reaches here
+  if (!SEG || sid >= 0) flush();
 }
 // ---------------------------------------------------------------------------------------------
 // Tree scans over items (filter: FA elements, smoothing: SA elements) in blocks of B items.

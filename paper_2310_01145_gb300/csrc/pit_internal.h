@@ -76,6 +76,11 @@ struct LaunchScope {
     __VA_ARGS__;                                 \
   } while (0)
 
+// Host-side validation of the C ABI arguments (PIT_OK or PIT_EINVAL with a message).
+int fill_problem(const pit_ode* ode, int q, const double* y0, Problem& pb, bool need_y0 = true);
+int fill_grid(const pit_grid* grid, Problem& pb);
+int check_opts(const pit_opts* in, pit_opts& o);
+
 // Host FP64 helpers shared by the instantiations.
 int prior_blocks(int q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
                  double* Tdiag);
@@ -96,6 +101,51 @@ struct Registrar {
 struct ScanRegistrar {
   ScanRegistrar(int dtype, int D, ScanFn filter_fn, ScanFn smooth_fn);
 };
+
+// ---- segmented (batched) solves -------------------------------------------------------------
+// A layout slot: instance `id` occupies global points off .. off + N_id of the current pass and
+// its linearisation trajectory is lin[cur].
+struct SegSlot {
+  int32_t id;
+  int32_t cur;
+  int64_t off;
+};
+// Per-instance reductions of one pass (same layout as the device-side InstAcc).
+struct SegResult {
+  double sigma2_sum;
+  double delta_max;
+  double y_max;
+  unsigned int flags;
+  unsigned int pad;
+};
+// Engine of one (dtype, d, q): device state of up to max_inst instances and the per-point
+// buffers of passes over up to max_points global points.
+class SegEngine {
+ public:
+  virtual ~SegEngine() {}
+  virtual int state_dim() const = 0;
+  virtual size_t traj_bytes(int64_t N) const = 0;   // one trajectory buffer, (N+1) x D
+  virtual size_t workspace_bytes(int64_t max_points, int max_inst, bool want_cov,
+                                 int chain_len) const = 0;
+  virtual int bind(void* ws, size_t bytes, int64_t max_points, int max_inst, bool want_cov,
+                   int chain_len) = 0;
+  // host-side constants of instance `id` (prior, exact initial state, parameters) -> device
+  virtual int set_instance(int id, const Problem& pb, void* lin0, void* lin1, void* mean,
+                           void* cov, cudaStream_t s) = 0;
+  // lin[cur] <- the constant initial trajectory mu0, for every slot
+  virtual int init_traj(const SegSlot* slots, int n, cudaStream_t s) = 0;
+  // one IEKS filter/smoother pass over the layout; means passes write lin[1 - cur], with_L
+  // passes write the instance outputs (mean, cov).  Returns the per-slot reductions (host).
+  virtual int pass(const SegSlot* slots, int n, bool with_L, int calibrate, SegResult* res,
+                   cudaStream_t s) = 0;
+  // mean <- T lin[1 - cur] (the last means pass), for every slot
+  virtual int export_means(const SegSlot* slots, int n, cudaStream_t s) = 0;
+};
+using SegFactory = SegEngine* (*)();
+struct SegRegistrar {
+  SegRegistrar(int dtype, int d, int q, SegFactory f);
+};
+SegFactory find_seg_engine(int dtype, int d, int q);
 
 // Workspace carving: 256-byte aligned bump allocator over a caller buffer.
 struct Carver {

@@ -34,6 +34,51 @@ namespace pit {
 constexpr int kMaxQ1 = 8;
 constexpr int kMaxD = 16;
 
+constexpr int kMaxInstParams = 12;  // ODE parameters per instance of a segmented solve
+
+// One instance of a segmented (batched) solve, indexed by instance id.  Many instances share
+// one global time axis: instance i occupies global points off .. off + N (its n = 0 .. N).  At
+// its n = 0 the filter scan meets a "reset" element (A = 0, b = delta_0, C = 0, eta = 0,
+// J = 0), and at its n = N the smoothing scan meets an element with E = 0, so neither scan
+// carries anything across an instance boundary (the associative operators of Section 3.1 are
+// applied unchanged; the instances form segments of one scan).
+template <typename T>
+struct InstDesc {
+  int64_t off;                  // global point of n = 0 in the current layout
+  int64_t N;                    // time steps
+  void* lin[2];                 // linearisation trajectories (TrajType<T>), (N+1) x D each
+  int cur;                      // lin[cur] is the trajectory of the current iteration
+  int pad_;
+  T* mean;                      // output means (N+1) x D, original coordinates
+  T* cov;                       // output square-root covariances (N+1) x D x D, or null
+  double pd[kMaxInstParams];    // ODE parameters (FP64)
+  double mu0d[kMaxD];           // preconditioned exact initial state
+  double T0d, T1invd;
+  double Tdiagd[kMaxQ1];
+  T p[kMaxInstParams];          // ODE parameters (arithmetic type)
+  T T0, T1inv, hq;
+  T Tdiag[kMaxQ1];
+};
+
+// Per-instance reductions of one pass (device, zeroed before each pass).
+struct InstAcc {
+  double sigma2_sum;   // sum_n ||sqrtS_n^-1 r_n||^2
+  double delta_max;    // max |change of E0 mean| (original coordinates)
+  double y_max;        // max |E0 mean|
+  unsigned int flags;  // bit 0: non-finite value seen
+  unsigned int pad;
+};
+
+// Segment view of a batched solve (all null for a single problem).
+template <typename T>
+struct SegView {
+  const InstDesc<T>* desc;   // by instance id
+  const int* inst_of;        // per global point: instance id, or ~id at the instance's n = 0
+  InstAcc* acc;              // by instance id
+};
+
+__device__ __forceinline__ int seg_id(int code) { return code < 0 ? ~code : code; }
+
 // Per-solve constants (kernel argument).
 template <typename T>
 struct IeksParams {
@@ -56,6 +101,7 @@ struct IeksParams {
   double pd[kMaxParams];
   double T0d, T1invd;
   double Tdiagd[kMaxQ1];
+  SegView<T> seg;   // segmented solve: instance table and point -> instance map
 };
 
 // Number type of the linearisation trajectory: double-float for the FP32 solver, double for the
@@ -311,6 +357,12 @@ __device__ __forceinline__ void solve_sS(const typename C::Tp (&sS)[C::DD][C::DD
 // Full associative operators on items in shared memory (group-cooperative).
 // =============================================================================================
 
+template <class C, int SZ>
+__device__ __forceinline__ void copy_item(const typename C::GR& g, const typename C::Tp* src,
+                                          typename C::Tp* dst) {
+  for (int i = g.gl; i < SZ; i += C::G) dst[i] = src[i];
+}
+
 // a_out = a_l (x)_f a_r   (Eq. sqrt-associative-filtering).  Items: [A | b | C | eta | J].
 // C of the right operand and J of the left operand must be lower-triangular (true for every
 // item the library produces: tria outputs, identity, triangularised inputs).
@@ -334,6 +386,22 @@ __device__ void combine_f(const typename C::GR& g, const typename C::Tp* al,
   int rr[RL];
 #pragma unroll
   for (int l = 0; l < RL; ++l) rr[l] = g.valid(l) ? g.row(l) : 0;
+  // A right operand with A_j = 0 (it contains the initial element of a segment) absorbs the
+  // left one: (x) gives b_j, C_j, A = 0 whatever a_l holds.  Copying it keeps non-finite values
+  // of another segment (0 * inf) out of this segment's values.
+  {
+    bool nz = false;
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) nz = nz || (g.valid(l) && !(Aj[rr[l] * D + c] == T(0)));
+    if (!__any_sync(g.mask, nz)) {
+      g.sync();
+      if (aout != ar) copy_item<C, C::FA>(g, ar, aout);
+      g.sync();
+      return;
+    }
+  }
   // 1. Xi = tria([[Ci^T Jj, I], [Jj, 0]]).  tria is invariant under a permutation of the
   // columns, so the rows are taken as top [I | Ci^T Jj], bottom [0 | Jj]: a lower-triangular
   // block plus a dense block, which the structured LQ reduces with D reflections.  Afterwards
@@ -552,6 +620,21 @@ __device__ void combine_s(const typename C::GR& g, const typename C::Tp* bl,
   int rr[RL];
 #pragma unroll
   for (int l = 0; l < RL; ++l) rr[l] = g.valid(l) ? g.row(l) : 0;
+  // A left operand with E_i = 0 (it contains the last element of a segment) absorbs the right
+  // one; copying it keeps another segment's non-finite values out (see combine_f).
+  {
+    bool nz = false;
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int c = 0; c < D; ++c) nz = nz || (g.valid(l) && !(Ei[rr[l] * D + c] == T(0)));
+    if (!__any_sync(g.mask, nz)) {
+      g.sync();
+      if (bout != bl) copy_item<C, C::SA>(g, bl, bout);
+      g.sync();
+      return;
+    }
+  }
   T En[RL][D], gn[RL];
   T tri[1][RL][D], ext[1][RL][D];
 #pragma unroll
@@ -624,10 +707,5 @@ __device__ __forceinline__ void set_identity_s(const typename C::GR& g, typename
   }
 }
 
-template <class C, int SZ>
-__device__ __forceinline__ void copy_item(const typename C::GR& g, const typename C::Tp* src,
-                                          typename C::Tp* dst) {
-  for (int i = g.gl; i < SZ; i += C::G) dst[i] = src[i];
-}
 
 }  // namespace pit

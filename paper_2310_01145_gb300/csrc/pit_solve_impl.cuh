@@ -447,6 +447,22 @@ struct SolverImpl {
     return PIT_OK;
   }
 
+  // kernels of the segmented (batched) solve
+  static int set_smem_attrs_seg() {
+    const int sm = static_cast<int>(chain_smem());
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_reduce<C, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, false, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, true, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return PIT_OK;
+  }
+
   static int run(const SolveArgs& a, size_t* wsq, bool eks) {
     const bool want_cov = a.opts.want_cov != 0;
     IeksParams<T> p;

@@ -126,3 +126,31 @@ def test_workspace_queries_scale_with_n(pit):
     sz = ctypes.c_size_t(0)
     assert lib.pit_filter_scan_workspace_size(1000, 8, 0, ctypes.byref(sz)) == 0 and sz.value > 0
     assert lib.pit_filter_scan_workspace_size(1000, 5, 0, ctypes.byref(sz)) == 8
+
+
+def test_batched_validation_on_host(pit):
+    """pit_solve_batched rejects mixed families and bad sizes before any device work."""
+    import ctypes
+    P = pit
+    lv = P.Ode(W.LOTKA_VOLTERRA, 2, np.array([1.5, 1.0, 3.0, 1.0]))
+    fhn = P.Ode(W.FITZHUGH_NAGUMO, 2, np.array([0.2, 0.2, 3.0]))
+    opts = P.make_opts(dtype="f32")
+    cs = (P._Ode * 2)(lv.c(), fhn.c())
+    gs = (P._Grid * 2)(P._Grid(0.0, 1.0, 10), P._Grid(0.0, 1.0, 12))
+    sz = ctypes.c_size_t(0)
+    lib = P.load()
+    assert lib.pit_solve_batched_workspace_size(2, cs, gs, 2, ctypes.byref(opts), ctypes.byref(sz)) == 1
+    cs2 = (P._Ode * 2)(lv.c(), lv.c())
+    assert lib.pit_solve_batched_workspace_size(2, cs2, gs, 2, ctypes.byref(opts), ctypes.byref(sz)) == 0
+    assert sz.value > 0
+    # workspace grows with the instances' lengths
+    gs3 = (P._Grid * 2)(P._Grid(0.0, 1.0, 1000), P._Grid(0.0, 1.0, 12))
+    sz3 = ctypes.c_size_t(0)
+    assert lib.pit_solve_batched_workspace_size(2, cs2, gs3, 2, ctypes.byref(opts), ctypes.byref(sz3)) == 0
+    assert sz3.value > sz.value
+    assert lib.pit_solve_batched_workspace_size(0, cs2, gs, 2, ctypes.byref(opts), ctypes.byref(sz)) == 1
+    bad = (P._Grid * 2)(P._Grid(0.0, 1.0, 10), P._Grid(1.0, 0.0, 12))
+    assert lib.pit_solve_batched_workspace_size(2, cs2, bad, 2, ctypes.byref(opts), ctypes.byref(sz)) == 1
+    assert b"instance 1" in lib.pit_last_error()
+    # q = 4 has no compiled segmented kernels
+    assert lib.pit_solve_batched_workspace_size(2, cs2, gs, 4, ctypes.byref(opts), ctypes.byref(sz)) == 8

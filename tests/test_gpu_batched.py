@@ -1,0 +1,205 @@
+"""GPU parity of the batched (segmented) solve: every instance against the FP64 oracle run on it
+alone, and each instance alone against the same instance in a mix.
+
+Bars as in test_gpu_parity: FP64 means 1e-10 and covariances 1e-8; FP32 solution means (E0 m)
+1e-5, the full FP32 state 1e-4 and covariances 1e-3 (relative to the instance's largest
+value).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from oracle import ieks  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pit():
+    import paper_2310_01145_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    P.load()
+    return P
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(1e-300, np.max(np.abs(b))))
+
+
+def cov(s):
+    return np.einsum("nij,nkj->nik", s, s)
+
+
+def _lv_mix(count, seed, n_min, n_max, q=2):
+    return W.lotka_volterra_batch(count=count, seed=seed, n_min=n_min, n_max=n_max, q=q)
+
+
+def _logistic_mix():
+    out = []
+    for N, y0, r in ((17, 0.01, 3.0), (64, 0.2, 1.0), (1, 0.5, 2.0), (100, 0.05, 3.0),
+                     (3, 0.3, 1.5), (33, 0.01, 0.5), (2, 0.9, 1.0)):
+        out.append(W.Problem(W.LOGISTIC, 1, np.array([r]), np.array([y0]), 0.0, 10.0, N, 2))
+    return out
+
+
+@pytest.mark.parametrize("chain_len", [0, 2, 3, 7])
+def test_batched_fp64_fixed_iterations_vs_oracle(pit, chain_len):
+    """Tiny and ragged instances (N = 1, 2, 3 next to longer ones) with short chains, so that
+    chains and tree nodes span several instance boundaries."""
+    probs = _logistic_mix()
+    res = pit.solve_problems_batched(probs, dtype=torch.float64, fixed_iters=3, want_cov=True,
+                                     chain_len=chain_len)
+    torch.cuda.synchronize()
+    assert res.call_status == 0
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, fixed_iters=3, want_cov=True, calibrate=True)
+        m, s = res.instance(i)
+        m = m.cpu().numpy()
+        s = s.cpu().numpy()
+        assert rel(m, orc.means) < 1e-10, (i, rel(m, orc.means))
+        assert rel(cov(s), cov(orc.sqrtcovs)) < 1e-8, i
+        assert res.iterations[i] == 3
+        assert abs(res.sigma2[i] - orc.sigma2) <= 1e-9 * orc.sigma2
+
+
+def test_batched_fp64_converged_vs_oracle(pit):
+    """Each instance stops on its own rule: iteration counts and results equal the oracle's."""
+    probs = _logistic_mix()
+    res = pit.solve_problems_batched(probs, dtype=torch.float64, max_iter=40, atol_delta=1e-10,
+                                     want_cov=True)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, atol=1e-10, max_iter=40, want_cov=True, calibrate=True)
+        m, s = res.instance(i)
+        assert res.iterations[i] == orc.iterations, (i, res.iterations[i], orc.iterations)
+        assert res.converged[i]
+        assert rel(m.cpu().numpy(), orc.means) < 1e-10, i
+        assert rel(cov(s.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8, i
+
+
+def test_batched_lotka_volterra_fp32_vs_oracle(pit):
+    """Lotka-Volterra instances with the batched workload's parameter distribution (shorter
+    grids), FP32 scans.  After one iteration every instance matches the oracle's first
+    iterate; instances 1, 2 and 7 converge under the oracle (10, 16 and 21 iterations) and
+    their FP32 fixed points match the oracle's.  (The others do not converge from the constant
+    initial trajectory: their later Gauss-Newton iterates amplify any rounding difference, so
+    they are compared at the first iterate only.)"""
+    probs = _lv_mix(8, seed=3, n_min=64, n_max=700)
+    one = pit.solve_problems_batched(probs, dtype=torch.float32, fixed_iters=1, want_cov=False)
+    conv = pit.solve_problems_batched(probs, dtype=torch.float32, fixed_iters=25,
+                                      want_cov=False)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, fixed_iters=1, want_cov=False, calibrate=False)
+        y = one.instance(i)[0].cpu().double().numpy()[:, 0::p.q + 1]
+        assert rel(y, orc.means[:, 0::p.q + 1]) < 1e-5, (i, rel(y, orc.means[:, 0::p.q + 1]))
+    for i in (1, 2, 7):
+        p = probs[i]
+        orc = ieks.ieks(p, atol=1e-10, max_iter=25, want_cov=False, calibrate=False)
+        assert orc.deltas[-1] <= 1e-10
+        y = conv.instance(i)[0].cpu().double().numpy()[:, 0::p.q + 1]
+        assert rel(y, orc.means[:, 0::p.q + 1]) < 1e-5, (i, rel(y, orc.means[:, 0::p.q + 1]))
+
+
+@pytest.mark.parametrize("dtype,tol,ctol", [(torch.float64, 1e-10, 1e-8),
+                                            (torch.float32, 1e-5, 1e-3)])
+def test_batched_alone_equals_in_mix(pit, dtype, tol, ctol):
+    """An instance solved alone (single solve, and a batch of one) gives the result it gets in
+    a mix of 24 Lotka-Volterra instances of uneven length: at its converged solution (instances
+    that converge in FP64 within 30 iterations; FP32 runs the FP64 count + 3 iterations, staying
+    at the fixed point), and after the first iteration for all instances.  (Intermediate
+    iterates of the instances that do not converge can be ill-conditioned: after two
+    iterations instance 5 differs by 1e-10 in FP64 and 1e-1 in FP32 between two partitions of
+    the same arithmetic, a rounding amplification of about 1e6.)"""
+    probs = _lv_mix(24, seed=11, n_min=40, n_max=3000)
+    ref = pit.solve_problems_batched(probs, dtype=torch.float64, max_iter=30, atol_delta=1e-10,
+                                     want_cov=False)
+    torch.cuda.synchronize()
+    converged = [i for i in range(24) if ref.converged[i]][:5]
+    assert len(converged) >= 3
+
+    def run(ps, **kw):
+        return pit.solve_problems_batched(ps, dtype=dtype, want_cov=True, **kw)
+
+    full_tol = tol if dtype == torch.float64 else 1e-4
+
+    def compare(mix, i, one, single):
+        m_mix, s_mix = mix.instance(i)
+        m_one, s_one = one.instance(0)
+        q1 = probs[i].q + 1
+        a_mix = m_mix.double().cpu().numpy()
+        for a in (m_one, single.mean):
+            a = a.double().cpu().numpy()
+            assert rel(a_mix[:, 0::q1], a[:, 0::q1]) < tol, i
+            assert rel(a_mix, a) < full_tol, i
+        c_mix = cov(s_mix.double().cpu().numpy())
+        assert rel(c_mix, cov(s_one.double().cpu().numpy())) < ctol, i
+        assert rel(c_mix, cov(single.sqrtcov.double().cpu().numpy())) < ctol, i
+
+    if dtype == torch.float64:
+        kw = dict(max_iter=30, atol_delta=1e-10)
+        mix = run(probs, **kw)
+        for i in converged:
+            one = run([probs[i]], **kw)
+            single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, **kw)
+            torch.cuda.synchronize()
+            assert mix.iterations[i] == one.iterations[0] == single.iterations == ref.iterations[i]
+            compare(mix, i, one, single)
+    else:
+        for i in converged:
+            kw = dict(fixed_iters=int(ref.iterations[i]) + 3)
+            mix = run(probs, **kw)
+            one = run([probs[i]], **kw)
+            single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, **kw)
+            torch.cuda.synchronize()
+            compare(mix, i, one, single)
+    mix1 = run(probs, fixed_iters=1)
+    for i in range(24):
+        one = run([probs[i]], fixed_iters=1)
+        single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, fixed_iters=1)
+        torch.cuda.synchronize()
+        compare(mix1, i, one, single)
+
+
+def test_batched_segment_isolation(pit):
+    """Changing one instance's data leaves every other instance's means bit-for-bit equal
+    (FP64, same layout; covariances carry the diffusion estimate, a sum whose atomic order
+    varies between runs, so they are compared to 1e-12)."""
+    probs = _lv_mix(6, seed=5, n_min=50, n_max=400)
+    a = pit.solve_problems_batched(probs, dtype=torch.float64, fixed_iters=3, want_cov=True)
+    probs2 = list(probs)
+    p = probs[2]
+    probs2[2] = W.Problem(p.kind, p.d, p.params * 1.1, p.y0 * 0.9, p.t0, p.t1, p.N, p.q)
+    b = pit.solve_problems_batched(probs2, dtype=torch.float64, fixed_iters=3, want_cov=True)
+    torch.cuda.synchronize()
+    for i in range(6):
+        ma, sa = a.instance(i)
+        mb, sb = b.instance(i)
+        if i == 2:
+            assert not torch.equal(ma, mb)
+            continue
+        assert torch.equal(ma, mb), i
+        assert rel(cov_t(sa).cpu().numpy(), cov_t(sb).cpu().numpy()) < 1e-12, i
+
+
+def cov_t(s):
+    return torch.einsum("nij,nkj->nik", s, s)
+
+
+def test_batched_single_instance_and_means_only(pit):
+    p = W.fitzhugh_nagumo(N=257, q=3)
+    r = pit.solve_problems_batched([p], dtype=torch.float64, fixed_iters=2, want_cov=False)
+    torch.cuda.synchronize()
+    orc = ieks.ieks(p, fixed_iters=2, want_cov=False, calibrate=False)
+    assert rel(r.mean.cpu().numpy(), orc.means) < 1e-9
+    assert r.sqrtcov is None
+
+
+def test_batched_rejects_mixed_families(pit):
+    probs = [W.lotka_volterra(N=10), W.fitzhugh_nagumo(N=10, q=2)]
+    with pytest.raises(pit.PitError) as ei:
+        pit.solve_problems_batched(probs, dtype=torch.float64)
+    assert ei.value.status == 1
