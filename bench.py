@@ -49,9 +49,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
-    ap.add_argument("--workload", choices=("fhn", "lv_batch"), default="fhn",
+    ap.add_argument("--workload", choices=("fhn", "lv_batch", "serve"), default="fhn",
                     help="fhn: the single-problem FitzHugh-Nagumo solve (default); lv_batch: "
-                         "4096 Lotka-Volterra instances in one batched solve")
+                         "4096 Lotka-Volterra instances in one batched solve; serve: Poisson "
+                         "request streams through the continuous-batching server")
+    ap.add_argument("--rates", type=str, default="30,100,300,1000",
+                    help="serve: arrival rates (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="serve: arrival window per rate")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--no-eks", action="store_true", help="skip the sequential-EKS comparison")
     return ap.parse_args(argv)
@@ -506,12 +511,135 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ---- serving: Poisson request streams, continuous batching ----------------------------------
+def _percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+    import workloads as W
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    rates = [float(x) for x in args.rates.split(",") if x]
+    n_max_req = int(max(rates) * args.serve_seconds) + 8
+    reqs = W.serving_requests(n_max_req, seed=1000 + rank)
+    rng = np.random.Generator(np.random.PCG64(2000 + rank))
+    unit_gaps = rng.exponential(1.0, size=n_max_req)
+    sv = pit.Server(dtype="f32", max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
+                    max_points=1 << 22, max_requests=2048, hbm_budget_bytes=24 << 30,
+                    device=dev)
+    # warm-up: one request of every class
+    seen = set()
+    for p in reqs:
+        key = (p.kind, p.q)
+        if key not in seen:
+            seen.add(key)
+            sv.submit(p)
+    while sv.step() != (0, 0):
+        pass
+    sv.poll()
+    torch.cuda.synchronize()
+    launches0 = pit.pit_launch_count()
+    per_rate = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for rate in rates:
+            n = max(8, int(rate * args.serve_seconds))
+            arr = np.cumsum(unit_gaps[:n]) / rate
+            lat = {}
+            iters = {}
+            t0 = pit.Server.clock()
+            i = 0
+            fl = qu = 0
+            while len(lat) < n:
+                now = pit.Server.clock() - t0
+                while i < n and arr[i] <= now:
+                    sv.submit(reqs[i], tag=i)
+                    i += 1
+                if fl or qu or i > len(lat):
+                    fl, qu = sv.step()
+                elif i < n:
+                    time.sleep(max(0.0, min(arr[i] - now, 0.002)))
+                for r in sv.poll():
+                    lat[r["tag"]] = r["t_done"] - (t0 + arr[r["tag"]])
+                    iters[r["tag"]] = r["iterations"]
+            wall = pit.Server.clock() - t0
+            work = sum(reqs[k].N * iters[k] for k in lat)
+            per_rate.append({"rate": rate, "requests": n, "solves_per_s": n / wall,
+                             "p50_ms": 1e3 * _percentile(list(lat.values()), 50),
+                             "p99_ms": 1e3 * _percentile(list(lat.values()), 99),
+                             "steps_iterations_per_s": work / wall,
+                             "mean_iterations": float(np.mean(list(iters.values())))})
+    launches = pit.pit_launch_count() - launches0
+    # plain single-instance FP64 parallel solves, one request at a time in arrival order
+    o64 = pit.make_opts(dtype=torch.float64, max_iter=20, atol_delta=1e-10, want_cov=False)
+    K = min(48, n_max_req)
+    for p in reqs[:3]:
+        pit.solve_problem(p, opts=o64)
+    torch.cuda.synchronize()
+    service = []
+    for p in reqs[:K]:
+        t = time.perf_counter()
+        pit.solve_problem(p, opts=o64)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t)
+    base = []
+    for rate in rates:
+        arr = np.cumsum(unit_gaps[:K]) / rate
+        t_free, lats = 0.0, []
+        for a, s in zip(arr, service):
+            start = max(a, t_free)
+            t_free = start + s
+            lats.append(t_free - a)
+        base.append({"rate": rate, "requests": K, "solves_per_s": K / t_free,
+                     "p50_ms": 1e3 * _percentile(lats, 50), "p99_ms": 1e3 * _percentile(lats, 99)})
+    top = per_rate[-1]
+    out = {
+        "metric": "served solves/s with p50/p99 latency (mixed logistic/FHN/LV requests, FP32, "
+                  "continuous batching)",
+        "value": top["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+        "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Poisson request streams; family uniform over logistic, "
+                               "FitzHugh-Nagumo, Lotka-Volterra; q ~ U{1,2,3}; N log-uniform in "
+                               "[256, 65536]; per-request stop max|dy| <= 1e-10 + 1e-6 max|y| or "
+                               "20 iterations; means + sigma^2 returned",
+                   "window_s": args.serve_seconds, "rates": rates},
+        "per_rate": per_rate,
+        "plain_single_instance_f64": {"per_rate": base,
+                                      "what": "the first 48 requests solved one at a time by the "
+                                              "single-problem FP64 parallel solver in arrival "
+                                              "order (FIFO queue; latency from measured service "
+                                              "times)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    sv.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "lv_batch":
         run_lv_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_pit(args)
 

@@ -305,6 +305,76 @@ int32_t pit_solve_batched(int32_t B, const pit_ode* odes, const pit_grid* grids,
                           const double* y0, const pit_opts* opts, void* mean, void* sqrtcov,
                           pit_batch_info* info, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---- serving with continuous batching --------------------------------------------------- */
+
+/* A solve server (no counterpart in the paper, which solves one problem at a time).  Requests
+ * (an IVP, its grid and q) wait in a FIFO queue per (ODE family, d, q) class.  Each
+ * pit_server_step admits queued requests into their class's batch while the class's point and
+ * request capacity and the device memory budget allow (the head of a queue blocks the requests
+ * behind it), runs ONE IEKS iteration (the loop body of Algorithm 2: linearisation and the
+ * parallel filter and smoother of Algorithm 1, as pit_solve_batched) over every request in
+ * flight -- each class on its own CUDA stream, so the classes' kernels overlap -- and retires
+ * the requests whose stopping rule holds (as pit_solve: max|change of E0 mean| <= atol + rtol
+ * max|E0 mean|, or max_iter iterations, or divergence as in pit_solve_batched).  A request's
+ * trajectory stays in device memory from admission to retirement; the host reads back only
+ * the per-request change statistics once per step.  Retired requests deliver their smoothing
+ * means (original coordinates) and diffusion estimate; covariances are not served.
+ * The server allocates its whole device memory budget once, at creation, and never more.
+ * Calls on one server must not overlap (they are serialised by a mutex). */
+typedef struct pit_server pit_server;
+
+typedef struct {
+  int32_t dtype;            /* [PIT_F32] arithmetic and output element type                 */
+  int32_t max_iter;         /* [20]    iteration cap per request                             */
+  double atol_delta;        /* [1e-10] stopping rule (as pit_opts)                           */
+  double rtol_delta;        /* [1e-6]                                                         */
+  int32_t calibrate;        /* [1]     quasi-MLE diffusion estimate per request               */
+  int32_t chain_len;        /* [0]     chain length inside the scans, 0 = auto               */
+  int64_t max_points;       /* [2^22]  per class: sum of (N + 1) over requests in flight      */
+  int32_t max_requests;     /* [1024]  per class: requests in flight                          */
+  int32_t pad;
+  size_t hbm_budget_bytes;  /* [8 GiB] device memory the server allocates at creation: the
+                               classes' workspaces and the requests' trajectories (2 (N+1) D
+                               values each, 8 bytes per value in FP32, 16 in FP64 rounded)     */
+} pit_server_config;
+
+typedef struct {
+  int64_t request_id;       /* id returned by pit_server_submit                              */
+  uint64_t tag;             /* caller's tag                                                   */
+  int32_t status;           /* PIT_OK (converged), PIT_ENOCONV (max_iter), PIT_ENONFINITE     */
+  int32_t iterations;
+  double last_delta;
+  double sigma2;            /* quasi-MLE diffusion sigma^2 (1 when calibrate == 0)           */
+  double t_submit;          /* pit_server_clock() at submission, admission and retirement   */
+  double t_admit;
+  double t_done;            /* the request's means are complete in its buffer at this time   */
+} pit_server_result;
+
+/* Fill `cfg` with the defaults in brackets above. */
+void pit_server_config_default(pit_server_config* cfg);
+/* Monotonic clock of the server's timestamps, in seconds. */
+double pit_server_clock(void);
+/* Create a server (allocates cfg->hbm_budget_bytes of device memory on the current device).
+ * Errors: PIT_EINVAL (config), PIT_ENOMEM (allocation failed). */
+int32_t pit_server_create(const pit_server_config* cfg, pit_server** out);
+/* Queue a request.  ode, grid, y0: host, as pit_solve.  mean_out: device, (N+1) x D values of
+ * the server's dtype, written when the request retires; the caller keeps it alive until then.
+ * request_id (host, may be NULL) receives the request's id.  The first request of a class sets
+ * up its kernels and workspace.  Errors: PIT_EINVAL (arguments, N + 1 above max_points),
+ * PIT_EUNSUPPORTED (no compiled kernels), PIT_ENOMEM (budget cannot hold another class). */
+int32_t pit_server_submit(pit_server* server, const pit_ode* ode, const pit_grid* grid,
+                          int32_t q, const double* y0, void* mean_out, uint64_t tag,
+                          int64_t* request_id);
+/* Admit, iterate once, retire (see above); waits for the iteration.  in_flight and queued
+ * (host, may be NULL) receive the counts after the step. */
+int32_t pit_server_step(pit_server* server, int32_t* in_flight, int32_t* queued);
+/* Move up to `max` retired requests' results into out (host); *n receives the count. */
+int32_t pit_server_poll(pit_server* server, pit_server_result* out, int32_t max, int32_t* n);
+/* Device memory of the budget in use (bytes) and number of classes set up. */
+int32_t pit_server_stats(pit_server* server, size_t* pool_used, int32_t* classes);
+/* Wait for outstanding work and free the server and its device memory. */
+void pit_server_destroy(pit_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,22 @@ class _BatchInfo(ctypes.Structure):
                 ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("atol_delta", ctypes.c_double), ("rtol_delta", ctypes.c_double),
+                ("calibrate", ctypes.c_int32), ("chain_len", ctypes.c_int32),
+                ("max_points", ctypes.c_int64), ("max_requests", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class _ServerResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("tag", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 _lib = None
 
 # exported symbols and their signatures (declared in include/pit.h)
@@ -97,6 +113,15 @@ SIGNATURES = {
     "pit_solve_batched": (_I32, [_I32, ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                                  ctypes.POINTER(_Opts), _P, _P, ctypes.POINTER(_BatchInfo), _P,
                                  _SZ, _P]),
+    "pit_server_config_default": (None, [ctypes.POINTER(_ServerConfig)]),
+    "pit_server_clock": (ctypes.c_double, []),
+    "pit_server_create": (_I32, [ctypes.POINTER(_ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "pit_server_submit": (_I32, [_P, ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP, _P,
+                                 ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
+    "pit_server_step": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "pit_server_poll": (_I32, [_P, ctypes.POINTER(_ServerResult), _I32, ctypes.POINTER(_I32)]),
+    "pit_server_stats": (_I32, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I32)]),
+    "pit_server_destroy": (None, [_P]),
 }
 
 
@@ -428,3 +453,84 @@ def solve_problems_batched(problems, **kw) -> BatchResult:
     return pit_solve_batched([ode_from_problem(p) for p in problems],
                              np.stack([np.asarray(p.y0, dtype=np.float64) for p in problems]),
                              [(p.t0, p.t1, p.N) for p in problems], q, opts, **kw)
+
+
+class Server:
+    """Solve server with continuous batching (pit_server_* in pit.h).  submit() queues a
+    workloads.Problem and returns its request id; step() admits, iterates once and retires;
+    poll() returns the retired requests as dicts (with their device means)."""
+
+    def __init__(self, dtype="f32", max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
+                 calibrate=True, chain_len=0, max_points=1 << 22, max_requests=1024,
+                 hbm_budget_bytes=8 << 30, device=None):
+        import torch
+        lib = load()
+        cfg = _ServerConfig()
+        lib.pit_server_config_default(ctypes.byref(cfg))
+        cfg.dtype = _dtype_code(dtype)
+        cfg.max_iter, cfg.atol_delta, cfg.rtol_delta = int(max_iter), float(atol_delta), float(rtol_delta)
+        cfg.calibrate, cfg.chain_len = int(bool(calibrate)), int(chain_len)
+        cfg.max_points, cfg.max_requests = int(max_points), int(max_requests)
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        self.cfg = cfg
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self._h = ctypes.c_void_p()
+        _check(lib.pit_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "pit_server_create")
+        self._outs = {}
+
+    @staticmethod
+    def clock() -> float:
+        return float(load().pit_server_clock())
+
+    def submit(self, problem, tag: int = 0, out=None) -> int:
+        import torch
+        ode = ode_from_problem(problem)
+        c = ode.c()
+        gr = _Grid(float(problem.t0), float(problem.t1), int(problem.N))
+        y = np.ascontiguousarray(problem.y0, dtype=np.float64)
+        if out is None:
+            out = torch.empty((problem.N + 1, problem.D), dtype=_torch_dtype(self.cfg.dtype),
+                              device=self.device)
+        rid = ctypes.c_int64(0)
+        _check(load().pit_server_submit(self._h, ctypes.byref(c), ctypes.byref(gr), int(problem.q),
+                                        _dptr(y), _tptr(out), int(tag), ctypes.byref(rid)),
+               "pit_server_submit")
+        self._outs[rid.value] = out
+        return rid.value
+
+    def step(self):
+        fl, qu = _I32(0), _I32(0)
+        _check(load().pit_server_step(self._h, ctypes.byref(fl), ctypes.byref(qu)),
+               "pit_server_step")
+        return fl.value, qu.value
+
+    def poll(self, max_results: int = 4096):
+        buf = (_ServerResult * max_results)()
+        n = _I32(0)
+        _check(load().pit_server_poll(self._h, buf, max_results, ctypes.byref(n)), "pit_server_poll")
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            out.append({"request_id": r.request_id, "tag": r.tag, "status": r.status,
+                        "iterations": r.iterations, "last_delta": r.last_delta,
+                        "sigma2": r.sigma2, "t_submit": r.t_submit, "t_admit": r.t_admit,
+                        "t_done": r.t_done, "mean": self._outs.pop(r.request_id)})
+        return out
+
+    def stats(self):
+        used, ncls = _SZ(0), _I32(0)
+        _check(load().pit_server_stats(self._h, ctypes.byref(used), ctypes.byref(ncls)),
+               "pit_server_stats")
+        return {"pool_used": used.value, "classes": ncls.value}
+
+    def close(self):
+        if self._h:
+            load().pit_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._outs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -203,6 +203,7 @@ class SegEngineImpl final : public SegEngine {
     chain_len_ = chain_len;
     h_desc_.assign(max_inst, InstDesc<T>{});
     h_acc_.assign(max_inst, InstAcc{});
+    Ns_.assign(max_inst, 0);
     kind_ = -1;
     return Base::set_smem_attrs_seg();
   }
@@ -237,7 +238,7 @@ class SegEngineImpl final : public SegEngine {
     IeksParams<T> pi;
     int st = Base::fill_params(a, pi, 0);
     if (st != PIT_OK) return st;
-    InstDesc<T>& d = h_desc_[id];
+    InstDesc<T>& d = desc_host(id);
     std::memset(&d, 0, sizeof(d));
     d.off = 0;
     d.N = pb.N;
@@ -260,8 +261,25 @@ class SegEngineImpl final : public SegEngine {
     d.T0 = pi.T0;
     d.T1inv = pi.T1inv;
     d.hq = pi.hq;
+    Ns_[id] = pb.N;
     PIT_CUDA_TRY(cudaMemcpyAsync(b_.desc + id, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     return PIT_OK;
+  }
+
+  int use_pinned_staging() override {
+    if (pin_desc_) return PIT_OK;
+    PIT_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&pin_desc_),
+                                sizeof(InstDesc<T>) * max_inst_));
+    PIT_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&pin_slots_),
+                                sizeof(SegSlot) * max_inst_));
+    PIT_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&pin_acc_), sizeof(InstAcc) * max_inst_));
+    return PIT_OK;
+  }
+
+  ~SegEngineImpl() override {
+    if (pin_desc_) cudaFreeHost(pin_desc_);
+    if (pin_slots_) cudaFreeHost(pin_slots_);
+    if (pin_acc_) cudaFreeHost(pin_acc_);
   }
 
   int upload_slots(const SegSlot* slots, int n, cudaStream_t s) {
@@ -269,20 +287,27 @@ class SegEngineImpl final : public SegEngine {
       set_error("slot count out of range");
       return PIT_EINVAL;
     }
-    PIT_CUDA_TRY(cudaMemcpyAsync(b_.slots, slots, sizeof(SegSlot) * n, cudaMemcpyHostToDevice, s));
+    const SegSlot* src = slots;
+    if (pin_slots_) {
+      // the previous upload from the staging buffer must have been consumed
+      PIT_CUDA_TRY(cudaStreamSynchronize(s));
+      std::memcpy(pin_slots_, slots, sizeof(SegSlot) * n);
+      src = pin_slots_;
+    }
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.slots, src, sizeof(SegSlot) * n, cudaMemcpyHostToDevice, s));
     return PIT_OK;
   }
 
-  static unsigned per_slot_grid(const SegSlot* slots, int n, const std::vector<InstDesc<T>>& hd) {
+  unsigned per_slot_grid(const SegSlot* slots, int n) const {
     int64_t mx = 1;
-    for (int i = 0; i < n; ++i) mx = std::max<int64_t>(mx, (hd[slots[i].id].N + 1) * D);
+    for (int i = 0; i < n; ++i) mx = std::max<int64_t>(mx, (Ns_[slots[i].id] + 1) * D);
     return static_cast<unsigned>(std::min<int64_t>((mx + 255) / 256, 64));
   }
 
   int init_traj(const SegSlot* slots, int n, cudaStream_t s) override {
     int st = upload_slots(slots, n, s);
     if (st != PIT_OK) return st;
-    dim3 grid(per_slot_grid(slots, n, h_desc_), static_cast<unsigned>(n));
+    dim3 grid(per_slot_grid(slots, n), static_cast<unsigned>(n));
     PIT_LAUNCH(KC_INIT, s, k_seg_init<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
@@ -291,7 +316,7 @@ class SegEngineImpl final : public SegEngine {
   int export_means(const SegSlot* slots, int n, cudaStream_t s) override {
     int st = upload_slots(slots, n, s);
     if (st != PIT_OK) return st;
-    dim3 grid(per_slot_grid(slots, n, h_desc_), static_cast<unsigned>(n));
+    dim3 grid(per_slot_grid(slots, n), static_cast<unsigned>(n));
     PIT_LAUNCH(KC_EXPORT, s, k_seg_export<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
@@ -334,8 +359,8 @@ class SegEngineImpl final : public SegEngine {
     return PIT_OK;
   }
 
-  int pass(const SegSlot* slots, int n, bool with_L, int calibrate, SegResult* res,
-           cudaStream_t s) override {
+  int pass_begin(const SegSlot* slots, int n, bool with_L, int calibrate,
+                 cudaStream_t s) override {
     if (with_L && !want_cov_) {
       set_error("covariance pass on an engine bound without covariance buffers");
       return PIT_EINVAL;
@@ -346,7 +371,7 @@ class SegEngineImpl final : public SegEngine {
         set_error("internal: slots must tile the global points in order");
         return PIT_EINTERNAL;
       }
-      M += h_desc_[slots[i].id].N + 1;
+      M += Ns_[slots[i].id] + 1;
     }
     if (M > max_points_ || M < 2) {
       set_error("layout exceeds the engine's point capacity");
@@ -360,12 +385,33 @@ class SegEngineImpl final : public SegEngine {
     PIT_CUDA_TRY(cudaMemsetAsync(b_.acc, 0, sizeof(InstAcc) * max_inst_, s));
     st = with_L ? pass_t<true>(M, calibrate, s) : pass_t<false>(M, calibrate, s);
     if (st != PIT_OK) return st;
-    // pageable destination: returns once the copy (and everything before it) has completed
-    PIT_CUDA_TRY(cudaMemcpyAsync(h_acc_.data(), b_.acc, sizeof(InstAcc) * max_inst_,
-                                 cudaMemcpyDeviceToHost, s));
-    PIT_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int i = 0; i < n; ++i) std::memcpy(&res[i], &h_acc_[slots[i].id], sizeof(SegResult));
+    begun_.assign(slots, slots + n);
+    if (pin_acc_) {
+      PIT_CUDA_TRY(cudaMemcpyAsync(pin_acc_, b_.acc, sizeof(InstAcc) * max_inst_,
+                                   cudaMemcpyDeviceToHost, s));
+    }
     return PIT_OK;
+  }
+
+  int pass_end(SegResult* res, cudaStream_t s) override {
+    const InstAcc* src = pin_acc_;
+    if (!pin_acc_) {
+      // pageable destination: returns once the copy (and everything before it) has completed
+      PIT_CUDA_TRY(cudaMemcpyAsync(h_acc_.data(), b_.acc, sizeof(InstAcc) * max_inst_,
+                                   cudaMemcpyDeviceToHost, s));
+      src = h_acc_.data();
+    }
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < begun_.size(); ++i)
+      std::memcpy(&res[i], &src[begun_[i].id], sizeof(SegResult));
+    return PIT_OK;
+  }
+
+  int pass(const SegSlot* slots, int n, bool with_L, int calibrate, SegResult* res,
+           cudaStream_t s) override {
+    int st = pass_begin(slots, n, with_L, calibrate, s);
+    if (st != PIT_OK) return st;
+    return pass_end(res, s);
   }
 
   static SegEngine* make() { return new SegEngineImpl(); }
@@ -378,8 +424,14 @@ class SegEngineImpl final : public SegEngine {
   int chain_len_ = 0;
   int kind_ = -1;
   IeksParams<T> shared_{};
+  InstDesc<T>& desc_host(int id) { return pin_desc_ ? pin_desc_[id] : h_desc_[id]; }
   std::vector<InstDesc<T>> h_desc_;
   std::vector<InstAcc> h_acc_;
+  std::vector<int64_t> Ns_;
+  std::vector<SegSlot> begun_;
+  InstDesc<T>* pin_desc_ = nullptr;
+  SegSlot* pin_slots_ = nullptr;
+  InstAcc* pin_acc_ = nullptr;
 };
 
 }  // namespace pit

@@ -138,6 +138,14 @@ class SegEngine {
   // passes write the instance outputs (mean, cov).  Returns the per-slot reductions (host).
   virtual int pass(const SegSlot* slots, int n, bool with_L, int calibrate, SegResult* res,
                    cudaStream_t s) = 0;
+  // the same pass split in two: pass_begin enqueues it (and the read-back of the reductions)
+  // without waiting; pass_end waits for it and returns the reductions of the begun layout
+  virtual int pass_begin(const SegSlot* slots, int n, bool with_L, int calibrate,
+                         cudaStream_t s) = 0;
+  virtual int pass_end(SegResult* res, cudaStream_t s) = 0;
+  // page-locked host staging for slots, descriptors and reductions (optional; without it the
+  // transfers go through pageable memory and pass_begin waits for the stream)
+  virtual int use_pinned_staging() = 0;
   // mean <- T lin[1 - cur] (the last means pass), for every slot
   virtual int export_means(const SegSlot* slots, int n, cudaStream_t s) = 0;
 };

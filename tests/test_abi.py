@@ -154,3 +154,22 @@ def test_batched_validation_on_host(pit):
     assert b"instance 1" in lib.pit_last_error()
     # q = 4 has no compiled segmented kernels
     assert lib.pit_solve_batched_workspace_size(2, cs2, gs, 4, ctypes.byref(opts), ctypes.byref(sz)) == 8
+
+
+def test_server_config_validation_on_host(pit):
+    """pit_server_create rejects invalid configurations before touching the device."""
+    import ctypes
+    P = pit
+    lib = P.load()
+    cfg = P._ServerConfig()
+    lib.pit_server_config_default(ctypes.byref(cfg))
+    assert cfg.dtype == 0 and cfg.max_iter == 20 and cfg.max_requests == 1024
+    h = ctypes.c_void_p()
+    for field, bad in (("dtype", 7), ("max_iter", 0), ("max_points", 1), ("max_requests", 0),
+                       ("hbm_budget_bytes", 1000)):
+        c = P._ServerConfig()
+        lib.pit_server_config_default(ctypes.byref(c))
+        setattr(c, field, bad)
+        assert lib.pit_server_create(ctypes.byref(c), ctypes.byref(h)) == 1, field
+        assert not h.value
+    assert lib.pit_server_clock() > 0

@@ -124,7 +124,10 @@ def test_batched_alone_equals_in_mix(pit, dtype, tol, ctol):
     def run(ps, **kw):
         return pit.solve_problems_batched(ps, dtype=dtype, want_cov=True, **kw)
 
-    full_tol = tol if dtype == torch.float64 else 1e-4
+    # FP32: the higher derivatives of the full state are the least accurate components (their
+    # preconditioned values grow like h^(i - q - 1/2)); at N ~ 3000 two FP32 evaluations of the
+    # first iterate differ by up to 2.5e-4 of the largest state entry there
+    full_tol = tol if dtype == torch.float64 else 1e-3
 
     def compare(mix, i, one, single):
         m_mix, s_mix = mix.instance(i)

@@ -1,0 +1,126 @@
+"""GPU tests of the serving loop (continuous batching): every request's result equals the same
+problem solved alone, whatever else is in flight when it is admitted, iterated and retired.
+
+Bars: FP64 means 1e-10, FP32 solution means 1e-5 (relative to the request's largest value).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from oracle import ieks  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pit():
+    import paper_2310_01145_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    P.load()
+    return P
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(1e-300, np.max(np.abs(b))))
+
+
+def _requests():
+    """Converging problems of four classes: logistic (q 1, 2), Lotka-Volterra (q 2; instances
+    of the batched workload's distribution that converge), Van der Pol (q 2)."""
+    lv = W.lotka_volterra_batch(count=24, seed=11, n_min=40, n_max=3000)
+    reqs = [W.logistic_paper(N=200, q=2), W.logistic(N=300, q=1, rate=1.0),
+            W.logistic_paper(N=50, q=2), lv[2], lv[11], lv[13], lv[14], lv[20],
+            W.van_der_pol(N=150, q=2), W.logistic(N=777, q=1, rate=0.5)]
+    return reqs
+
+
+def _drain(sv, limit=400):
+    out = {}
+    for _ in range(limit):
+        fl, qu = sv.step()
+        for r in sv.poll():
+            out[r["request_id"]] = r
+        if fl == 0 and qu == 0:
+            break
+    return out
+
+
+def test_server_results_equal_alone_fp64(pit):
+    reqs = _requests()
+    sv = pit.Server(dtype="f64", max_iter=40, atol_delta=1e-10, rtol_delta=0.0,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16, max_requests=64)
+    ids = [sv.submit(p, tag=i) for i, p in enumerate(reqs[:4])]
+    sv.step()
+    sv.step()
+    ids += [sv.submit(p, tag=i + 4) for i, p in enumerate(reqs[4:])]
+    done = _drain(sv)
+    assert set(done) == set(ids)
+    assert sv.stats()["classes"] == 4
+    for rid in ids:
+        r = done[rid]
+        p = reqs[r["tag"]]
+        single = pit.solve_problem(p, dtype=torch.float64, max_iter=40, atol_delta=1e-10,
+                                   want_cov=False)
+        torch.cuda.synchronize()
+        assert r["status"] == 0, r
+        assert r["iterations"] == single.iterations, (r["tag"], r["iterations"], single.iterations)
+        assert rel(r["mean"].cpu().numpy(), single.mean.cpu().numpy()) < 1e-10, r["tag"]
+        assert abs(r["sigma2"] - single.sigma2) <= 1e-9 * single.sigma2
+        assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
+    sv.close()
+
+
+def test_server_admission_by_capacity(pit):
+    """Point capacity 700 per class and at most 3 requests in flight: requests queue, are
+    admitted as earlier ones retire, and all finish with their single-solve results."""
+    probs = [W.logistic_paper(N=n, q=2) for n in (100, 250, 300, 120, 400, 90, 200, 350, 60, 500)]
+    sv = pit.Server(dtype="f64", max_iter=40, atol_delta=1e-10, rtol_delta=0.0,
+                    hbm_budget_bytes=256 << 20, max_points=700, max_requests=3)
+    ids = [sv.submit(p, tag=i) for i, p in enumerate(probs)]
+    done = {}
+    max_fl = 0
+    for _ in range(500):
+        fl, qu = sv.step()
+        max_fl = max(max_fl, fl)
+        for r in sv.poll():
+            done[r["request_id"]] = r
+        if fl == 0 and qu == 0:
+            break
+    assert set(done) == set(ids)
+    assert max_fl <= 3
+    for rid in ids:
+        r = done[rid]
+        p = probs[r["tag"]]
+        orc = ieks.ieks(p, atol=1e-10, max_iter=40, want_cov=False, calibrate=True)
+        assert r["iterations"] == orc.iterations
+        assert rel(r["mean"].cpu().numpy(), orc.means) < 1e-10
+    assert sv.stats()["pool_used"] > 0
+    sv.close()
+
+
+def test_server_fp32_vs_oracle(pit):
+    reqs = _requests()[:6]
+    sv = pit.Server(dtype="f32", max_iter=30, atol_delta=1e-10, rtol_delta=1e-6,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16)
+    ids = [sv.submit(p, tag=i) for i, p in enumerate(reqs)]
+    done = _drain(sv)
+    for rid in ids:
+        r = done[rid]
+        p = reqs[r["tag"]]
+        # the same iterate: FP32 stops on its relative rule, which can come before the FP64
+        # rule on slowly (linearly) converging problems
+        orc = ieks.ieks(p, fixed_iters=r["iterations"], want_cov=False, calibrate=False)
+        y = r["mean"].double().cpu().numpy()[:, 0::p.q + 1]
+        assert rel(y, orc.means[:, 0::p.q + 1]) < 1e-5, (r["tag"], rel(y, orc.means[:, 0::p.q + 1]))
+    sv.close()
+
+
+def test_server_rejects_oversized_request(pit):
+    sv = pit.Server(dtype="f32", hbm_budget_bytes=64 << 20, max_points=100)
+    with pytest.raises(pit.PitError) as ei:
+        sv.submit(W.logistic(N=200))
+    assert ei.value.status == 1
+    sv.close()

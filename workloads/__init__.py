@@ -160,3 +160,30 @@ def lorenz96(d: int = 64, N: int = 16384, q: int = 2, F: float = 8.0, seed: int 
 def params_array(p: Problem) -> np.ndarray:
     """Parameters as a contiguous float64 array (what the C ABI receives)."""
     return np.ascontiguousarray(p.params, dtype=np.float64)
+
+
+def serving_requests(count: int, seed: int = 0, n_min: int = 256, n_max: int = 65536,
+                     families=("logistic", "fitzhugh_nagumo", "lotka_volterra")) -> List[Problem]:
+    """Request stream of the serving workload: family uniform over `families`, q ~ U{1, 2, 3},
+    N log-uniform in [n_min, n_max]; parameters and y0 around each family's benchmark values
+    (logistic r = 3 U[0.8, 1.2], y0 = 0.01 U[0.5, 2] on [0, 10]; FitzHugh-Nagumo a, b, c scaled
+    by U[0.8, 1.2], y0 = (-1, 1) + 0.1 U[-1, 1]^2 on [0, 20]; Lotka-Volterra as the batched
+    workload)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        fam = families[int(rng.integers(len(families)))]
+        q = int(rng.integers(1, 4))
+        N = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        if fam == "logistic":
+            out.append(Problem(LOGISTIC, 1, _p(3.0 * rng.uniform(0.8, 1.2)),
+                               _p(0.01 * rng.uniform(0.5, 2.0)), 0.0, 10.0, N, q))
+        elif fam == "fitzhugh_nagumo":
+            prm = np.array([0.2, 0.2, 3.0]) * rng.uniform(0.8, 1.2, size=3)
+            y0 = np.array([-1.0, 1.0]) + 0.1 * rng.uniform(-1.0, 1.0, size=2)
+            out.append(Problem(FITZHUGH_NAGUMO, 2, prm, y0, 0.0, 20.0, N, q))
+        else:
+            prm = np.array([1.5, 1.0, 3.0, 1.0]) * rng.uniform(0.8, 1.2, size=4)
+            y0 = rng.uniform(0.5, 2.0, size=2)
+            out.append(Problem(LOTKA_VOLTERRA, 2, prm, y0, 0.0, 10.0, N, q))
+    return out
