@@ -290,7 +290,10 @@ def run_pit(args):
         achieved = fl * steps_per_launch / (avg_ms / 1e3) / 1e12
         peak = roofline.fp32_alu_peak_tflops()
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic(dom, steps_per_launch, D, args.dtype),
+                "traffic_source": "ncu dram bytes read+written per launch, scaled from N=2^19 "
+                                  "by time steps (profiles/); null if the kernels changed",
                 "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "algorithmic_flops_per_step": fl}
     else:
@@ -473,6 +476,32 @@ def run_lv_batch(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# DRAM traffic per time step of the chain kernels, from the ncu capture summarised in
+# profiles/k_filter_chain_kernels_fhn_q3_N524288_full.md (dram bytes read + written per launch /
+# time steps, FitzHugh-Nagumo IWP(3), FP32).  Valid only for the kernel sources it was taken on:
+# KERNEL_SOURCES_HASH is the hash of those sources, and the roofline's traffic is null when the
+# current sources differ.
+NCU_TRAFFIC_PER_STEP = {"filter_down": 136.53e6 / 524288, "filter_reduce": 25.25e6 / 524288}
+KERNEL_SOURCES_HASH = "9db45fbe6d2e622e"
+
+
+def kernel_sources_hash() -> str:
+    import hashlib
+    base = os.path.join(ROOT, "paper_2310_01145_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("pit_group.cuh", "pit_ode.cuh", "pit_kernels.cuh", "pit_chains.cuh"):
+        with open(os.path.join(base, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str, steps: int, D: int, dtype: str):
+    if (kernel not in NCU_TRAFFIC_PER_STEP or D != 8 or dtype != "f32"
+            or kernel_sources_hash() != KERNEL_SOURCES_HASH):
+        return None
+    return NCU_TRAFFIC_PER_STEP[kernel] * steps
 
 
 def _measured_hbm():
