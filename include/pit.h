@@ -100,7 +100,17 @@ typedef struct {
   int32_t chain_len;    /* [0]   time steps per sequential chain inside the scans, 0 = auto  */
   int32_t variant;      /* [0]   kernel layout: 0 = one state row per lane; 1 = two rows per
                                  lane (half the lanes per chain); others PIT_EUNSUPPORTED    */
+  int32_t linearization;/* [PIT_LIN_EK1] Jacobian of the linearisation (Sec. 3.2.1, remark on
+                                 approximate Jacobians): exact, its diagonal, or zero         */
+  int32_t objective;    /* [0]   1: evaluate the objective V (Eq. objective-value) of the
+                                 initial trajectory and of every iterate (pit_solve_info)     */
+  double atol_objective;/* [0]   second stopping criterion of Sec. 3.2.2: also stop when      */
+  double rtol_objective;/* [0]   |V(k) - V(k-1)| <= atol_objective + rtol_objective |V(k)|;
+                                 enabled (and V evaluated) when either is > 0                 */
 } pit_opts;
+
+/* Linearisation of the vector field (pit_opts.linearization). */
+typedef enum { PIT_LIN_EK1 = 0, PIT_LIN_DIAGONAL_EK1 = 1, PIT_LIN_EK0 = 2 } pit_linearization;
 
 /* Per-solve report, written by pit_solve (host memory). */
 typedef struct {
@@ -111,6 +121,8 @@ typedef struct {
   int64_t kernel_launches; /* CUDA kernels this call launched                               */
   double deltas[64];    /* max |change of E0 mean| of iterations 1..min(iterations, 64) (0 when
                            fixed_iters skips the per-iteration readback)                     */
+  double objective;     /* V of the returned means (0 unless V is evaluated, see pit_opts)  */
+  double objectives[65];/* V of the initial trajectory and of iterations 1..64 (same)       */
 } pit_solve_info;
 
 /* ---- library ------------------------------------------------------------------------- */

@@ -39,23 +39,39 @@ from .prior import iwp_transition, projection
 from .taylor import initial_state
 
 
-def linearize(kind, params, eta_n, t, q, d):
-    """H_n, d_n of Eq. linearized-observation-model."""
+LINEARIZATIONS = ("ek1", "diag", "ek0")
+
+
+def approximate_jacobian(F, mode: str):
+    """The Jacobian used by the linearisation: exact (EK1), its diagonal (DiagonalEK1) or zero
+    (EK0) -- the approximate-Jacobian linearisations of Section 3.2.1 (remark on approximate
+    Jacobians)."""
+    if mode == "ek1":
+        return F
+    if mode == "diag":
+        return np.diag(np.diag(F))
+    if mode == "ek0":
+        return np.zeros_like(F)
+    raise ValueError(mode)
+
+
+def linearize(kind, params, eta_n, t, q, d, mode: str = "ek1"):
+    """H_n, d_n of Eq. linearized-observation-model (with the Jacobian of `mode`)."""
     E0 = projection(0, q, d)
     E1 = projection(1, q, d)
     y = E0 @ eta_n
-    F = odes.jac(kind, params, y, t)
+    F = approximate_jacobian(odes.jac(kind, params, y, t), mode)
     fy = odes.f(kind, params, y, t)
     return E1 - F @ E0, fy - F @ y
 
 
-def linearize_all(problem, traj):
+def linearize_all(problem, traj, mode: str = "ek1"):
     d, q = problem.d, problem.q
     ts = problem.t0 + problem.h * np.arange(problem.N + 1)
     Hs = [None]
     ds = [None]
     for n in range(1, problem.N + 1):
-        H, dv = linearize(problem.kind, problem.params, traj[n], ts[n], q, d)
+        H, dv = linearize(problem.kind, problem.params, traj[n], ts[n], q, d, mode)
         Hs.append(H)
         ds.append(dv)
     return Hs, ds
@@ -67,10 +83,10 @@ def prior_factors(problem):
     return Phi, Q, sQ
 
 
-def linear_smoother(problem, traj, mu0, Phi, sQ, want_cov=True):
+def linear_smoother(problem, traj, mu0, Phi, sQ, want_cov=True, mode: str = "ek1"):
     """One linearise + filter + smoother pass (Alg. 1 in the linearised model)."""
     D = problem.D
-    Hs, ds = linearize_all(problem, traj)
+    Hs, ds = linearize_all(problem, traj, mode)
     mf, sPf, sS, res = sequential_filter(mu0, np.zeros((D, D)), Phi, sQ, Hs, ds)
     ms, sPs = rts_smoother(mf, sPf, Phi, sQ)
     return dict(Hs=Hs, ds=ds, mf=mf, sPf=sPf, sS=sS, res=res, ms=ms, sPs=sPs)
@@ -104,15 +120,21 @@ class IEKSResult:
     iterates: Optional[List[np.ndarray]] = None   # means after each iteration (if recorded)
     mu0: Optional[np.ndarray] = None
     last_pass: Optional[dict] = None
+    objectives: Optional[List[float]] = None      # V of the initial trajectory and each iterate
 
 
 def ieks(problem, atol: float = 1e-10, max_iter: int = 20, fixed_iters: Optional[int] = None,
          calibrate: bool = True, record_iterates: bool = False, init: str = "mu0",
-         want_cov: bool = True, rtol: float = 0.0, init_traj=None) -> IEKSResult:
+         want_cov: bool = True, rtol: float = 0.0, init_traj=None, linearization: str = "ek1",
+         obj_atol: Optional[float] = None, obj_rtol: float = 0.0,
+         record_objective: bool = False) -> IEKSResult:
     """Algorithm 2.  ``fixed_iters`` runs exactly that many iterations (no stopping rule);
     ``init='y0'`` starts from eta_n = [y0, 0, ..., 0] instead of mu0 (Section 3.2.2 notes that
     only E0 eta matters for the linearisation); ``init_traj`` ((N+1) x D) replaces the constant
-    initial trajectory (a warm start)."""
+    initial trajectory (a warm start).  ``linearization`` picks the Jacobian (EK1, diagonal EK1
+    or EK0, Section 3.2.1).  ``obj_atol`` enables the second stopping criterion of Section 3.2.2:
+    stop when |V(eta^k) - V(eta^(k-1))| <= obj_atol + obj_rtol |V(eta^k)| (Eq. objective-value),
+    in addition to the change rule; ``record_objective`` records V without using it."""
     d, q, N, D = problem.d, problem.q, problem.N, problem.D
     Phi, Q, sQ = prior_factors(problem)
     mu0 = initial_state(problem.kind, problem.params, problem.y0, q)
@@ -124,11 +146,13 @@ def ieks(problem, atol: float = 1e-10, max_iter: int = 20, fixed_iters: Optional
     traj = np.tile(start, (N + 1, 1)) if init_traj is None else np.array(init_traj, dtype=float)
     deltas = []
     iterates = [] if record_iterates else None
+    use_obj = obj_atol is not None
+    objectives = [objective(traj, Phi, sQ)] if (use_obj or record_objective) else None
     k = 0
     last = None
     limit = fixed_iters if fixed_iters is not None else max_iter
     while k < limit:
-        last = linear_smoother(problem, traj, mu0, Phi, sQ)
+        last = linear_smoother(problem, traj, mu0, Phi, sQ, mode=linearization)
         new = last["ms"]
         delta = float(np.max(np.abs(new[:, 0::q + 1] - traj[:, 0::q + 1])))
         deltas.append(delta)
@@ -136,10 +160,16 @@ def ieks(problem, atol: float = 1e-10, max_iter: int = 20, fixed_iters: Optional
         k += 1
         if record_iterates:
             iterates.append(new.copy())
-        if fixed_iters is None and delta <= atol + rtol * float(np.max(np.abs(new[:, 0::q + 1]))):
+        if objectives is not None:
+            objectives.append(objective(traj, Phi, sQ))
+        if fixed_iters is not None:
+            continue
+        if delta <= atol + rtol * float(np.max(np.abs(new[:, 0::q + 1]))):
+            break
+        if use_obj and abs(objectives[-1] - objectives[-2]) <= obj_atol + obj_rtol * abs(objectives[-1]):
             break
     s2 = sigma2_hat(last["sS"], last["res"], N, d) if calibrate else 1.0
     scale = np.sqrt(s2)
     return IEKSResult(means=traj, sqrtcovs=last["sPs"] * scale if want_cov else None,
                       sigma2=s2, iterations=k, deltas=deltas, iterates=iterates, mu0=mu0,
-                      last_pass=last)
+                      last_pass=last, objectives=objectives)

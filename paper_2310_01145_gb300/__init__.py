@@ -43,13 +43,22 @@ class _Opts(ctypes.Structure):
                 ("atol_delta", ctypes.c_double), ("rtol_delta", ctypes.c_double),
                 ("dtype", ctypes.c_int32), ("calibrate", ctypes.c_int32),
                 ("want_cov", ctypes.c_int32), ("chain_len", ctypes.c_int32),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("linearization", ctypes.c_int32),
+                ("objective", ctypes.c_int32), ("atol_objective", ctypes.c_double),
+                ("rtol_objective", ctypes.c_double)]
 
 
 class _Info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("deltas", ctypes.c_double * 64)]
+                ("kernel_launches", ctypes.c_int64), ("deltas", ctypes.c_double * 64),
+                ("objective", ctypes.c_double), ("objectives", ctypes.c_double * 65)]
+
+
+LINEARIZATIONS = {"ek1": 0, "diag": 1, "diagonal_ek1": 1, "ek0": 2}
+_OPT_KEYS = ("dtype", "max_iter", "fixed_iters", "atol_delta", "rtol_delta", "calibrate",
+             "want_cov", "chain_len", "variant", "linearization", "objective", "atol_objective",
+             "rtol_objective")
 
 
 class _BatchInfo(ctypes.Structure):
@@ -199,13 +208,18 @@ def pit_opts_default() -> _Opts:
 
 
 def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
-              calibrate=True, want_cov=True, chain_len=0, variant=0) -> _Opts:
+              calibrate=True, want_cov=True, chain_len=0, variant=0, linearization="ek1",
+              objective=False, atol_objective=0.0, rtol_objective=0.0) -> _Opts:
     o = pit_opts_default()
     o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
     o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
     o.dtype = _dtype_code(dtype)
     o.calibrate, o.want_cov, o.chain_len = int(bool(calibrate)), int(bool(want_cov)), int(chain_len)
     o.variant = int(variant)
+    o.linearization = (LINEARIZATIONS[linearization] if isinstance(linearization, str)
+                       else int(linearization))
+    o.objective = int(bool(objective))
+    o.atol_objective, o.rtol_objective = float(atol_objective), float(rtol_objective)
     return o
 
 
@@ -350,6 +364,8 @@ def _solve_like(fn_ws, fn_run, ode: Ode, y0, t0, t1, N, q, opts: _Opts, init_tra
     res = SolveResult(mean, cov, info.iterations, bool(info.converged), info.last_delta,
                       info.sigma2, int(info.kernel_launches), int(st))
     res.deltas = [float(info.deltas[i]) for i in range(min(info.iterations, 64))]
+    res.objective = float(info.objective)
+    res.objectives = [float(info.objectives[i]) for i in range(min(info.iterations, 64) + 1)]
     return res
 
 
@@ -376,9 +392,7 @@ def pit_eks_sequential(ode: Ode, y0, t0: float, t1: float, N: int, q: int,
 def solve_problem(problem, **kw) -> SolveResult:
     """Convenience wrapper for a workloads.Problem."""
     opts = kw.pop("opts", None) or make_opts(**{k: kw.pop(k) for k in list(kw)
-                                                if k in ("dtype", "max_iter", "fixed_iters",
-                                                         "atol_delta", "rtol_delta", "calibrate",
-                                                         "want_cov", "chain_len")})
+                                                if k in _OPT_KEYS})
     return pit_solve(ode_from_problem(problem), problem.y0, problem.t0, problem.t1, problem.N,
                      problem.q, opts, **kw)
 
@@ -446,9 +460,7 @@ def pit_solve_batched(odes: Sequence[Ode], y0s, grids: Sequence[tuple], q: int,
 def solve_problems_batched(problems, **kw) -> BatchResult:
     """Batched solve of workloads.Problem instances (same family, d and q)."""
     opts = kw.pop("opts", None) or make_opts(**{k: kw.pop(k) for k in list(kw)
-                                                if k in ("dtype", "max_iter", "fixed_iters",
-                                                         "atol_delta", "rtol_delta", "calibrate",
-                                                         "want_cov", "chain_len")})
+                                                if k in _OPT_KEYS})
     q = problems[0].q
     return pit_solve_batched([ode_from_problem(p) for p in problems],
                              np.stack([np.asarray(p.y0, dtype=np.float64) for p in problems]),

@@ -266,6 +266,8 @@ class SegEngineImpl final : public SegEngine {
     return PIT_OK;
   }
 
+  void set_linearization(int mode) override { lin_mode_ = mode; }
+
   int use_pinned_staging() override {
     if (pin_desc_) return PIT_OK;
     PIT_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&pin_desc_),
@@ -330,6 +332,7 @@ class SegEngineImpl final : public SegEngine {
     p.P = p.N / p.L + 1;
     p.want_cov = WITH_L ? 1 : 0;
     p.calibrate = calibrate;
+    p.lin_mode = lin_mode_;
     p.seg.desc = b_.desc;
     p.seg.inst_of = b_.inst_of;
     p.seg.acc = b_.acc;
@@ -423,6 +426,7 @@ class SegEngineImpl final : public SegEngine {
   bool want_cov_ = false;
   int chain_len_ = 0;
   int kind_ = -1;
+  int lin_mode_ = 0;
   IeksParams<T> shared_{};
   InstDesc<T>& desc_host(int id) { return pin_desc_ ? pin_desc_[id] : h_desc_[id]; }
   std::vector<InstDesc<T>> h_desc_;

@@ -31,25 +31,6 @@ __device__ __forceinline__ int64_t chain_index(int grp_in_block) {
 // k_residuals; the scans then handle only increment-sized numbers in FP32.
 // ---------------------------------------------------------------------------------------------
 template <class C>
-__device__ __forceinline__ void step_inputs(const IeksParams<typename C::Tp>& p,
-                                            const typename C::Tp* __restrict__ Yv,
-                                            const typename C::Tp* __restrict__ R, int64_t n,
-                                            typename C::Tp (&Ft)[C::DD][C::DD],
-                                            typename C::Tp (&rr)[C::DD]) {
-  using T = typename C::Tp;
-  T y[C::DD], f[C::DD], F[C::DD][C::DD];
-#pragma unroll
-  for (int k = 0; k < C::DD; ++k) y[k] = Yv[n * C::DD + k];
-  ode_eval<T, C::DD>(p.ode, y, f, F);
-#pragma unroll
-  for (int k = 0; k < C::DD; ++k) {
-    rr[k] = R[n * C::DD + k];
-#pragma unroll
-    for (int m = 0; m < C::DD; ++m) Ft[k][m] = F[k][m] * p.hq;
-  }
-}
-
-template <class C>
 __device__ __forceinline__ void load_forcing(const typename C::GR& g,
                                              const typename C::Tp* __restrict__ U, int64_t n,
                                              typename C::Tp (&uf)[C::RL]) {
@@ -77,10 +58,11 @@ struct StepIn {
     load_forcing<C>(g, U, n - 1, u);
     code = SEG ? p.seg.inst_of[n] : 0;
   }
-  __device__ __forceinline__ void jacobian(const OdeParams<T>& ode, T hq,
+  __device__ __forceinline__ void jacobian(const OdeParams<T>& ode, T hq, int lin_mode,
                                            T (&Ft)[C::DD][C::DD]) const {
     T f[C::DD], F[C::DD][C::DD];
     ode_eval<T, C::DD>(ode, y, f, F);
+    approximate_jacobian<T, C::DD>(lin_mode, F);
 #pragma unroll
     for (int k = 0; k < C::DD; ++k)
 #pragma unroll
@@ -207,7 +189,7 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
       if (cur.code != mdl.id) mdl.select(p, cur.code);
     }
     T Ft[DD][DD], rr[DD], uf[RL];
-    cur.jacobian(mdl.params(p), mdl.scale(p), Ft);
+    cur.jacobian(mdl.params(p), mdl.scale(p), p.lin_mode, Ft);
 #pragma unroll
     for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll
@@ -499,7 +481,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     }
     T Ft[DD][DD], rr[DD], uf[RL];
     if constexpr (!LOCAL_LIN) {
-      cur.jacobian(mdl.params(p), mdl.scale(p), Ft);
+      cur.jacobian(mdl.params(p), mdl.scale(p), p.lin_mode, Ft);
 #pragma unroll
       for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll

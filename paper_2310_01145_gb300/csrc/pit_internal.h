@@ -129,6 +129,8 @@ class SegEngine {
                                  int chain_len) const = 0;
   virtual int bind(void* ws, size_t bytes, int64_t max_points, int max_inst, bool want_cov,
                    int chain_len) = 0;
+  // Jacobian of the linearisation for every instance (pit_linearization)
+  virtual void set_linearization(int mode) = 0;
   // host-side constants of instance `id` (prior, exact initial state, parameters) -> device
   virtual int set_instance(int id, const Problem& pb, void* lin0, void* lin1, void* mean,
                            void* cov, cudaStream_t s) = 0;

@@ -102,7 +102,21 @@ struct IeksParams {
   double T0d, T1invd;
   double Tdiagd[kMaxQ1];
   SegView<T> seg;   // segmented solve: instance table and point -> instance map
+  int lin_mode;     // Jacobian: 0 exact (EK1), 1 diagonal (DiagonalEK1), 2 zero (EK0)
+  double sqbd[kMaxQ1 * kMaxQ1];   // sqrt(Qbar) in FP64 (objective value)
 };
+
+// The Jacobian used by the linearisation (Section 3.2.1, remark on approximate Jacobians):
+// exact, its diagonal, or zero.
+template <typename T, int DD>
+__device__ __forceinline__ void approximate_jacobian(int mode, T (&F)[DD][DD]) {
+  if (mode == 0) return;
+#pragma unroll
+  for (int i = 0; i < DD; ++i)
+#pragma unroll
+    for (int j = 0; j < DD; ++j)
+      if (mode == 2 || i != j) F[i][j] = T(0);
+}
 
 // Number type of the linearisation trajectory: double-float for the FP32 solver, double for the
 // FP64 solver.
@@ -124,6 +138,7 @@ struct SolveScalars {
   double y_max;        // max |E0 mean| (original coordinates)
   unsigned int flags;  // bit 0: non-finite value seen
   unsigned int pad;
+  double objective;    // V of the trajectory (Eq. objective-value), when evaluated
 };
 
 template <typename T, int DD_, int Q1_, int G_, int RL_>
@@ -195,6 +210,7 @@ __device__ __forceinline__ void linearize_y(const IeksParams<typename C::Tp>& p,
   using T = typename C::Tp;
   T f[C::DD], F[C::DD][C::DD];
   ode_eval<T, C::DD>(p.ode, y, f, F);
+  approximate_jacobian<T, C::DD>(p.lin_mode, F);
 #pragma unroll
   for (int k = 0; k < C::DD; ++k) {
     T acc = f[k];

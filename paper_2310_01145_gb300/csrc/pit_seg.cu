@@ -121,6 +121,7 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
   }
   st = e->bind(workspace, eng, M, B, want_cov, o.chain_len);
   if (st != PIT_OK) return st;
+  e->set_linearization(o.linearization);
   char* lp = static_cast<char*>(workspace) + eng;
   for (int i = 0; i < B; ++i) {
     const size_t tb = round256(e->traj_bytes(pbs[i].N));

@@ -81,6 +81,49 @@ k_residuals(const IeksParams<typename C::Tp> p,
   }
 }
 
+// Objective value of a trajectory (Eq. objective-value), V = 1/2 sum_{n=1..N}
+// || lin_n - Phi lin_{n-1} ||^2_{Q^-1}.  In preconditioned coordinates Phi, Q become Phibar,
+// Qbar and the quadratic form is unchanged, so each dimension block contributes
+// || sqrt(Qbar)^-1 (xbar_n - Phibar xbar_{n-1}) ||^2 (differences in the trajectory's number
+// type, the triangular solve and the sum in FP64).
+template <class C>
+__global__ void __launch_bounds__(256)
+k_objective(const IeksParams<typename C::Tp> p,
+            const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+            SolveScalars* __restrict__ scal) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  double acc = 0.0;
+  for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= p.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DD; ++k) {
+      double w[Q1];
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        V a = lin[n * D + k * Q1 + i] - lin[(n - 1) * D + k * Q1 + i];
+#pragma unroll
+        for (int j = i + 1; j < Q1; ++j)
+          a = a - lin[(n - 1) * D + k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+        w[i] = v_to_double(a);
+      }
+      double z[Q1];
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        double s = w[i];
+#pragma unroll
+        for (int j = 0; j < i; ++j) s -= p.sqbd[i * kMaxQ1 + j] * z[j];
+        z[i] = s / p.sqbd[i * kMaxQ1 + i];
+        acc += z[i] * z[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(&scal->objective, 0.5 * acc);
+}
+
 template <class C>
 __global__ void k_export_mean(const IeksParams<typename C::Tp> p,
                               const typename TrajType<typename C::Tp>::type* __restrict__ lin,
@@ -330,6 +373,7 @@ struct SolverImpl {
       p.pd[i] = pb.params[i];
     }
     p.N = pb.N;
+    p.lin_mode = a.opts.linearization;
     p.L = a.opts.chain_len > 0 ? a.opts.chain_len : default_chain_len(pb.N);
     p.P = pb.N / p.L + 1;
     p.want_cov = want_cov;
@@ -343,6 +387,7 @@ struct SolverImpl {
       for (int j = 0; j < Q1; ++j) {
         p.phib[i * kMaxQ1 + j] = static_cast<T>(Phib[i * Q1 + j]);
         p.sqb[i * kMaxQ1 + j] = static_cast<T>(sqb[i * Q1 + j]);
+        p.sqbd[i * kMaxQ1 + j] = sqb[i * Q1 + j];
       }
     }
     p.t0 = static_cast<T>(pb.t0);
@@ -540,6 +585,20 @@ struct SolverImpl {
     V* nxt = b.linB;  // its smoothing means
     const int fixed = a.opts.fixed_iters;
     const int limit = fixed > 0 ? fixed : std::max(1, a.opts.max_iter);
+    // objective value V (Eq. objective-value): evaluated when requested or used by the rule
+    const bool obj_rule = a.opts.atol_objective > 0 || a.opts.rtol_objective > 0;
+    const bool want_obj = obj_rule || a.opts.objective != 0;
+    const unsigned og = elem_grid(p.N, 256);
+    double v_prev = 0.0;
+    if (want_obj) {
+      PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
+      PIT_LAUNCH(KC_EXPORT, s, k_objective<C><<<og, 256, 0, s>>>(p, cur, b.scal););
+      PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      PIT_CUDA_TRY(cudaStreamSynchronize(s));
+      v_prev = hs.objective;
+      info.objectives[0] = v_prev;
+      info.objective = v_prev;
+    }
     bool converged = fixed > 0;
     int k = 0;
     while (k < limit) {
@@ -547,9 +606,10 @@ struct SolverImpl {
       if (st != PIT_OK) return st;
       st = pass<false>(p, b, cur, nxt, nullptr, nullptr, s);
       if (st != PIT_OK) return st;
+      if (want_obj) PIT_LAUNCH(KC_EXPORT, s, k_objective<C><<<og, 256, 0, s>>>(p, nxt, b.scal););
       ++k;
       bool stop = (k == limit);
-      if (fixed <= 0) {
+      if (fixed <= 0 || want_obj) {
         PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
         PIT_CUDA_TRY(cudaStreamSynchronize(s));
         if (hs.flags & 1u) {
@@ -558,10 +618,22 @@ struct SolverImpl {
         }
         info.last_delta = hs.delta_max;
         if (k <= 64) info.deltas[k - 1] = hs.delta_max;
-        if (hs.delta_max <= a.opts.atol_delta + a.opts.rtol_delta * hs.y_max) {
-          converged = true;
-          stop = true;
+        if (want_obj) {
+          if (k <= 64) info.objectives[k] = hs.objective;
+          info.objective = hs.objective;
         }
+        if (fixed <= 0) {
+          if (hs.delta_max <= a.opts.atol_delta + a.opts.rtol_delta * hs.y_max) {
+            converged = true;
+            stop = true;
+          }
+          if (obj_rule && std::fabs(hs.objective - v_prev) <=
+                              a.opts.atol_objective + a.opts.rtol_objective * std::fabs(hs.objective)) {
+            converged = true;
+            stop = true;
+          }
+        }
+        v_prev = hs.objective;
       }
       if (stop) break;
       std::swap(cur, nxt);

@@ -1,0 +1,107 @@
+"""GPU parity of the approximate-Jacobian linearisations (EK0, DiagonalEK1; Section 3.2.1,
+remark on approximate Jacobians) and of the objective value V with its stopping rule (Section
+3.2.2, Eq. objective-value), against the FP64 oracle.
+
+Bars: FP64 means 1e-10 (relative to the largest value), V 1e-9 relative; FP32 solution means
+1e-5 at the same iteration.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from oracle import ieks  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pit():
+    import paper_2310_01145_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    P.load()
+    return P
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(1e-300, np.max(np.abs(b))))
+
+
+def cov(s):
+    return np.einsum("nij,nkj->nik", s, s)
+
+
+CASES = [
+    (W.logistic_paper(N=100, q=2), "ek0"),
+    (W.lotka_volterra(N=300, q=2, t1=2.0), "ek0"),
+    (W.lotka_volterra(N=300, q=2, t1=2.0), "diag"),
+    (W.van_der_pol(N=200, q=2), "diag"),
+    (W.fitzhugh_nagumo(N=257, q=3), "diag"),
+]
+
+
+@pytest.mark.parametrize("p,mode", CASES)
+def test_fixed_iterations_fp64(pit, p, mode):
+    r = pit.solve_problem(p, dtype=torch.float64, fixed_iters=3, linearization=mode,
+                          want_cov=True, objective=True)
+    torch.cuda.synchronize()
+    orc = ieks.ieks(p, fixed_iters=3, linearization=mode, want_cov=True, calibrate=True,
+                    record_objective=True)
+    assert rel(r.mean.cpu().numpy(), orc.means) < 1e-10
+    assert rel(cov(r.sqrtcov.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8
+    for k in range(4):
+        assert r.objectives[k] == pytest.approx(orc.objectives[k], rel=1e-9), k
+
+
+@pytest.mark.parametrize("p,mode", CASES[:4])
+def test_converged_fp64_and_fp32(pit, p, mode):
+    orc = ieks.ieks(p, atol=1e-10, max_iter=100, linearization=mode, want_cov=False,
+                    calibrate=False)
+    r = pit.solve_problem(p, dtype=torch.float64, max_iter=100, atol_delta=1e-10,
+                          linearization=mode, want_cov=False)
+    torch.cuda.synchronize()
+    assert r.iterations == orc.iterations
+    assert rel(r.mean.cpu().numpy(), orc.means) < 1e-10
+    r32 = pit.solve_problem(p, dtype=torch.float32, fixed_iters=orc.iterations,
+                            linearization=mode, want_cov=False)
+    torch.cuda.synchronize()
+    q1 = p.q + 1
+    assert rel(r32.mean.double().cpu().numpy()[:, 0::q1], orc.means[:, 0::q1]) < 1e-5
+
+
+def test_objective_stopping_rule_matches_oracle(pit):
+    """Change rule off (atol 0): only |V(k) - V(k-1)| <= 1e-9 + 1e-6 |V(k)| stops."""
+    for p in (W.logistic_paper(N=100, q=2), W.van_der_pol(N=150, q=2)):
+        orc = ieks.ieks(p, atol=0.0, max_iter=40, obj_atol=1e-9, obj_rtol=1e-6, want_cov=True,
+                        calibrate=True)
+        r = pit.solve_problem(p, dtype=torch.float64, max_iter=40, atol_delta=0.0,
+                              atol_objective=1e-9, rtol_objective=1e-6, want_cov=True)
+        torch.cuda.synchronize()
+        assert r.iterations == orc.iterations < 40
+        assert r.converged
+        assert rel(r.mean.cpu().numpy(), orc.means) < 1e-10
+        assert rel(cov(r.sqrtcov.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8
+        assert r.objective == pytest.approx(orc.objectives[-1], rel=1e-9)
+
+
+def test_objective_fp32(pit):
+    p = W.fitzhugh_nagumo(N=1000, q=3)
+    orc = ieks.ieks(p, fixed_iters=2, want_cov=False, calibrate=False, record_objective=True)
+    r = pit.solve_problem(p, dtype=torch.float32, fixed_iters=2, want_cov=False, objective=True)
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert r.objectives[k] == pytest.approx(orc.objectives[k], rel=1e-4), k
+
+
+def test_batched_with_diagonal_ek1(pit):
+    probs = [W.lotka_volterra(alpha=a, N=n, q=2, t1=2.0) for a, n in ((1.5, 120), (1.3, 77), (1.7, 301))]
+    res = pit.solve_problems_batched(probs, dtype=torch.float64, fixed_iters=3, want_cov=True,
+                                     linearization="diag")
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, fixed_iters=3, linearization="diag", want_cov=True, calibrate=True)
+        m, s = res.instance(i)
+        assert rel(m.cpu().numpy(), orc.means) < 1e-10
+        assert rel(cov(s.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8

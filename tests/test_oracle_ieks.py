@@ -121,3 +121,76 @@ def test_posterior_mean_minimises_objective_under_constraints():
             pert[n] = null.T @ rng.standard_normal(null.shape[0])
         for eps in (1e-3, -1e-3):
             assert ieks.objective(r.means + eps * pert, Phi, sQ) > V0
+
+
+# ---- approximate Jacobians (Section 3.2.1, remark on EK0 and DiagonalEK1) -----------------------
+def test_diagonal_ek1_equals_ek1_for_scalar_odes():
+    """For d = 1 the Jacobian is its own diagonal: DiagonalEK1 iterates are EK1's."""
+    p = W.logistic_paper(N=60, q=2)
+    a = ieks.ieks(p, fixed_iters=4, want_cov=False, calibrate=False, record_iterates=True)
+    b = ieks.ieks(p, fixed_iters=4, want_cov=False, calibrate=False, record_iterates=True,
+                  linearization="diag")
+    for x, y in zip(a.iterates, b.iterates):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_ek0_equals_ek1_when_the_field_does_not_depend_on_y():
+    """y' = c (affine with L = 0): the Jacobian is zero, so EK0 is EK1."""
+    p = W.affine(np.zeros((2, 2)), [0.5, -1.0], [1.0, 2.0], t1=2.0, N=9, q=2)
+    a = ieks.ieks(p, fixed_iters=2, want_cov=True, calibrate=True)
+    b = ieks.ieks(p, fixed_iters=2, want_cov=True, calibrate=True, linearization="ek0")
+    np.testing.assert_allclose(a.means, b.means, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("p,mode", [
+    (W.logistic_paper(N=100, q=2), "ek0"),
+    (W.lotka_volterra(N=500, q=2, t1=2.0), "ek0"),
+    (W.lotka_volterra(N=500, q=2, t1=2.0), "diag"),
+    (W.van_der_pol(N=300, q=2), "diag"),
+])
+def test_approximate_jacobian_fixed_points_solve_the_ode_on_the_grid(p, mode):
+    """A fixed point of the approximate-Jacobian iteration satisfies the linearised constraint
+    at itself, H(eta) eta = d(eta), i.e. E1 eta_n = f(E0 eta_n) for every n >= 1 whatever the
+    Jacobian; it is feasible, so its objective V is not below EK1's (the MAP)."""
+    from oracle import odes
+    r = ieks.ieks(p, atol=1e-12, max_iter=200, want_cov=False, calibrate=False,
+                  linearization=mode, record_objective=True)
+    assert r.deltas[-1] <= 1e-12
+    q1 = p.q + 1
+    for n in range(1, p.N + 1):
+        np.testing.assert_allclose(r.means[n, 1::q1], odes.f(p.kind, p.params, r.means[n, 0::q1], 0.0),
+                                   rtol=0, atol=1e-9)
+    e = ieks.ieks(p, atol=1e-12, max_iter=200, want_cov=False, calibrate=False,
+                  record_objective=True)
+    assert r.objectives[-1] >= e.objectives[-1] * (1 - 1e-10)
+    # the approximate Jacobian does change the iteration
+    a1 = ieks.ieks(p, fixed_iters=1, want_cov=False, calibrate=False, linearization=mode)
+    b1 = ieks.ieks(p, fixed_iters=1, want_cov=False, calibrate=False)
+    assert np.max(np.abs(a1.means - b1.means)) > 1e-6
+
+
+# ---- the objective value V (Eq. objective-value) and its stopping rule ---------------------------
+def test_objective_closed_form_iwp1_one_step():
+    """IWP(1), one step h: Q(h)^-1 = [[12/h^3, -6/h^2], [-6/h^2, 4/h]] (the textbook inverse of
+    [[h^3/3, h^2/2], [h^2/2, h]]), so V = 1/2 w^T Q^-1 w with w = eta_1 - Phi eta_0."""
+    h = 0.37
+    p = W.Problem(W.AFFINE, 1, np.array([0.0, 0.0]), np.array([0.0]), 0.0, h, 1, 1)
+    Phi, Q, sQ = ieks.prior_factors(p)
+    e0 = np.array([0.3, -1.2])
+    e1 = np.array([0.9, 0.4])
+    w = np.array([e1[0] - e0[0] - h * e0[1], e1[1] - e0[1]])
+    Qi = np.array([[12 / h ** 3, -6 / h ** 2], [-6 / h ** 2, 4 / h]])
+    V = 0.5 * w @ Qi @ w
+    assert ieks.objective(np.stack([e0, e1]), Phi, sQ) == pytest.approx(V, rel=1e-12)
+
+
+def test_objective_stopping_rule():
+    """Affine ODE: one iteration reaches the posterior mean, so V does not change in the second
+    and the objective rule (with the change rule disabled) stops there."""
+    p = W.affine([[-1.0]], [1.0], [0.0], t1=3.0, N=12, q=2)
+    r = ieks.ieks(p, atol=-1.0, max_iter=10, obj_atol=1e-9, obj_rtol=1e-6, want_cov=False,
+                  calibrate=False)
+    assert r.iterations == 2
+    assert len(r.objectives) == 3
+    assert abs(r.objectives[2] - r.objectives[1]) <= 1e-9
+    assert r.objectives[0] > r.objectives[1]
