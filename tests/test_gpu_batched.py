@@ -159,10 +159,13 @@ def test_batched_alone_equals_in_mix(pit, dtype, tol, ctol):
             single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, **kw)
             torch.cuda.synchronize()
             compare(mix, i, one, single)
-    mix1 = run(probs, fixed_iters=1)
+    # first iterates, without the diffusion estimate: on these wild iterates sigma^2 is a sum
+    # dominated by a few ill-conditioned terms (FP32: 2% apart between two partitions)
+    mix1 = run(probs, fixed_iters=1, calibrate=False)
     for i in range(24):
-        one = run([probs[i]], fixed_iters=1)
-        single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, fixed_iters=1)
+        one = run([probs[i]], fixed_iters=1, calibrate=False)
+        single = pit.solve_problem(probs[i], dtype=dtype, want_cov=True, fixed_iters=1,
+                                   calibrate=False)
         torch.cuda.synchronize()
         compare(mix1, i, one, single)
 
