@@ -107,6 +107,11 @@ typedef struct {
   double atol_objective;/* [0]   second stopping criterion of Sec. 3.2.2: also stop when      */
   double rtol_objective;/* [0]   |V(k) - V(k-1)| <= atol_objective + rtol_objective |V(k)|;
                                  enabled (and V evaluated) when either is > 0                 */
+  int32_t init_coarse;  /* [0]   > 0: initial trajectory from the sequential EKS on a coarse
+                                 uniform grid of this many steps (<= N) over the same interval,
+                                 the prior mean Phi(t - t_k) m_k between coarse nodes (Sec.
+                                 3.2.2, remark on the initial trajectory); 0: constant mu0     */
+  int32_t pad_;
 } pit_opts;
 
 /* Linearisation of the vector field (pit_opts.linearization). */

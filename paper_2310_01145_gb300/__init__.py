@@ -45,7 +45,8 @@ class _Opts(ctypes.Structure):
                 ("want_cov", ctypes.c_int32), ("chain_len", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("linearization", ctypes.c_int32),
                 ("objective", ctypes.c_int32), ("atol_objective", ctypes.c_double),
-                ("rtol_objective", ctypes.c_double)]
+                ("rtol_objective", ctypes.c_double), ("init_coarse", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -58,7 +59,7 @@ class _Info(ctypes.Structure):
 LINEARIZATIONS = {"ek1": 0, "diag": 1, "diagonal_ek1": 1, "ek0": 2}
 _OPT_KEYS = ("dtype", "max_iter", "fixed_iters", "atol_delta", "rtol_delta", "calibrate",
              "want_cov", "chain_len", "variant", "linearization", "objective", "atol_objective",
-             "rtol_objective")
+             "rtol_objective", "init_coarse")
 
 
 class _BatchInfo(ctypes.Structure):
@@ -209,7 +210,8 @@ def pit_opts_default() -> _Opts:
 
 def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
               calibrate=True, want_cov=True, chain_len=0, variant=0, linearization="ek1",
-              objective=False, atol_objective=0.0, rtol_objective=0.0) -> _Opts:
+              objective=False, atol_objective=0.0, rtol_objective=0.0,
+              init_coarse=0) -> _Opts:
     o = pit_opts_default()
     o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
     o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
@@ -220,6 +222,7 @@ def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_
                        else int(linearization))
     o.objective = int(bool(objective))
     o.atol_objective, o.rtol_objective = float(atol_objective), float(rtol_objective)
+    o.init_coarse = int(init_coarse)
     return o
 
 

@@ -375,7 +375,7 @@ int check_opts(const pit_opts* in, pit_opts& o) {
   if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||
       (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20) ||
       o.variant < 0 || o.variant > 9 || o.linearization < 0 || o.linearization > 2 ||
-      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0)) {
+      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0) || o.init_coarse < 0) {
     set_error("invalid pit_opts");
     return PIT_EINVAL;
   }
@@ -497,6 +497,8 @@ void pit_opts_default(pit_opts* o) {
   o->objective = 0;
   o->atol_objective = 0.0;
   o->rtol_objective = 0.0;
+  o->init_coarse = 0;
+  o->pad_ = 0;
 }
 
 int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,

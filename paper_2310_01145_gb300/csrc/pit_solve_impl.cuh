@@ -124,6 +124,40 @@ k_objective(const IeksParams<typename C::Tp> p,
   if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(&scal->objective, 0.5 * acc);
 }
 
+// Initial trajectory from a coarse-grid solution (Section 3.2.2, remark on the initial
+// trajectory): fine point n takes the coarse smoothing mean at node k = floor(n Nc / N),
+// propagated by the prior mean over tau = t_n - t_k, x = Phi(tau) m_k with
+// Phi(tau)_ij = tau^(j-i) / (j-i)! per dimension block (original coordinates, FP64), then
+// preconditioned.
+template <class C>
+__global__ void k_coarse_init(const IeksParams<typename C::Tp> p,
+                              const typename C::Tp* __restrict__ cm, int64_t Nc, double span,
+                              typename TrajType<typename C::Tp>::type* __restrict__ lin) {
+  using V = typename TrajType<typename C::Tp>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  const double scale = span / (static_cast<double>(p.N) * static_cast<double>(Nc));
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= p.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = (n * Nc) / p.N;
+    k = k < Nc ? k : Nc;
+    const double tau = static_cast<double>(n * Nc - k * p.N) * scale;
+    double pw[Q1];  // tau^m / m!
+    pw[0] = 1.0;
+#pragma unroll
+    for (int m = 1; m < Q1; ++m) pw[m] = pw[m - 1] * tau / static_cast<double>(m);
+#pragma unroll
+    for (int b = 0; b < DD; ++b) {
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        double x = 0.0;
+#pragma unroll
+        for (int j = i; j < Q1; ++j) x += pw[j - i] * static_cast<double>(cm[k * D + b * Q1 + j]);
+        lin[n * D + b * Q1 + i] = v_from_double<V>(x / p.Tdiagd[i]);
+      }
+    }
+  }
+}
+
 template <class C>
 __global__ void k_export_mean(const IeksParams<typename C::Tp> p,
                               const typename TrajType<typename C::Tp>::type* __restrict__ lin,
@@ -411,7 +445,26 @@ struct SolverImpl {
     T *U, *R, *Yv, *d0;
     T *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
     SolveScalars* scal;
+    T* coarse_mean;       // coarse-grid initialisation: EKS means and its workspace
+    char* coarse_ws;
+    size_t coarse_ws_bytes;
   };
+
+  // The sequential EKS on the coarse grid of the initial trajectory.
+  static SolveArgs coarse_args(const SolveArgs& a) {
+    SolveArgs c = a;
+    c.pb.N = a.opts.init_coarse;
+    c.opts.init_coarse = 0;
+    c.opts.want_cov = 0;
+    c.opts.calibrate = 0;
+    c.opts.objective = 0;
+    c.opts.atol_objective = c.opts.rtol_objective = 0;
+    c.opts.chain_len = 0;
+    c.init_traj = nullptr;
+    c.info = nullptr;
+    c.sqrtcov = nullptr;
+    return c;
+  }
 
   static size_t carve(const SolveArgs& a, const IeksParams<T>& p, bool want_cov, Buffers& b) {
     Carver cv(a.workspace, a.ws_bytes);
@@ -432,6 +485,16 @@ struct SolverImpl {
                                       Tree<CT, false, true, true>::upper_bytes(p.P));
     b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
     b.scal = cv.take<SolveScalars>(1);
+    b.coarse_mean = nullptr;
+    b.coarse_ws = nullptr;
+    b.coarse_ws_bytes = 0;
+    if (a.opts.init_coarse > 0) {
+      size_t cw = 0;
+      run(coarse_args(a), &cw, true);
+      b.coarse_mean = cv.take<T>(static_cast<size_t>(a.opts.init_coarse + 1) * D);
+      b.coarse_ws = cv.take<char>(cw);
+      b.coarse_ws_bytes = cw;
+    }
     return cv.used();
   }
 
@@ -578,8 +641,25 @@ struct SolverImpl {
       return PIT_OK;
     }
 
-    PIT_LAUNCH(KC_INIT, s, 
-               k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA););
+    if (a.opts.init_coarse > 0) {
+      if (a.opts.init_coarse > p.N || a.init_traj) {
+        set_error("init_coarse must be <= N and excludes init_traj");
+        return PIT_EINVAL;
+      }
+      SolveArgs c = coarse_args(a);
+      c.mean = b.coarse_mean;
+      c.workspace = b.coarse_ws;
+      c.ws_bytes = b.coarse_ws_bytes;
+      st = run(c, nullptr, true);
+      if (st != PIT_OK) return st;
+      PIT_LAUNCH(KC_INIT, s,
+                 k_coarse_init<C><<<elem_grid(p.N + 1, 256), 256, 0, s>>>(
+                     p, b.coarse_mean, static_cast<int64_t>(a.opts.init_coarse),
+                     a.pb.t1 - a.pb.t0, b.linA););
+    } else {
+      PIT_LAUNCH(KC_INIT, s,
+                 k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA););
+    }
     PIT_CUDA_TRY(cudaGetLastError());
     V* cur = b.linA;  // linearisation trajectory of the current iteration
     V* nxt = b.linB;  // its smoothing means

@@ -110,3 +110,33 @@ def test_batched_with_diagonal_ek1(pit):
         m, s = res.instance(i)
         assert rel(m.cpu().numpy(), orc.means) < 1e-10
         assert rel(cov(s.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8
+
+
+# ---- coarse-grid initial trajectory (Section 3.2.2, remark on the initial trajectory) ------------
+@pytest.mark.parametrize("p,nc", [(W.van_der_pol(N=200, q=2), 50), (W.logistic_paper(N=301, q=1), 7),
+                                  (W.fitzhugh_nagumo(N=256, q=3), 256)])
+def test_coarse_init_fixed_iterations_fp64(pit, p, nc):
+    orc = ieks.ieks(p, fixed_iters=2, coarse_n=nc, want_cov=True, calibrate=True)
+    r = pit.solve_problem(p, dtype=torch.float64, fixed_iters=2, init_coarse=nc, want_cov=True)
+    torch.cuda.synchronize()
+    assert rel(r.mean.cpu().numpy(), orc.means) < 1e-10
+    assert rel(cov(r.sqrtcov.cpu().numpy()), cov(orc.sqrtcovs)) < 1e-8
+
+
+def test_coarse_init_converged(pit):
+    p = W.fitzhugh_nagumo(N=400, q=3)
+    orc = ieks.ieks(p, atol=1e-10, max_iter=80, coarse_n=100, want_cov=False, calibrate=False)
+    r = pit.solve_problem(p, dtype=torch.float64, max_iter=80, init_coarse=100, want_cov=False)
+    r32 = pit.solve_problem(p, dtype=torch.float32, fixed_iters=orc.iterations + 2,
+                            init_coarse=100, want_cov=False)
+    torch.cuda.synchronize()
+    assert r.iterations == orc.iterations
+    assert rel(r.mean.cpu().numpy(), orc.means) < 1e-10
+    assert rel(r32.mean.double().cpu().numpy()[:, 0::4], orc.means[:, 0::4]) < 1e-5
+
+
+def test_coarse_init_rejects_too_many_coarse_steps(pit):
+    p = W.logistic_paper(N=20, q=2)
+    with pytest.raises(pit.PitError) as ei:
+        pit.solve_problem(p, dtype=torch.float64, init_coarse=21)
+    assert ei.value.status == 1

@@ -194,3 +194,35 @@ def test_objective_stopping_rule():
     assert len(r.objectives) == 3
     assert abs(r.objectives[2] - r.objectives[1]) <= 1e-9
     assert r.objectives[0] > r.objectives[1]
+
+
+# ---- coarse-grid initial trajectory (Section 3.2.2, remark on the initial trajectory) ------------
+def test_coarse_initial_trajectory_special_cases():
+    """coarse_n = N: the trajectory is the sequential EKS itself (tau = 0 at every node).
+    Affine ODE: the coarse EKS is exact at its nodes, and between nodes the trajectory is the
+    prior mean Phi(tau) m_k; one IEKS iteration from any start reaches the posterior."""
+    p = W.van_der_pol(N=40, q=2)
+    traj = ieks.coarse_initial_trajectory(p, 40)
+    ms, _, _ = eks.eks(p, calibrate=False)
+    np.testing.assert_allclose(traj, ms, rtol=0, atol=1e-13)
+    # nodes of a coarser grid coincide with every (N / coarse_n)-th fine point
+    traj4 = ieks.coarse_initial_trajectory(p, 8)
+    import dataclasses
+    ms8, _, _ = eks.eks(dataclasses.replace(p, N=8), calibrate=False)
+    np.testing.assert_allclose(traj4[::5], ms8, rtol=0, atol=1e-13)
+    # between nodes: the Taylor shift of the node's state (tau = 2 h after node 1)
+    from oracle.prior import iwp_transition
+    Phi2, _ = iwp_transition(p.q, 2 * p.h, p.d)
+    np.testing.assert_allclose(traj4[7], Phi2 @ ms8[1], rtol=1e-14, atol=1e-14)
+    a = W.affine([[-1.0]], [1.0], [0.0], t1=3.0, N=12, q=2)
+    r1 = ieks.ieks(a, fixed_iters=1, want_cov=False, calibrate=False)
+    r2 = ieks.ieks(a, fixed_iters=1, want_cov=False, calibrate=False, coarse_n=3)
+    np.testing.assert_allclose(r1.means, r2.means, rtol=0, atol=1e-12)
+
+
+def test_coarse_init_converges_to_the_same_fixed_point_in_fewer_iterations():
+    p = W.fitzhugh_nagumo(N=400, q=3)
+    a = ieks.ieks(p, atol=1e-10, max_iter=80, want_cov=False, calibrate=False)
+    b = ieks.ieks(p, atol=1e-10, max_iter=80, want_cov=False, calibrate=False, coarse_n=100)
+    assert b.iterations < a.iterations
+    np.testing.assert_allclose(a.means[:, 0::4], b.means[:, 0::4], rtol=0, atol=1e-8)
