@@ -49,7 +49,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
-    ap.add_argument("--workload", choices=("fhn", "lv_batch", "serve"), default="fhn",
+    ap.add_argument("--workload", choices=("fhn", "lv_batch", "serve", "sweep"), default="fhn",
                     help="fhn: the single-problem FitzHugh-Nagumo solve (default); lv_batch: "
                          "4096 Lotka-Volterra instances in one batched solve; serve: Poisson "
                          "request streams through the continuous-batching server")
@@ -661,6 +661,69 @@ def run_serve(args):
         dist.destroy_process_group()
 
 
+# ---- the paper's test problems over step sizes h = 2^0 .. 2^-14 ------------------------------
+def run_sweep(args):
+    import math
+    import numpy as np
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    pit.load()
+    kmax = 14
+
+    def logistic_exact(t, y0=0.01):
+        return 1.0 / (1.0 + (1.0 / y0 - 1.0) * np.exp(-t))
+
+    rows = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for name, make, T in (("logistic", lambda N, q: W.logistic_paper(N=N, q=q), 10.0),
+                              ("rigid_body", lambda N, q: W.rigid_body(N=N, q=q), 20.0),
+                              ("van_der_pol", lambda N, q: W.van_der_pol(N=N, q=q), 6.3)):
+            for q in (1, 2):
+                for k in range(0, kmax + 1):
+                    N = max(1, int(round(T * 2.0 ** k)))
+                    p = make(N, q)
+                    o = pit.make_opts(dtype=torch.float64, max_iter=100, atol_delta=1e-10,
+                                      want_cov=True)
+                    r = pit.solve_problem(p, opts=o)  # warm-up (and the result)
+                    torch.cuda.synchronize()
+                    reps = 3 if N <= 65536 else 1
+                    ts = []
+                    for _ in range(reps):
+                        t0 = time.perf_counter()
+                        r = pit.solve_problem(p, opts=o)
+                        torch.cuda.synchronize()
+                        ts.append(time.perf_counter() - t0)
+                    t_par = min(ts)
+                    t0 = time.perf_counter()
+                    e = pit.pit_eks_sequential(pit.ode_from_problem(p), p.y0, p.t0, p.t1, p.N,
+                                               p.q, o)
+                    torch.cuda.synchronize()
+                    t_seq = time.perf_counter() - t0
+                    row = {"problem": name, "q": q, "N": N, "h": T / N,
+                           "iterations": r.iterations, "converged": r.converged,
+                           "t_par_ms": 1e3 * t_par, "t_seq_eks_ms": 1e3 * t_seq,
+                           "speedup": t_seq / t_par}
+                    if name == "logistic":
+                        t = p.t0 + p.h * np.arange(N + 1)
+                        y = r.mean.cpu().numpy()[:, 0]
+                        row["err_vs_exact"] = float(np.max(np.abs(y - logistic_exact(t))))
+                        ye = e.mean.cpu().numpy()[:, 0]
+                        row["eks_err_vs_exact"] = float(np.max(np.abs(ye - logistic_exact(t))))
+                    rows.append(row)
+    out = {"metric": "time to solution vs N (ParaIEKS and sequential EKS on the same GPU, FP64)",
+           "value": None, "unit": "ms", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "the paper's test problems (logistic r=1 on [0,10], rigid body "
+                                  "on [0,20], Van der Pol mu=1 on [0,6.3]), q in {1,2}, h = "
+                                  "2^0..2^-14 (N = T/h), stop max|dy| <= 1e-10 or 100 "
+                                  "iterations, calibrated covariances"},
+           "table": rows, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -669,6 +732,8 @@ def main(argv=None):
         run_lv_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_pit(args)
 
