@@ -266,8 +266,8 @@ void f_series(const Problem& pb, const Ser* y, Ser* out) {
 
 int taylor_init(const Problem& pb, double* mu0) {
   const int d = pb.d, q = pb.q;
-  if (q + 1 > kMaxOrd || d > 16) return PIT_EINVAL;
-  Ser y[16], fy[16];
+  if (q + 1 > kMaxOrd || d > kMaxOdeDim) return PIT_EINVAL;
+  Ser y[kMaxOdeDim], fy[kMaxOdeDim];
   for (int i = 0; i < d; ++i) y[i] = s_const(pb.y0[i]);
   for (int k = 0; k < q; ++k) {
     f_series(pb, y, fy);
@@ -299,7 +299,7 @@ static int expected_d(int kind, int d) {
     case PIT_ODE_VAN_DER_POL: return 2;
     case PIT_ODE_RIGID_BODY: return 3;
     case PIT_ODE_AFFINE: return (d >= 1 && d <= 16) ? d : -1;
-    case PIT_ODE_LORENZ96: return (d >= 4 && d <= 16) ? d : -1;
+    case PIT_ODE_LORENZ96: return (d >= 4 && d <= kMaxOdeDim) ? d : -1;
     default: return -1;
   }
 }
@@ -610,6 +610,30 @@ static int32_t solve_common(const pit_ode* ode, const pit_grid* grid, int32_t q,
   if (st != PIT_OK) return st;
   st = check_opts(opts, a.opts);
   if (st != PIT_OK) return st;
+  // approximate Jacobians decouple the components (variant 2, and always for d > 3)
+  if (!eks && a.opts.linearization != PIT_LIN_EK1 && (a.opts.variant == 2 || a.pb.d > 3)) {
+    a.init_traj = init_traj;
+    a.mean = mean;
+    a.sqrtcov = sqrtcov;
+    a.info = info;
+    a.workspace = workspace;
+    a.ws_bytes = ws_bytes;
+    a.stream = static_cast<cudaStream_t>(stream);
+    if (query) return solve_decoupled(a, query);
+    if (!mean || (a.opts.want_cov && !sqrtcov) || !workspace) {
+      set_error("null output or workspace buffer");
+      return PIT_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) {
+      set_error("workspace must be 256-byte aligned");
+      return PIT_EINVAL;
+    }
+    return solve_decoupled(a, nullptr);
+  }
+  if (a.opts.variant == 2) {
+    set_error("variant 2 (decoupled components) needs an approximate Jacobian");
+    return PIT_EINVAL;
+  }
   SolveFn fn = find_solver(a.opts.dtype, a.pb.d, q, a.opts.variant);
   if (!fn) {
     set_error("no compiled kernels for this (dtype, d, q, variant); compiled: d in 1..3, q in 1..3 "

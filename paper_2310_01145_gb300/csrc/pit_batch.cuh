@@ -61,7 +61,62 @@ __global__ void k_seg_export(const SegSlot* __restrict__ slots,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % C::D);
-    d.mean[i] = d.Tdiag[r % C::Q1] * v_to_T<T>(lin[i]);
+    d.mean[(i / C::D) * d.mean_ld + r] = d.Tdiag[r % C::Q1] * v_to_T<T>(lin[i]);
+  }
+}
+
+// Decoupled residuals: every instance is component k = id of one d-dimensional problem solved
+// with an approximate (diagonal or zero) Jacobian, laid out at offset k (N + 1); component k's
+// residual reads the whole state y_j(n) = T_0 lin_j(n) of that problem.  Writes U, R as
+// k_seg_residuals and, in place of the state, the diagonal Jacobian entry dF_kk/dy_k (Yv),
+// which the chain kernels read through the kOdeDiagJacobian family.
+template <class C>
+__global__ void __launch_bounds__(256)
+k_dec_residuals(const IeksParams<typename C::Tp> p, int d_full, int kind_full,
+                typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
+                typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  constexpr int D = C::D, Q1 = C::Q1;
+  static_assert(C::DD == 1, "decoupled components are one-dimensional");
+  for (int64_t gp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gp <= p.N;
+       gp += (int64_t)gridDim.x * blockDim.x) {
+    const int id = seg_id(p.seg.inst_of[gp]);
+    const InstDesc<T>& d = p.seg.desc[id];
+    const int64_t n = gp - d.off;
+    const V* lin = static_cast<const V*>(d.lin[d.cur]);
+    V x[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[r] = lin[n * D + r];
+    if (n < d.N) {
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        V acc = x[i];
+#pragma unroll
+        for (int j = i + 1; j < Q1; ++j)
+          acc = acc + x[j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+        acc = acc - lin[(n + 1) * D + i];
+        U[gp * D + i] = v_to_T<T>(acc);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < D; ++r) U[gp * D + r] = T(0);
+    }
+    const V T0v = v_from_double<V>(d.T0d);
+    const V T1iv = v_from_double<V>(d.T1invd);
+    auto yv = [&](int j) -> V {
+      const InstDesc<T>& e = p.seg.desc[j];
+      return T0v * static_cast<const V*>(e.lin[e.cur])[n * D];
+    };
+    const V f = component_f<V, T>(kind_full, d.pd, d_full, id, yv);
+    auto yt = [&](int j) -> T { return v_to_T<T>(yv(j)); };
+    Yv[gp] = component_jac_diag<T>(kind_full, d.pd, d_full, id, yt);
+    R[gp] = v_to_T<T>(f * T1iv - x[1]);
+    if (n == 0) {
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+        d0[static_cast<int64_t>(id) * D + r] = v_to_T<T>(v_from_double<V>(d.mu0d[r]) - x[r]);
+    }
   }
 }
 
@@ -247,6 +302,9 @@ class SegEngineImpl final : public SegEngine {
     d.cur = 0;
     d.mean = static_cast<T*>(mean);
     d.cov = static_cast<T*>(cov);
+    d.mean_ld = D;
+    d.cov_ld = D * D;
+    d.cov_rld = D;
     for (int j = 0; j < pb.n_params; ++j) {
       d.pd[j] = pb.params[j];
       d.p[j] = static_cast<T>(pb.params[j]);
@@ -267,6 +325,77 @@ class SegEngineImpl final : public SegEngine {
   }
 
   void set_linearization(int mode) override { lin_mode_ = mode; }
+  void set_decoupled(bool on) override { decoupled_ = on; }
+
+  int set_component(int id, const Problem& pb, int k, const double* mu0k, void* lin0,
+                    void* lin1, void* mean, void* cov, cudaStream_t s) override {
+    if constexpr (DD != 1) {
+      set_error("internal: decoupled components need the d = 1 engine");
+      return PIT_EINTERNAL;
+    } else {
+      if (id < 0 || id >= max_inst_) {
+        set_error("instance id out of range");
+        return PIT_EINVAL;
+      }
+      if (pb.n_params > kMaxInstParams) {
+        set_error("too many ODE parameters for a decoupled solve");
+        return PIT_EINVAL;
+      }
+      const int Dfull = pb.d * Q1;
+      // prior blocks and preconditioner of the common step size (the component problem is the
+      // 1-dimensional IWP(q) with the full problem's grid)
+      Problem p1 = pb;
+      p1.kind = PIT_ODE_LOGISTIC;
+      p1.d = 1;
+      p1.n_params = 1;
+      p1.params[0] = 0.0;
+      p1.y0[0] = 0.0;
+      SolveArgs a;
+      std::memset(&a, 0, sizeof(a));
+      a.pb = p1;
+      pit_opts_default(&a.opts);
+      IeksParams<T> pi;
+      int st = Base::fill_params(a, pi, 0);
+      if (st != PIT_OK) return st;
+      if (kind_ < 0) {
+        shared_ = pi;
+        shared_.ode.kind = kOdeDiagJacobian;
+        shared_.ode.d = 1;
+        kind_ = kOdeDiagJacobian;
+      }
+      InstDesc<T>& d = desc_host(id);
+      std::memset(&d, 0, sizeof(d));
+      d.N = pb.N;
+      d.lin[0] = lin0;
+      d.lin[1] = lin1;
+      d.mean = static_cast<T*>(mean) + static_cast<int64_t>(k) * Q1;
+      d.cov = cov ? static_cast<T*>(cov) + static_cast<int64_t>(k) * Q1 * Dfull +
+                        static_cast<int64_t>(k) * Q1
+                  : nullptr;
+      d.mean_ld = Dfull;
+      d.cov_ld = static_cast<int64_t>(Dfull) * Dfull;
+      d.cov_rld = Dfull;
+      for (int j = 0; j < pb.n_params; ++j) {
+        d.pd[j] = pb.params[j];
+        d.p[j] = static_cast<T>(pb.params[j]);
+      }
+      for (int r = 0; r < Q1; ++r) d.mu0d[r] = mu0k[r] / pi.Tdiagd[r];
+      d.T0d = pi.T0d;
+      d.T1invd = pi.T1invd;
+      for (int i = 0; i < Q1; ++i) {
+        d.Tdiagd[i] = pi.Tdiagd[i];
+        d.Tdiag[i] = pi.Tdiag[i];
+      }
+      d.T0 = pi.T0;
+      d.T1inv = pi.T1inv;
+      d.hq = pi.hq;
+      Ns_[id] = pb.N;
+      dec_kind_ = pb.kind;
+      dec_d_ = pb.d;
+      PIT_CUDA_TRY(cudaMemcpyAsync(b_.desc + id, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+      return PIT_OK;
+    }
+  }
 
   int use_pinned_staging() override {
     if (pin_desc_) return PIT_OK;
@@ -333,6 +462,7 @@ class SegEngineImpl final : public SegEngine {
     p.want_cov = WITH_L ? 1 : 0;
     p.calibrate = calibrate;
     p.lin_mode = lin_mode_;
+    p.sigma_pool = decoupled_ ? dec_d_ : 0;
     p.seg.desc = b_.desc;
     p.seg.inst_of = b_.inst_of;
     p.seg.acc = b_.acc;
@@ -342,9 +472,17 @@ class SegEngineImpl final : public SegEngine {
     }
     const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
     const size_t sm = Base::chain_smem();
-    PIT_LAUNCH(KC_RESIDUALS, s,
-               k_seg_residuals<C><<<Base::elem_grid(M, 256), 256, 0, s>>>(p, b_.U, b_.R, b_.Yv,
-                                                                         b_.d0););
+    if (decoupled_) {
+      if constexpr (DD == 1) {
+        PIT_LAUNCH(KC_RESIDUALS, s,
+                   k_dec_residuals<C><<<Base::elem_grid(M, 256), 256, 0, s>>>(
+                       p, dec_d_, dec_kind_, b_.U, b_.R, b_.Yv, b_.d0););
+      }
+    } else {
+      PIT_LAUNCH(KC_RESIDUALS, s,
+                 k_seg_residuals<C><<<Base::elem_grid(M, 256), 256, 0, s>>>(p, b_.U, b_.R, b_.Yv,
+                                                                           b_.d0););
+    }
     PIT_LAUNCH(KC_FILTER_REDUCE, s,
                k_filter_reduce<C, true><<<grid, kThreads, sm, s>>>(p, b_.U, b_.R, b_.Yv, b_.d0,
                                                                   b_.fagg););
@@ -427,6 +565,8 @@ class SegEngineImpl final : public SegEngine {
   int chain_len_ = 0;
   int kind_ = -1;
   int lin_mode_ = 0;
+  bool decoupled_ = false;
+  int dec_kind_ = 0, dec_d_ = 1;
   IeksParams<T> shared_{};
   InstDesc<T>& desc_host(int id) { return pin_desc_ ? pin_desc_[id] : h_desc_[id]; }
   std::vector<InstDesc<T>> h_desc_;

@@ -660,6 +660,7 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   V* snew = lin_new;
   T* smean = mean_out;
   T* scov = cov_out;
+  int64_t mld = D, cld = D * D, crld = D;  // output strides (point, point, row)
   // ... and the instance being loaded (one step ahead)
   int lid = -1;
   int64_t loff = 0;
@@ -743,13 +744,25 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
         snew = static_cast<V*>(d.lin[1 - d.cur]);
         smean = d.mean;
         scov = d.cov;
+        mld = d.mean_ld;
+        cld = d.cov_ld;
+        crld = d.cov_rld;
         T0 = d.T0;
 #pragma unroll
         for (int l = 0; l < RL; ++l) Trow[l] = d.Tdiag[rr[l] % C::Q1];
-        if constexpr (WITH_L)
-          sigma = static_cast<T>(p.calibrate ? sqrt(p.seg.acc[ic].sigma2_sum /
-                                                    (static_cast<double>(d.N) * C::DD))
-                                             : 1.0);
+        if constexpr (WITH_L) {
+          double s2 = 1.0;
+          if (p.calibrate) {
+            if (p.sigma_pool > 0) {
+              double tot = 0.0;
+              for (int j = 0; j < p.sigma_pool; ++j) tot += p.seg.acc[j].sigma2_sum;
+              s2 = tot / (static_cast<double>(d.N) * p.sigma_pool * C::DD);
+            } else {
+              s2 = p.seg.acc[ic].sigma2_sum / (static_cast<double>(d.N) * C::DD);
+            }
+          }
+          sigma = static_cast<T>(sqrt(s2));
+        }
       }
     }
     const int64_t on = SEG ? n - soff : n;  // index within the output arrays
@@ -787,9 +800,9 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
       const int r = rr[l];
       const V lnew = v_add_small(lc[l], mn[l]);
       if constexpr (WITH_L) {
-        smean[on * D + r] = Trow[l] * v_to_T<T>(lnew);
+        smean[on * mld + r] = Trow[l] * v_to_T<T>(lnew);
 #pragma unroll
-        for (int c = 0; c < D; ++c) scov[on * D * D + r * D + c] = sigma * Trow[l] * sPs[l][c];
+        for (int c = 0; c < D; ++c) scov[on * cld + r * crld + c] = sigma * Trow[l] * sPs[l][c];
       } else {
         snew[on * D + r] = lnew;
         if (r % C::Q1 == 0) {

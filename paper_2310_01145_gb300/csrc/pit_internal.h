@@ -12,6 +12,8 @@
 
 namespace pit {
 
+constexpr int kMaxOdeDim = 64;  // largest ODE dimension d accepted at the boundary
+
 // Problem description after host-side validation.
 struct Problem {
   int kind;
@@ -21,7 +23,7 @@ struct Problem {
   int n_params;
   double t0, t1;
   int64_t N;
-  double y0[16];
+  double y0[kMaxOdeDim];
 };
 
 struct SolveArgs {
@@ -134,6 +136,11 @@ class SegEngine {
   // host-side constants of instance `id` (prior, exact initial state, parameters) -> device
   virtual int set_instance(int id, const Problem& pb, void* lin0, void* lin1, void* mean,
                            void* cov, cudaStream_t s) = 0;
+  // decoupled solves (approximate Jacobians, see solve_decoupled): instance `id` is component
+  // k of the d-dimensional problem pb, with its (q+1)-block mu0k of the exact initial state;
+  // outputs are written into the full (N+1) x d(q+1) mean and (N+1) x D x D covariance arrays
+  virtual int set_component(int id, const Problem& pb, int k, const double* mu0k, void* lin0,
+                            void* lin1, void* mean, void* cov, cudaStream_t s) = 0;
   // lin[cur] <- the constant initial trajectory mu0, for every slot
   virtual int init_traj(const SegSlot* slots, int n, cudaStream_t s) = 0;
   // one IEKS filter/smoother pass over the layout; means passes write lin[1 - cur], with_L
@@ -144,6 +151,8 @@ class SegEngine {
   // without waiting; pass_end waits for it and returns the reductions of the begun layout
   virtual int pass_begin(const SegSlot* slots, int n, bool with_L, int calibrate,
                          cudaStream_t s) = 0;
+  // decoupled residuals: component instances read the whole state of their problem
+  virtual void set_decoupled(bool on) = 0;
   virtual int pass_end(SegResult* res, cudaStream_t s) = 0;
   // page-locked host staging for slots, descriptors and reductions (optional; without it the
   // transfers go through pageable memory and pass_begin waits for the stream)
@@ -156,6 +165,10 @@ struct SegRegistrar {
   SegRegistrar(int dtype, int d, int q, SegFactory f);
 };
 SegFactory find_seg_engine(int dtype, int d, int q);
+
+// ParaIEKS with an approximate (diagonal or zero) Jacobian, solved as d decoupled
+// (q+1)-dimensional problems on the segmented engine (pit_seg.cu).
+int solve_decoupled(const SolveArgs& a, size_t* ws_query);
 
 // Workspace carving: 256-byte aligned bump allocator over a caller buffer.
 struct Carver {

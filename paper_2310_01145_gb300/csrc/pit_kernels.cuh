@@ -49,8 +49,11 @@ struct InstDesc {
   void* lin[2];                 // linearisation trajectories (TrajType<T>), (N+1) x D each
   int cur;                      // lin[cur] is the trajectory of the current iteration
   int pad_;
-  T* mean;                      // output means (N+1) x D, original coordinates
-  T* cov;                       // output square-root covariances (N+1) x D x D, or null
+  T* mean;                      // output means, original coordinates: point n, row r at
+                                // mean[n * mean_ld + r]
+  T* cov;                       // output square-root covariances, or null: point n, (r, c) at
+                                // cov[n * cov_ld + r * cov_rld + c]
+  int64_t mean_ld, cov_ld, cov_rld;
   double pd[kMaxInstParams];    // ODE parameters (FP64)
   double mu0d[kMaxD];           // preconditioned exact initial state
   double T0d, T1invd;
@@ -103,6 +106,8 @@ struct IeksParams {
   double Tdiagd[kMaxQ1];
   SegView<T> seg;   // segmented solve: instance table and point -> instance map
   int lin_mode;     // Jacobian: 0 exact (EK1), 1 diagonal (DiagonalEK1), 2 zero (EK0)
+  int sigma_pool;   // segmented: > 0 pools the diffusion sums of instances 0..sigma_pool-1
+                    // (the components of one decoupled problem) into one sigma-hat
   double sqbd[kMaxQ1 * kMaxQ1];   // sqrt(Qbar) in FP64 (objective value)
 };
 

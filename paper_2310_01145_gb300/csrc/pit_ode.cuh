@@ -8,6 +8,9 @@
 namespace pit {
 
 constexpr int kMaxParams = 32;
+// Internal family code of the components of a decoupled solve (approximate Jacobians): the
+// solver passes the precomputed diagonal Jacobian entry in place of the state.
+constexpr int kOdeDiagJacobian = 100;
 
 template <typename T>
 struct OdeParams {
@@ -101,6 +104,9 @@ __device__ __forceinline__ void ode_eval(const OdeParams<T>& P, const T (&y)[DD]
       }
       break;
     }
+    case kOdeDiagJacobian:  // component of a decoupled solve: y[0] carries dF_kk/dy_k
+      if constexpr (DD == 1) F[0][0] = y[0];
+      break;
     default:
       break;
   }
@@ -288,6 +294,67 @@ __device__ __forceinline__ void ode_consts_v(const OdeParams<T>& P, const double
       break;
     default: break;
   }
+}
+
+
+// Component k of the vector field f(y) of a d-dimensional problem, in number type V, with the
+// state read through y(j) (decoupled solves).  Families with d <= 3 evaluate the full field;
+// Lorenz-96 reads its three neighbours only.
+template <typename V, typename T, typename Get>
+__device__ __forceinline__ V component_f(int kind, const double* pd, int d, int k, Get y) {
+  if (kind == 3) {  // Lorenz-96: (y_{k+1} - y_{k-2}) y_{k-1} - y_k + F
+    const V a = y((k + 1) % d), b = y((k - 2 + d) % d), c = y((k - 1 + d) % d);
+    return (a - b) * c - y(k) + v_from_double<V>(pd[0]);
+  }
+  OdeParams<T> P;
+  P.kind = kind;
+  P.d = d;
+  V out = v_from_zero<V>();
+  if (d == 1) {
+    OdeConstsV<V> oc;
+    ode_consts_v<V, T, 1>(P, pd, oc);
+    V yy[1] = {y(0)}, f[1];
+    ode_f_v<V, 1>(oc, yy, f);
+    out = f[0];
+  } else if (d == 2) {
+    OdeConstsV<V> oc;
+    ode_consts_v<V, T, 2>(P, pd, oc);
+    V yy[2] = {y(0), y(1)}, f[2];
+    ode_f_v<V, 2>(oc, yy, f);
+    out = f[k];
+  } else if (d == 3) {
+    OdeConstsV<V> oc;
+    ode_consts_v<V, T, 3>(P, pd, oc);
+    V yy[3] = {y(0), y(1), y(2)}, f[3];
+    ode_f_v<V, 3>(oc, yy, f);
+    out = f[k];
+  }
+  return out;
+}
+
+// Diagonal entry dF_kk/dy_k of the Jacobian (arithmetic type T), state through y(j).
+template <typename T, typename Get>
+__device__ __forceinline__ T component_jac_diag(int kind, const double* pd, int d, int k, Get y) {
+  if (kind == 3) return T(-1);  // Lorenz-96
+  OdeParams<T> P;
+  P.kind = kind;
+  P.d = d;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) P.p[i] = static_cast<T>(pd[i]);
+  if (d == 1) {
+    T yy[1] = {y(0)}, f[1], F[1][1];
+    ode_eval<T, 1>(P, yy, f, F);
+    return F[0][0];
+  } else if (d == 2) {
+    T yy[2] = {y(0), y(1)}, f[2], F[2][2];
+    ode_eval<T, 2>(P, yy, f, F);
+    return F[k][k];
+  } else if (d == 3) {
+    T yy[3] = {y(0), y(1), y(2)}, f[3], F[3][3];
+    ode_eval<T, 3>(P, yy, f, F);
+    return F[k][k];
+  }
+  return T(0);
 }
 
 }  // namespace pit

@@ -1,5 +1,6 @@
 // Host side of the segmented (batched) solves: engine registry, the active-set iteration of
 // pit_solve_batched (Algorithm 2 per instance, all instances in the same launches), and its C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -231,6 +232,124 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
 }
 
 }  // namespace
+
+// Approximate Jacobians make the linearised model of a d-dimensional problem block diagonal:
+// the prior is I_d (x) IWP(q), H_n = E1 - F E0 with F diagonal (or zero) acts on each
+// component's block alone, and Sigma_0 = 0.  The filter and smoother of one iteration are then
+// d independent (q+1)-dimensional ones (Section 3.2.1, remark on approximate Jacobians), coupled
+// only through the residuals f(E0 lin) of the common trajectory.  They run as d segments of one
+// scan on the d = 1 segmented engine, iterated together under the global stopping rule.
+int solve_decoupled(const SolveArgs& a, size_t* wsq) {
+  const Problem& pb = a.pb;
+  const pit_opts& o = a.opts;
+  const int d = pb.d, q = pb.q, Q1 = q + 1, Dfull = d * Q1;
+  if (o.linearization == PIT_LIN_EK1) {
+    set_error("the decoupled solve needs an approximate Jacobian (DiagonalEK1 or EK0)");
+    return PIT_EINVAL;
+  }
+  if (a.init_traj || o.init_coarse > 0 || o.objective || o.atol_objective > 0 ||
+      o.rtol_objective > 0) {
+    set_error("decoupled solves support neither warm starts, coarse initialisation nor the "
+              "objective value");
+    return PIT_EINVAL;
+  }
+  SegFactory fac = find_seg_engine(o.dtype, 1, q);
+  if (!fac) {
+    set_error("no compiled kernels for the decoupled components (q in 1..3)");
+    return PIT_EUNSUPPORTED;
+  }
+  std::unique_ptr<SegEngine> e(fac());
+  const int64_t M = static_cast<int64_t>(d) * (pb.N + 1);
+  const bool want_cov = o.want_cov != 0;
+  const size_t eng = round256(e->workspace_bytes(M, d, want_cov, o.chain_len));
+  const size_t tb = round256(e->traj_bytes(pb.N));
+  const size_t total = eng + static_cast<size_t>(d) * 2 * tb;
+  if (wsq) {
+    *wsq = total;
+    return PIT_OK;
+  }
+  if (a.ws_bytes < total) {
+    set_error("workspace too small: need " + std::to_string(total) + " bytes, got " +
+              std::to_string(a.ws_bytes));
+    return PIT_ENOMEM;
+  }
+  cudaStream_t s = a.stream;
+  const int64_t launches0 = launches_total();
+  int st = e->bind(a.workspace, eng, M, d, want_cov, o.chain_len);
+  if (st != PIT_OK) return st;
+  e->set_linearization(o.linearization);
+  e->set_decoupled(true);
+  std::vector<double> mu0(Dfull);
+  st = taylor_init(pb, mu0.data());
+  if (st != PIT_OK) {
+    set_error("exact initial state: unsupported problem size");
+    return st;
+  }
+  const size_t esz = (o.dtype == PIT_F32) ? sizeof(float) : sizeof(double);
+  if (want_cov)
+    PIT_CUDA_TRY(cudaMemsetAsync(a.sqrtcov, 0,
+                                 static_cast<size_t>(pb.N + 1) * Dfull * Dfull * esz, s));
+  char* lp = static_cast<char*>(a.workspace) + eng;
+  std::vector<SegSlot> slots(d);
+  for (int k = 0; k < d; ++k) {
+    st = e->set_component(k, pb, k, mu0.data() + static_cast<size_t>(k) * Q1, lp, lp + tb,
+                          a.mean, want_cov ? a.sqrtcov : nullptr, s);
+    if (st != PIT_OK) return st;
+    lp += 2 * tb;
+    slots[k] = SegSlot{k, 0, static_cast<int64_t>(k) * (pb.N + 1)};
+  }
+  st = e->init_traj(slots.data(), d, s);
+  if (st != PIT_OK) return st;
+  pit_solve_info info;
+  std::memset(&info, 0, sizeof(info));
+  std::vector<SegResult> res(d);
+  const int fixed = o.fixed_iters;
+  const int limit = fixed > 0 ? fixed : std::max(1, o.max_iter);
+  bool converged = fixed > 0;
+  int k = 0;
+  double s2sum = 0.0;
+  while (k < limit) {
+    st = e->pass(slots.data(), d, false, o.calibrate, res.data(), s);
+    if (st != PIT_OK) return st;
+    ++k;
+    double dmax = 0.0, ymax = 0.0;
+    unsigned flags = 0;
+    s2sum = 0.0;
+    for (int j = 0; j < d; ++j) {
+      dmax = std::max(dmax, res[j].delta_max);
+      ymax = std::max(ymax, res[j].y_max);
+      flags |= res[j].flags;
+      s2sum += res[j].sigma2_sum;
+    }
+    if ((flags & 1u) || !(dmax == dmax)) {
+      set_error("non-finite value in the smoothing means at iteration " + std::to_string(k));
+      return PIT_ENONFINITE;
+    }
+    info.last_delta = dmax;
+    if (k <= 64) info.deltas[k - 1] = dmax;
+    bool stop = (k == limit);
+    if (fixed <= 0 && dmax <= o.atol_delta + o.rtol_delta * ymax) {
+      converged = true;
+      stop = true;
+    }
+    if (stop) break;
+    for (auto& sl : slots) sl.cur ^= 1;
+  }
+  if (want_cov) {
+    st = e->pass(slots.data(), d, true, o.calibrate, res.data(), s);
+  } else {
+    st = e->export_means(slots.data(), d, s);
+  }
+  if (st != PIT_OK) return st;
+  PIT_CUDA_TRY(cudaStreamSynchronize(s));
+  info.iterations = k;
+  info.converged = converged ? 1 : 0;
+  info.sigma2 = o.calibrate ? s2sum / (static_cast<double>(pb.N) * d) : 1.0;
+  info.kernel_launches = launches_total() - launches0;
+  if (a.info) *a.info = info;
+  return converged ? PIT_OK : PIT_ENOCONV;
+}
+
 }  // namespace pit
 
 using namespace pit;
