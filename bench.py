@@ -45,7 +45,9 @@ def parse_args(argv=None):
     ap.add_argument("--dtype", choices=("f32", "f64"), default="f32")
     ap.add_argument("--max-iter", type=int, default=64)
     ap.add_argument("--atol", type=float, default=1e-10)
-    ap.add_argument("--chain-len", type=int, default=0)
+    ap.add_argument("--chain-len", type=int, default=-1,
+                    help="chain length of the scans; -1 (default) takes the autotuner's table "
+                         "(paper_2310_01145_gb300/tuning.json), 0 the library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
@@ -197,8 +199,12 @@ def run_pit(args):
     prob = W.fitzhugh_nagumo(N=args.N, q=args.q)
     tdt = torch.float32 if args.dtype == "f32" else torch.float64
     esz = 4 if args.dtype == "f32" else 8
+    variant, chain_len = 0, args.chain_len
+    if chain_len < 0:
+        from paper_2310_01145_gb300 import autotune
+        variant, chain_len = autotune.lookup(prob, args.dtype)
     opts = pit.make_opts(dtype=tdt, max_iter=args.max_iter, atol_delta=args.atol,
-                         chain_len=args.chain_len)
+                         chain_len=chain_len, variant=variant)
     ode = pit.ode_from_problem(prob)
     D = prob.D
     mean = torch.empty((prob.N + 1, D), dtype=tdt, device=dev)
@@ -349,6 +355,9 @@ def run_pit(args):
                                f"max|dy|<={args.atol:g} or {args.max_iter} iterations, "
                                f"calibrated covariances",
                    "iterations_per_solve": iters, "parallelism": f"replicas x{world}",
+                   "launch_shape": {"variant": variant, "chain_len": chain_len,
+                                    "source": "autotuner table" if args.chain_len < 0
+                                    else "command line"},
                    "l2": "working set (E, g, trajectories: >300 MB) exceeds the 129 MB L2; "
                          "no flush between steps"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

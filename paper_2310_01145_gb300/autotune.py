@@ -105,13 +105,17 @@ def main():
     ap.add_argument("--N", type=int, nargs="+", default=[2 ** 20])
     ap.add_argument("--dtype", default="f32")
     ap.add_argument("--iters", type=int, default=6)
+    ap.add_argument("--out", default=TABLE, help="tuning table to update (JSON)")
+    ap.add_argument("--chain-lens", type=int, nargs="+",
+                    default=[0, 16, 24, 32, 48, 64, 96, 128])
     args = ap.parse_args()
     make = {"fitzhugh_nagumo": W.fitzhugh_nagumo, "logistic": W.logistic,
             "van_der_pol": W.van_der_pol, "rigid_body": W.rigid_body,
             "lotka_volterra": lambda N, q: W.lotka_volterra(N=N, q=q)}[args.family]
     for N in args.N:
         p = make(N=N, q=args.q)
-        best = tune(p, args.dtype, iters=args.iters)
+        best = tune(p, args.dtype, path=args.out, iters=args.iters,
+                    chain_lens=tuple(args.chain_lens))
         print(json.dumps({"family": args.family, "q": args.q, "N": N, "dtype": args.dtype,
                           **best}))
 

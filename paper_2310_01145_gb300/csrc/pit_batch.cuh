@@ -462,6 +462,7 @@ class SegEngineImpl final : public SegEngine {
     p.want_cov = WITH_L ? 1 : 0;
     p.calibrate = calibrate;
     p.lin_mode = lin_mode_;
+    p.want_sigma = 1;
     p.sigma_pool = decoupled_ ? dec_d_ : 0;
     p.seg.desc = b_.desc;
     p.seg.inst_of = b_.inst_of;

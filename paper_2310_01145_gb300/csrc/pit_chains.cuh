@@ -246,12 +246,12 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     }
     // information part: G = sqrtS^-1 Htilde A';  J += G^T G (square root), eta += G^T sqrtS^-1 nu
     T znu[DD];
-    solve_sS<C>(u.sS, u.nu, znu);
+    solve_sS<C>(u.sS, u.rS, u.nu, znu);
     T Gt[1][RL][DD];
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       T z[DD];
-      solve_sS<C>(u.sS, HAcol[l], z);
+      solve_sS<C>(u.sS, u.rS, HAcol[l], z);
       T acc = eta[l];
 #pragma unroll
       for (int kk = 0; kk < DD; ++kk) {
@@ -563,9 +563,9 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 #pragma unroll
       for (int cc = 0; cc < D; ++cc) sP[l][cc] = (cc < W) ? sPn[l][cc < W ? cc : 0] : T(0);
     }
-    if (g.gl == 0) {
+    if (p.want_sigma && g.gl == 0) {
       T z[DD];
-      solve_sS<C>(u.sS, u.nu, z);
+      solve_sS<C>(u.sS, u.rS, u.nu, z);
       double s = 0.0;
 #pragma unroll
       for (int kk = 0; kk < DD; ++kk) s += static_cast<double>(z[kk]) * static_cast<double>(z[kk]);

@@ -106,6 +106,7 @@ struct IeksParams {
   double Tdiagd[kMaxQ1];
   SegView<T> seg;   // segmented solve: instance table and point -> instance map
   int lin_mode;     // Jacobian: 0 exact (EK1), 1 diagonal (DiagonalEK1), 2 zero (EK0)
+  int want_sigma;   // accumulate the quasi-MLE diffusion sum in this pass
   int sigma_pool;   // segmented: > 0 pools the diffusion sums of instances 0..sigma_pool-1
                     // (the components of one decoupled problem) into one sigma-hat
   double sqbd[kMaxQ1 * kMaxQ1];   // sqrt(Qbar) in FP64 (objective value)
@@ -146,6 +147,13 @@ struct SolveScalars {
   double objective;    // V of the trajectory (Eq. objective-value), when evaluated
 };
 
+#ifndef PIT_LDM_PAD
+#define PIT_LDM_PAD 0
+#endif
+#ifndef PIT_SCR_SHIFT
+#define PIT_SCR_SHIFT 0
+#endif
+
 template <typename T, int DD_, int Q1_, int G_, int RL_>
 struct Cfg {
   using Tp = T;
@@ -156,7 +164,8 @@ struct Cfg {
   static constexpr int G = G_;
   static constexpr int RL = RL_;
   static constexpr int RP = G_ * RL_;
-  static constexpr int LDM = D;
+  // row stride of published matrices (FP32: optionally padded against bank conflicts)
+  static constexpr int LDM = D + (sizeof(T) == 4 ? PIT_LDM_PAD : 0);
   // group scratch layout (elements of T)
   static constexpr int MAT0 = 0;
   static constexpr int MAT1 = MAT0 + RP * LDM;
@@ -167,8 +176,12 @@ struct Cfg {
   static constexpr int VEC3 = VEC2 + RP;
   static constexpr int SV = VEC3 + RP;
   static constexpr int PIV = SV + RoundUp<(DD_ * DD_ > 1 ? DD_ * DD_ : 1), 2>::value;
-  static constexpr int SCR =
+  static constexpr int SCR_RAW =
       RoundUp<PIV + 2 * ((2 * D > 4 * DD_ ? 2 * D : 4 * DD_) + 1), 4>::value;
+  // group scratch size; PIT_SCR_SHIFT makes consecutive groups start G banks apart
+  static constexpr int SCR = (PIT_SCR_SHIFT && sizeof(T) == 4)
+                                 ? RoundUp<SCR_RAW, 32>::value + G_
+                                 : SCR_RAW;
   // item sizes
   static constexpr int FA = 3 * D * D + 2 * D;   // filter element (A, b, C, eta, J)
   static constexpr int SA = 2 * D * D + D;       // smoothing element (E, g, L)
@@ -289,6 +302,7 @@ struct UpdateOut {
   using T = typename C::Tp;
   T K[C::RL][C::DD];
   T sS[C::DD][C::DD];
+  T rS[C::DD];   // reciprocals of sqrtS's diagonal
   T nu[C::DD];
 };
 
@@ -345,6 +359,8 @@ __device__ __forceinline__ void sqrt_update(const typename C::GR& g, typename C:
 #pragma unroll
     for (int b = 0; b < DD; ++b) u.sS[a][b] = (b <= a) ? scr[C::SV + a * DD + b] : T(0);
   g.sync();
+#pragma unroll
+  for (int a = 0; a < DD; ++a) u.rS[a] = recip<T>(u.sS[a][a]);
   // K = Psi21 sqrtS^-1 :  K[l] sqrtS = Psi21[l]  (backward substitution)
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
@@ -353,16 +369,17 @@ __device__ __forceinline__ void sqrt_update(const typename C::GR& g, typename C:
       T acc = U[1][l][c];
 #pragma unroll
       for (int k = c + 1; k < DD; ++k) acc -= u.K[l][k] * u.sS[k][c];
-      u.K[l][c] = acc / u.sS[c][c];
+      u.K[l][c] = acc * u.rS[c];
     }
 #pragma unroll
     for (int c = 0; c < C::W; ++c) sPnew[l][c] = U[1][l][DD + c];
   }
 }
 
-// Forward substitution with sqrtS: z = sqrtS^-1 x.
+// Forward substitution with sqrtS: z = sqrtS^-1 x (rS: reciprocals of its diagonal).
 template <class C>
 __device__ __forceinline__ void solve_sS(const typename C::Tp (&sS)[C::DD][C::DD],
+                                         const typename C::Tp (&rS)[C::DD],
                                          const typename C::Tp (&x)[C::DD],
                                          typename C::Tp (&z)[C::DD]) {
 #pragma unroll
@@ -370,7 +387,7 @@ __device__ __forceinline__ void solve_sS(const typename C::Tp (&sS)[C::DD][C::DD
     typename C::Tp acc = x[a];
 #pragma unroll
     for (int b = 0; b < a; ++b) acc -= sS[a][b] * z[b];
-    z[a] = acc / sS[a][a];
+    z[a] = acc * rS[a];
   }
 }
 

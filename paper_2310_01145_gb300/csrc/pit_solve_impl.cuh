@@ -408,6 +408,7 @@ struct SolverImpl {
     }
     p.N = pb.N;
     p.lin_mode = a.opts.linearization;
+    p.want_sigma = 1;
     p.L = a.opts.chain_len > 0 ? a.opts.chain_len : default_chain_len(pb.N);
     p.P = pb.N / p.L + 1;
     p.want_cov = want_cov;
@@ -515,8 +516,12 @@ struct SolverImpl {
   // One filter pass + smoother pass at trajectory `lin` (Algorithm 1 in the linearised model);
   // needs residuals(lin) to have run.
   template <bool WITH_L>
-  static int pass(const IeksParams<T>& p, const Buffers& b, const V* lin, V* lin_out,
+  static int pass(const IeksParams<T>& p_in, const Buffers& b, const V* lin, V* lin_out,
                   T* mean_out, T* cov_out, cudaStream_t s) {
+    // the diffusion sum is needed by the pass that reports it: the covariance pass, or every
+    // means pass of a solve without covariances (its last one is the final iteration)
+    IeksParams<T> p = p_in;
+    p.want_sigma = (WITH_L || !p.want_cov) ? 1 : 0;
     const unsigned grid = static_cast<unsigned>((p.P + NG - 1) / NG);
     const size_t sm = chain_smem();
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));

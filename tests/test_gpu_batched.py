@@ -122,7 +122,10 @@ def test_batched_alone_equals_in_mix(pit, dtype, tol, ctol):
     assert len(converged) >= 3
 
     def run(ps, **kw):
-        return pit.solve_problems_batched(ps, dtype=dtype, want_cov=True, **kw)
+        # non-converging instances of the mix may wander until their FP32 scans overflow; they
+        # are reported as diverged and do not affect the others
+        return pit.solve_problems_batched(ps, dtype=dtype, want_cov=True, allow_diverged=True,
+                                          **kw)
 
     # FP32: the higher derivatives of the full state are the least accurate components (their
     # preconditioned values grow like h^(i - q - 1/2)); at N ~ 3000 two FP32 evaluations of the
