@@ -47,10 +47,22 @@ __device__ __forceinline__ float recip<float>(float x) {
 #endif
 }
 
+#ifndef PIT_SQRT_MODE
+#define PIT_SQRT_MODE 2
+#endif
+
 template <typename T>
 __device__ __forceinline__ T dsqrt(T x);
+// FP32 square root of the reflections' norms: 1 = IEEE sqrtf, 2 = x * rsqrtf(x) (about 2 ulp;
+// the callers pass x in the safe range [1e-30, 1e30])
 template <>
-__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ float dsqrt<float>(float x) {
+#if PIT_SQRT_MODE == 2
+  return x * rsqrtf(x);
+#else
+  return sqrtf(x);
+#endif
+}
 template <>
 __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 

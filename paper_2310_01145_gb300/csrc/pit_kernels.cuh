@@ -319,19 +319,25 @@ __device__ __forceinline__ void sqrt_update(const typename C::GR& g, typename C:
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     const int r = g.row(l);
+    // observation row r of Htilde Lp (lanes holding rows r < d); rows >= d stay zero
+    const bool obs = r < DD;
+    const int kk = obs ? r : 0;
+    T Fr[DD];
+#pragma unroll
+    for (int m = 0; m < DD; ++m) {
+      T f = T(0);
+#pragma unroll
+      for (int j = 0; j < DD; ++j) f = (j == kk) ? Ft[j][m] : f;
+      Fr[m] = f;
+    }
+    const T* x1 = scr + C::MAT0 + (kk * C::Q1 + 1) * C::LDM;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       U[1][l][c] = Lp[l][c];
-      U[0][l][c] = T(0);
-    }
+      T v = x1[c];
 #pragma unroll
-    for (int kk = 0; kk < DD; ++kk) {
-      const bool mine = (r == kk);
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const T v = hrow_entry<C>(scr + C::MAT0, Ft, kk, c);
-        if (mine) U[0][l][c] = v;
-      }
+      for (int m = 0; m < DD; ++m) v -= Fr[m] * scr[C::MAT0 + (m * C::Q1) * C::LDM + c];
+      U[0][l][c] = obs ? v : T(0);
     }
   }
 #pragma unroll
