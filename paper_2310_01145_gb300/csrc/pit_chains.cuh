@@ -106,7 +106,10 @@ __device__ __forceinline__ const typename C::Tp* first_d0(const IeksParams<typen
   else return d0;
 }
 
-constexpr int kJBatch = 4;  // leaves whose information rows are folded into sqrtJ at once
+#ifndef PIT_JBATCH
+#define PIT_JBATCH 4
+#endif
+constexpr int kJBatch = PIT_JBATCH;  // leaves whose information rows are folded into sqrtJ at once
 
 // ---------------------------------------------------------------------------------------------
 // Filter reduce: chain c folds its leaves n = cL+1 .. min(cL+L, N) into the aggregate
