@@ -96,6 +96,7 @@ static void profile_flush() {
 struct Registry {
   std::mutex mu;
   std::map<int, SolveFn> solvers;  // key variant*100000 + dtype*10000 + d*100 + q
+  std::map<int, SolveFn> dense;    // key dtype
   std::map<int, ScanFn> fscans;    // key dtype*100 + D
   std::map<int, ScanFn> sscans;
 };
@@ -107,6 +108,17 @@ Registrar::Registrar(int dtype, int d, int q, int variant, SolveFn fn) {
   Registry& r = registry();
   std::lock_guard<std::mutex> lk(r.mu);
   r.solvers[variant * 100000 + dtype * 10000 + d * 100 + q] = fn;
+}
+DenseRegistrar::DenseRegistrar(int dtype, SolveFn fn) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.dense[dtype] = fn;
+}
+SolveFn find_dense_solver(int dtype) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.dense.find(dtype);
+  return it == r.dense.end() ? nullptr : it->second;
 }
 ScanRegistrar::ScanRegistrar(int dtype, int D, ScanFn f, ScanFn s) {
   Registry& r = registry();
@@ -634,7 +646,9 @@ static int32_t solve_common(const pit_ode* ode, const pit_grid* grid, int32_t q,
     set_error("variant 2 (decoupled components) needs an approximate Jacobian");
     return PIT_EINVAL;
   }
-  SolveFn fn = find_solver(a.opts.dtype, a.pb.d, q, a.opts.variant);
+  // the large-state solver: every d > 3 (exact Jacobian), and any d with variant 3
+  SolveFn fn = (a.pb.d > 3 || a.opts.variant == 3) ? find_dense_solver(a.opts.dtype)
+                                                   : find_solver(a.opts.dtype, a.pb.d, q, a.opts.variant);
   if (!fn) {
     set_error("no compiled kernels for this (dtype, d, q, variant); compiled: d in 1..3, q in 1..3 "
               "(d=3: q <= 2), variant 1 for D = d (q+1) in {6, 8}");

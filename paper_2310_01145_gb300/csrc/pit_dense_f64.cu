@@ -1,0 +1,9 @@
+// Large-state solver, FP64 arithmetic.
+#include "pit_dense_impl.cuh"
+
+namespace pit {
+namespace {
+int solve_dense_f64(const SolveArgs& a, size_t* w, bool e) { return dn::DenseSolver<double>::run(a, w, e); }
+DenseRegistrar reg_dense_f64(PIT_F64, solve_dense_f64);
+}  // namespace
+}  // namespace pit

@@ -93,12 +93,17 @@ using SolveFn = int (*)(const SolveArgs&, size_t* ws_query, bool eks);
 using ScanFn = int (*)(const ScanArgs&, size_t* ws_query);
 
 SolveFn find_solver(int dtype, int d, int q, int variant);
+// The large-state solver (pit_dense_impl.cuh): any family and d with D = d (q+1) <= 256, EK1.
+SolveFn find_dense_solver(int dtype);
 ScanFn find_filter_scan(int dtype, int D);
 ScanFn find_smooth_scan(int dtype, int D);
 
 // Registration (each instantiation file registers its functions at static-init time).
 struct Registrar {
   Registrar(int dtype, int d, int q, int variant, SolveFn fn);
+};
+struct DenseRegistrar {
+  DenseRegistrar(int dtype, SolveFn fn);
 };
 struct ScanRegistrar {
   ScanRegistrar(int dtype, int D, ScanFn filter_fn, ScanFn smooth_fn);

@@ -1,0 +1,159 @@
+"""GPU parity of the large-state solver (one thread block per chain, block-level dense tria and
+products; any d with D = d (q+1) <= 256) against the FP64 oracle, and against the lane-group
+kernels where both apply.
+
+Bars as in test_gpu_parity.py: FP64 means 1e-10 and covariances (S S^T) 1e-8 relative; FP32
+solution means 1e-5 and covariances 1e-3 at convergence.  Chain lengths are chosen so that the
+trees have padded levels and the chain that owns n = N sometimes has no leaves.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import workloads as W  # noqa: E402
+from oracle import ieks  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pit():
+    import paper_2310_01145_gb300 as P
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    P.load()
+    return P
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(1e-300, np.max(np.abs(b))))
+
+
+def cov(s):
+    return np.einsum("nij,nkj->nik", s, s)
+
+
+def _np(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("d,N,chain_len", [(8, 40, 0), (8, 41, 3), (16, 25, 4), (64, 12, 0),
+                                           (64, 13, 5)])
+def test_lorenz96_fixed_iterations_fp64(pit, d, N, chain_len):
+    """Lorenz-96 (d = 64: D = 192) per iteration against the oracle's sequential IEKS."""
+    p = W.lorenz96(d=d, N=N, q=2)
+    orc = ieks.ieks(p, fixed_iters=2, want_cov=True, calibrate=True)
+    r = pit.solve_problem(p, dtype=torch.float64, fixed_iters=2, want_cov=True,
+                          chain_len=chain_len)
+    torch.cuda.synchronize()
+    assert rel(_np(r.mean), orc.means) < 1e-10
+    assert rel(cov(_np(r.sqrtcov)), cov(orc.sqrtcovs)) < 1e-8
+    assert r.sigma2 == pytest.approx(orc.sigma2, rel=1e-9)
+
+
+@pytest.mark.parametrize("d,N", [(8, 300), (64, 40)])
+def test_lorenz96_converged(pit, d, N):
+    """Converged solves: FP64 takes the oracle's iterations and matches it; FP32 (scans on the
+    Gauss-Newton increment, double-float trajectory) matches it at the FP32 bars."""
+    p = W.lorenz96(d=d, N=N, q=2)
+    orc = ieks.ieks(p, atol=1e-10, max_iter=30, want_cov=True, calibrate=True)
+    r = pit.solve_problem(p, dtype=torch.float64, max_iter=30, want_cov=True)
+    r32 = pit.solve_problem(p, dtype=torch.float32, fixed_iters=orc.iterations + 2,
+                            want_cov=True)
+    torch.cuda.synchronize()
+    assert r.converged and r.iterations == orc.iterations
+    assert rel(_np(r.mean), orc.means) < 1e-10
+    assert rel(cov(_np(r.sqrtcov)), cov(orc.sqrtcovs)) < 1e-8
+    ys = slice(0, None, p.q + 1)
+    assert rel(_np(r32.mean)[:, ys], orc.means[:, ys]) < 1e-5
+    assert rel(cov(_np(r32.sqrtcov)), cov(orc.sqrtcovs)) < 1e-3
+
+
+@pytest.mark.parametrize("p,tm", [(W.fitzhugh_nagumo(N=301, q=3), 1e-9), (W.logistic(N=97, q=2), 1e-10),
+                                  (W.rigid_body(N=150, q=2), 1e-10), (W.van_der_pol(N=64, q=1), 1e-10)],
+                         ids=lambda x: getattr(x, "name", str(x)))
+def test_large_state_solver_equals_lane_group_kernels(pit, p, tm):
+    """variant 3 forces the large-state solver for d <= 3: the same iterates as the lane-group
+    kernels (and the oracle) in FP64.  FitzHugh-Nagumo's third iterate from the constant start
+    (values up to 1.5e4) carries the 1e-9 means bar of the element-scan parity tests."""
+    a = pit.solve_problem(p, dtype=torch.float64, fixed_iters=3, want_cov=True, variant=3)
+    b = pit.solve_problem(p, dtype=torch.float64, fixed_iters=3, want_cov=True)
+    torch.cuda.synchronize()
+    orc = ieks.ieks(p, fixed_iters=3, want_cov=True, calibrate=True)
+    for r in (a, b):
+        assert rel(_np(r.mean), orc.means) < tm
+        assert rel(cov(_np(r.sqrtcov)), cov(orc.sqrtcovs)) < 1e-8
+    for r in (a, b):
+        assert r.sigma2 == pytest.approx(orc.sigma2, rel=10 * tm)
+
+
+def test_affine_one_iteration_is_exact(pit):
+    """An affine ODE (d = 5, D = 10): the first iteration is the exact linear smoother, so the
+    second does not move it (Section 3.1)."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    d = 5
+    L = rng.standard_normal((d, d)) * 0.5 - np.eye(d)
+    p = W.affine(L, rng.standard_normal(d), rng.standard_normal(d), t1=2.0, N=33, q=1)
+    orc = ieks.ieks(p, fixed_iters=1, want_cov=True, calibrate=True)
+    r = pit.solve_problem(p, dtype=torch.float64, max_iter=2, atol_delta=0.0, want_cov=True,
+                          chain_len=4)
+    torch.cuda.synchronize()
+    assert r.iterations == 2
+    assert r.deltas[1] <= 1e-11 * np.max(np.abs(orc.means))
+    assert rel(_np(r.mean), orc.means) < 1e-10
+    assert rel(cov(_np(r.sqrtcov)), cov(orc.sqrtcovs)) < 1e-8
+
+
+@pytest.mark.parametrize("p,dtype,tm", [(W.lorenz96(d=8, N=30, q=2), torch.float64, 1e-10),
+                                        (W.lorenz96(d=64, N=12, q=2), torch.float64, 1e-10),
+                                        (W.lorenz96(d=16, N=200, q=2, F=0.5), torch.float32, 1e-5)],
+                         ids=["l96_d8_f64", "l96_d64_f64", "l96_d16_F05_f32"])
+def test_sequential_eks(pit, p, dtype, tm):
+    """The sequential EKS (local linearisation at the predicted mean, one block walking all
+    steps) against the oracle's.  The FP32 case uses the forcing F = 0.5, whose equilibrium is
+    stable: at F = 8 Lorenz-96 is chaotic and its linearisation at the initial state grows like
+    e^(8 t), so FP32 rounding of any solve is amplified far beyond 1e-5 (8.9e-5 on [0, 1], 1.7e-2
+    on [0, 5] against the FP64 oracle, measured on GB300)."""
+    from oracle import eks as oeks
+    ms, sPs, s2 = oeks.eks(p, calibrate=True)
+    r = pit.pit_eks_sequential(pit.ode_from_problem(p), p.y0, p.t0, p.t1, p.N, p.q,
+                               pit.make_opts(dtype=dtype))
+    torch.cuda.synchronize()
+    ys = slice(0, None, p.q + 1)
+    assert rel(_np(r.mean)[:, ys], ms[:, ys]) < tm
+    assert rel(cov(_np(r.sqrtcov)), cov(sPs)) < (1e-8 if dtype == torch.float64 else 1e-3)
+    assert r.sigma2 == pytest.approx(s2, rel=1e-8 if dtype == torch.float64 else 1e-3)
+
+
+def test_sequential_eks_equals_lane_group_kernels(pit):
+    p = W.fitzhugh_nagumo(N=200, q=3)
+    a = pit.pit_eks_sequential(pit.ode_from_problem(p), p.y0, p.t0, p.t1, p.N, p.q,
+                               pit.make_opts(dtype=torch.float64, variant=3))
+    b = pit.pit_eks_sequential(pit.ode_from_problem(p), p.y0, p.t0, p.t1, p.N, p.q,
+                               pit.make_opts(dtype=torch.float64))
+    torch.cuda.synchronize()
+    assert rel(_np(a.mean), _np(b.mean)) < 1e-10
+    assert rel(cov(_np(a.sqrtcov)), cov(_np(b.sqrtcov))) < 1e-8
+
+
+@pytest.mark.parametrize("N,nc", [(60, 15), (61, 61)])
+def test_coarse_initial_trajectory(pit, N, nc):
+    """Coarse-grid start (sequential EKS on nc steps, prior-mean interpolation) against the
+    oracle's, two IEKS iterations, Lorenz-96 d = 8."""
+    p = W.lorenz96(d=8, N=N, q=2)
+    orc = ieks.ieks(p, fixed_iters=2, want_cov=True, calibrate=True, coarse_n=nc)
+    r = pit.solve_problem(p, dtype=torch.float64, fixed_iters=2, want_cov=True, init_coarse=nc)
+    torch.cuda.synchronize()
+    assert rel(_np(r.mean), orc.means) < 1e-10
+    assert rel(cov(_np(r.sqrtcov)), cov(orc.sqrtcovs)) < 1e-8
+
+
+def test_large_state_rejections(pit):
+    p = W.lorenz96(d=8, N=10, q=2)
+    with pytest.raises(pit.PitError) as ei:
+        pit.solve_problem(p, dtype=torch.float64, objective=1)
+    assert ei.value.status == 8
+    with pytest.raises(pit.PitError) as ei:
+        pit.solve_problem(p, dtype=torch.float64, init_coarse=11)
+    assert ei.value.status == 1

@@ -192,10 +192,6 @@ def test_decoupled_lorenz96_first_iterations(pit, d, N):
 
 
 def test_decoupled_rejections(pit):
-    p = W.lorenz96(d=8, N=10, q=2)
-    with pytest.raises(pit.PitError) as ei:
-        pit.solve_problem(p, dtype=torch.float64)          # dense EK1 for d > 3: not compiled
-    assert ei.value.status == 8
     with pytest.raises(pit.PitError) as ei:
         pit.solve_problem(W.van_der_pol(N=10), dtype=torch.float64, variant=2)  # EK1 + variant 2
     assert ei.value.status == 1
