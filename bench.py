@@ -51,10 +51,17 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
-    ap.add_argument("--workload", choices=("fhn", "lv_batch", "serve", "sweep"), default="fhn",
+    ap.add_argument("--workload", choices=("fhn", "lv_batch", "serve", "sweep", "l96"),
+                    default="fhn",
                     help="fhn: the single-problem FitzHugh-Nagumo solve (default); lv_batch: "
                          "4096 Lotka-Volterra instances in one batched solve; serve: Poisson "
-                         "request streams through the continuous-batching server")
+                         "request streams through the continuous-batching server; l96: "
+                         "Lorenz-96 d=64 (D=192) on the large-state solver")
+    ap.add_argument("--l96-iters", type=int, default=3,
+                    help="l96: IEKS iterations per timed solve (fixed; the iteration does not "
+                         "converge from the constant trajectory at this grid size)")
+    ap.add_argument("--l96-N", type=int, default=16384)
+    ap.add_argument("--l96-dtype", choices=("f32", "f64"), default="f64")
     ap.add_argument("--rates", type=str, default="30,100,300,1000",
                     help="serve: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
@@ -492,21 +499,35 @@ def run_lv_batch(args):
 # time steps, FitzHugh-Nagumo IWP(3), FP32).  Valid only for the kernel sources it was taken on:
 # KERNEL_SOURCES_HASH is the hash of those sources, and the roofline's traffic is null when the
 # current sources differ.
-NCU_TRAFFIC_PER_STEP = {"filter_down": 136.53e6 / 524288, "filter_reduce": 25.25e6 / 524288}
-KERNEL_SOURCES_HASH = "9db45fbe6d2e622e"
+NCU_TRAFFIC_PER_STEP = {"filter_down": 135.792384e6 / 524288, "filter_reduce": 25.232128e6 / 524288}
+KERNEL_SOURCES_HASH = "056fbf6970c9c4bd"
+# The same for the large-state kernels of the Lorenz-96 workload (FP64, ncu at N = 2048;
+# profiles/k_ddown_k_dreduce_lorenz96_d64_N2048_f64_full.md).
+NCU_TRAFFIC_PER_STEP_L96 = {"filter_down": 11.977289e9 / 2048, "filter_reduce": 6.692363e9 / 2048}
+DENSE_SOURCES_HASH = "22579b40d4b576bc"
 
 
-def kernel_sources_hash() -> str:
+def kernel_sources_hash(files=("pit_group.cuh", "pit_ode.cuh", "pit_kernels.cuh",
+                               "pit_chains.cuh")) -> str:
     import hashlib
     base = os.path.join(ROOT, "paper_2310_01145_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("pit_group.cuh", "pit_ode.cuh", "pit_kernels.cuh", "pit_chains.cuh"):
+    for f in files:
         with open(os.path.join(base, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
+DENSE_FILES = ("pit_dense.cuh", "pit_dense_impl.cuh", "pit_ode.cuh")
+
+
 def _traffic(kernel: str, steps: int, D: int, dtype: str):
+    if kernel.startswith("l96_"):
+        k = kernel[4:]
+        if (k not in NCU_TRAFFIC_PER_STEP_L96 or dtype != "f64"
+                or kernel_sources_hash(DENSE_FILES) != DENSE_SOURCES_HASH):
+            return None
+        return NCU_TRAFFIC_PER_STEP_L96[k] * steps
     if (kernel not in NCU_TRAFFIC_PER_STEP or D != 8 or dtype != "f32"
             or kernel_sources_hash() != KERNEL_SOURCES_HASH):
         return None
@@ -733,6 +754,192 @@ def run_sweep(args):
     print(json.dumps(out))
 
 
+# ---- Lorenz-96 d = 64 on the large-state solver -------------------------------------------------
+def oracle_l96_sample(N_full: int, N_sample: int) -> dict:
+    """One IEKS iteration of the FP64 oracle on the first N_sample steps of the Lorenz-96 grid
+    (same step size), single-threaded, in a child process."""
+    code = f"""
+import sys, time, json, dataclasses
+sys.path.insert(0, {ROOT!r})
+import workloads as W
+from oracle import ieks
+p = W.lorenz96(d=64, N={N_full}, q=2)
+p = dataclasses.replace(p, N={N_sample}, t1=p.t0 + p.h * {N_sample})
+t = time.perf_counter()
+ieks.ieks(p, fixed_iters=1, want_cov=False, calibrate=False)
+print(json.dumps({{"seconds": time.perf_counter() - t, "steps": {N_sample}}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_l96(args):
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+    from paper_2310_01145_gb300 import roofline
+    import workloads as W
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    prob = W.lorenz96(d=64, N=args.l96_N, q=2)
+    f64 = args.l96_dtype == "f64"
+    tdt = torch.float64 if f64 else torch.float32
+    esz = 8 if f64 else 4
+    K = args.l96_iters
+    opts = pit.make_opts(dtype=tdt, fixed_iters=K, want_cov=False, calibrate=True)
+    ode = pit.ode_from_problem(prob)
+    D, d, Q1 = prob.D, prob.d, prob.q + 1
+    mean = torch.empty((prob.N + 1, D), dtype=tdt, device=dev)
+    import ctypes
+    lib = pit.load()
+    sz = ctypes.c_size_t(0)
+    c_ode, c_grid = ode.c(), pit._Grid(prob.t0, prob.t1, prob.N)
+    lib.pit_solve_workspace_size(ctypes.byref(c_ode), ctypes.byref(c_grid), prob.q,
+                                 ctypes.byref(opts), ctypes.byref(sz))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return pit.pit_solve(ode, prob.y0, prob.t0, prob.t1, prob.N, prob.q, opts,
+                             workspace=ws, out=(mean, None), stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pit.pit_profile_reset()
+    pit.pit_profile_enable(True)
+    launches0 = pit.pit_launch_count()
+    work = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            work += prob.N * r.iterations
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = pit.pit_launch_count() - launches0
+    pit.pit_profile_enable(False)
+    prof = pit.pit_profile_read()
+    ms_local = e0.elapsed_time(e1)
+    ms = reduce_max(ms_local, world, dev)
+    value = reduce_sum(float(work), world, dev) / (ms / 1e3)
+    clocks = clk.summary()
+
+    # end to end: the means copied to pinned host memory every solve
+    host_mean = torch.empty(mean.shape, dtype=tdt, pin_memory=True)
+    h2d = (prob.params.size + prob.y0.size) * 8
+    d2h = host_mean.numel() * esz
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    work_e2e = 0
+    for _ in range(args.steps):
+        r = step()
+        host_mean.copy_(mean, non_blocking=True)
+        torch.cuda.synchronize()
+        work_e2e += prob.N * r.iterations
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e_value = reduce_sum(float(work_e2e), world, dev) / t_e2e
+
+    # roofline of the dominant kernel: algorithmic flops of the chain step it runs per time step
+    shares = {k: v for k, v in prof.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in shares.values())
+    dom = max(shares, key=lambda k: shares[k][0])
+    dom_ms, dom_n = shares[dom]
+    fl = (roofline.filter_down_flops(D, d, Q1) if dom == "filter_down"
+          else roofline.filter_reduce_flops(D, d, Q1))
+    achieved = fl * prob.N / (dom_ms / dom_n / 1e3) / 1e12
+    peak = roofline.fp64_alu_peak_tflops() if f64 else roofline.fp32_alu_peak_tflops()
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": _traffic("l96_" + dom, prob.N, D, args.l96_dtype),
+            "traffic_source": "ncu dram bytes read+written per launch (profiles/); null if the "
+                              "kernels changed",
+            "peak_source": ("nominal: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz" if f64 else
+                            "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+            "algorithmic_flops_per_step": fl}
+    kernel_shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                         "share": v[0] / total_ms} for k, v in shares.items()}
+
+    # the sequential EKS on the same GPU and dtype, on the first steps of the same grid
+    eks = None
+    if rank == 0 and not args.no_eks:
+        ne = min(prob.N, 1024)
+        eopts = pit.make_opts(dtype=tdt, want_cov=False)
+        t1s = prob.t0 + prob.h * ne
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pit.pit_eks_sequential(ode, prob.y0, prob.t0, t1s, ne, prob.q, eopts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eks_ms = e0.elapsed_time(e1)
+        eks = {"value": ne / (eks_ms / 1e3), "unit": "steps/s", "steps": ne,
+               "ms": eks_ms,
+               "what": f"sequential EKS (one block, strictly in time order) on the first {ne} "
+                       f"steps of the same grid, same dtype; its time grows linearly in N",
+               "parallel_ms_per_iteration": ms_local / args.steps / K}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            smp = oracle_l96_sample(prob.N, 256)
+            cpu = {"value": smp["steps"] / smp["seconds"], "unit": UNIT, "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"1 IEKS iteration of the FP64 numpy oracle on the first "
+                             f"{smp['steps']} of the {prob.N} steps (same h), single thread, "
+                             f"{smp['seconds']:.1f} s"}
+        except Exception as exc:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"failed: {exc}"[:300]}
+
+    out = {
+        "metric": "IEKS steps*iterations/s (Lorenz-96 d=64, IWP(2), D=192)", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.l96_dtype, "data": "synthetic",
+        "config": {"workload": f"Lorenz-96 d=64, F=8, y0=F+0.01 N(0,1) (seed 0), t in [0,5], "
+                               f"IWP(2) D=192, N={prob.N}, {K} IEKS iterations per solve from "
+                               f"the constant trajectory, means and diffusion estimate",
+                   "parallelism": f"replicas x{world}",
+                   "precision_note": ("FP64: on this chaotic workload the FP32 parallel scans lose "
+                                      "all accuracy (the filtering elements carry the flow map "
+                                      "over long spans, growing like e^(8 t)); FP64 follows the "
+                                      "oracle" if f64 else
+                                      "FP32 kernel speed only: results on this workload are not "
+                                      "accurate in FP32"),
+                   "l2": "working set (E: 2.4 GB per iteration in FP32) exceeds the 129 MB L2"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_shares": kernel_shares,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "sequential_eks_gpu": eks,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -743,6 +950,8 @@ def main(argv=None):
         run_serve(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "l96":
+        run_l96(args)
     else:
         run_pit(args)
 

@@ -35,6 +35,13 @@
 #include "pit_internal.h"
 
 namespace pit {
+
+// FP32 values of the vector field for the sequential EKS's local linearisation
+template <>
+__device__ __forceinline__ float v_from_double<float>(double x) {
+  return static_cast<float>(x);
+}
+
 namespace dn {
 
 constexpr int kMaxDenseD = 256;
@@ -65,6 +72,18 @@ struct DenseParams {
 };
 
 // ---- per-step model inputs ------------------------------------------------------------------
+// Component k of the vector field in number type V, the state read through y(j): the affine
+// family for any d here, every other family through component_f.
+template <typename V, typename T, typename Get>
+__device__ __forceinline__ V dense_f(int kind, const double* pd, int d, int k, Get y) {
+  if (kind == 4 && d > 3) {  // y' = L y + c, params [L (d x d), c (d)]
+    V acc = v_from_double<V>(pd[d * d + k]);
+    for (int j = 0; j < d; ++j) acc = acc + v_from_double<V>(pd[k * d + j]) * y(j);
+    return acc;
+  }
+  return component_f<V, T>(kind, pd, d, k, y);
+}
+
 // Jacobian of the vector field at y (original coordinates), entry (i, j), arithmetic type T.
 template <typename T, int DD>
 __device__ __forceinline__ T small_jac(const DenseParams<T>& p, const T* y, int i, int j) {
@@ -296,7 +315,7 @@ k_dres(const DenseParams<T> p, const Vt<T>* __restrict__ lin, T* __restrict__ U,
         U[n * D + k * Q1 + i] = v_to_T<T>(acc);
       }
     }
-    const V fk = component_f<V, T>(p.kind, p.pd, d, k, [&](int j) { return T0v * x[j * Q1]; });
+    const V fk = dense_f<V, T>(p.kind, p.pd, d, k, [&](int j) { return T0v * x[j * Q1]; });
     Yv[n * d + k] = v_to_T<T>(T0v * x[k * Q1]);
     R[n * d + k] = v_to_T<T>(fk * T1iv - x[k * Q1 + 1]);
     if (n == 0)
@@ -711,7 +730,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
       __syncthreads();
       cta_jacobian<T>(p, y, Ft);
       for (int k = threadIdx.x; k < d; k += NT) {
-        T acc = component_f<T, T>(p.kind, p.pd, d, k, [&](int j) { return y[j]; });
+        T acc = dense_f<T, T>(p.kind, p.pd, d, k, [&](int j) { return y[j]; });
         for (int j = 0; j < d; ++j) acc -= jac_entry<T>(p, y, k, j) * y[j];
         rr[k] = acc * p.T1inv;
       }

@@ -178,8 +178,6 @@ __device__ __forceinline__ V v_from_double(double x);
 template <>
 __device__ __forceinline__ double v_from_double<double>(double x) { return x; }
 template <>
-__device__ __forceinline__ float v_from_double<float>(double x) { return static_cast<float>(x); }
-template <>
 __device__ __forceinline__ df32 v_from_double<df32>(double x) {
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - static_cast<double>(h))};
@@ -307,11 +305,6 @@ __device__ __forceinline__ V component_f(int kind, const double* pd, int d, int 
   if (kind == 3) {  // Lorenz-96: (y_{k+1} - y_{k-2}) y_{k-1} - y_k + F
     const V a = y((k + 1) % d), b = y((k - 2 + d) % d), c = y((k - 1 + d) % d);
     return (a - b) * c - y(k) + v_from_double<V>(pd[0]);
-  }
-  if (kind == 4 && d > 3) {  // affine, y' = L y + c with params [L (d x d), c (d)]
-    V acc = v_from_double<V>(pd[d * d + k]);
-    for (int j = 0; j < d; ++j) acc = acc + v_from_double<V>(pd[k * d + j]) * y(j);
-    return acc;
   }
   OdeParams<T> P;
   P.kind = kind;

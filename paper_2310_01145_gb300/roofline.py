@@ -42,7 +42,9 @@ def filter_down_flops(D: int, d: int, Q1: int, with_cov: bool = False) -> float:
     W = D - d
     fma = 0
     fma += _phi_fma(D, d, Q1, D) + _phi_fma(D, d, Q1, 1)           # Phi sqrtP, Phi m (+ u)
-    fma += _lq_tri_ext_fma(D, D, rows_other=D)                       # Pi: [sqrtQ | Phi sqrtP] / [0 | sqrtP]
+    # Pi: [sqrtQ | Phi sqrtP] / [0 | sqrtP]; sqrtP has W columns after an update (only the first
+    # step of a chain starts from the tree's D-column prefix factor, 1 step in L)
+    fma += _lq_tri_ext_fma(D, W, rows_other=D)
     fma += D * D * (D - 1) // 2 + D * D                              # E = Pi21 Pi11^-1 (back subst.)
     fma += D * D                                                     # g = m - E m-
     fma += D * D * D + D * D                                         # aggregate E~ E, x += E~ g
@@ -112,3 +114,10 @@ def fp32_alu_peak_tflops(sm_count: int = 152, fp32_lanes_per_sm: int = 128,
                          clock_mhz: float = 2070.0) -> float:
     """Nominal FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock."""
     return sm_count * fp32_lanes_per_sm * 2.0 * clock_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_count: int = 152, fma_per_clk_per_sm: int = 2,
+                         clock_mhz: float = 2070.0) -> float:
+    """Nominal FP64 peak of GB300 (its FP64 rate is cut to 1.25 TFLOP/s): SMs x FP64 FMA per
+    clock x 2 flops x clock."""
+    return sm_count * fma_per_clk_per_sm * 2.0 * clock_mhz * 1e6 / 1e12
