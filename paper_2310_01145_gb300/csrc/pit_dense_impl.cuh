@@ -46,6 +46,7 @@ namespace dn {
 
 constexpr int kMaxDenseD = 256;
 constexpr int kJBatchDense = 2;  // information rows of kJ steps are folded into sqrtJ at once
+constexpr int kTreeGroup = 8;    // chain aggregates combined by tree levels before the look-back
 
 template <typename T>
 struct DenseParams {
@@ -617,6 +618,52 @@ k_dtree_level(const DenseParams<T> p, T* __restrict__ items, int64_t s, T* __res
   }
 }
 
+// Look-back across groups of G tree positions.  After the up-sweep inside the groups, position
+// (g+1) G - 1 holds group g's total; one block walks the groups in order, stores each group's
+// exclusive prefix at that position (the root of the group's down-sweep) and extends the running
+// prefix with the group's total (values-only for the filter).  Applying a short-span aggregate
+// to a running prefix is conditioned like the sequential filter; tree levels above the groups
+// would instead form elements whose flow maps span up to the whole interval, whose rounding
+// strongly unstable linearisations amplify.  pre, tot: two item-sized buffers.
+template <typename T, bool FILTER, bool WITH_L>
+__global__ void __launch_bounds__(NT, 1)
+k_dtree_seq(const DenseParams<T> p, T* __restrict__ items, int64_t G, int64_t ngroups,
+            T* __restrict__ pre, T* __restrict__ tot, T* __restrict__ scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int D = p.D;
+  const int64_t P = p.P;
+  const int64_t sz = FILTER ? fitem(D) : sitem(D);
+  const TreeLayout tl(D);
+  T* res = scratch + tl.out;
+  for (int64_t e = threadIdx.x; e < sz; e += NT) {
+    T v = T(0);
+    if (e < static_cast<int64_t>(D) * D) v = (e / D == e % D) ? T(1) : T(0);
+    pre[e] = v;
+  }
+  __syncthreads();
+  for (int64_t g = 0; g < ngroups; ++g) {
+    const int64_t pos = (g + 1) * G - 1;
+    if (pos - G + 1 >= P) break;  // this group and all later ones are padding
+    T* root = items + tree_idx(pos, P, !FILTER) * sz;
+    for (int64_t e = threadIdx.x; e < sz; e += NT) {
+      tot[e] = root[e];
+      root[e] = pre[e];
+    }
+    __syncthreads();
+    if (pos + 1 >= P) break;      // no later group holds a chain
+    if (FILTER) {
+      dcombine_f<T, true>(p, pre, tot, res, scratch, sm);
+      const int64_t DD = static_cast<int64_t>(D) * D;
+      for (int64_t e = threadIdx.x; e < DD + D; e += NT) pre[DD + e] = res[DD + e];
+    } else {
+      dcombine_s<T, WITH_L>(p, tot, pre, res, scratch, sm);
+      for (int64_t e = threadIdx.x; e < sz; e += NT) pre[e] = res[e];
+    }
+    __syncthreads();
+  }
+}
+
 // Filter down: chain c starts from its exclusive prefix (the filtering marginal at n = cL; chain
 // 0 from the initial state) and runs square-root Kalman steps; step n emits the smoothing element
 // b_{n-1} and folds it into the chain's smoothing aggregate; the chain owning n = N also emits
@@ -926,7 +973,7 @@ struct DenseSolver {
     V *linA, *linB;
     T *U, *R, *Yv, *d0;
     T *Es, *gs, *Ls;
-    T *fagg, *sagg, *scratch;
+    T *fagg, *sagg, *scratch, *seq;
     SolveScalars* scal;
     double* pd;
     T* pt;
@@ -1010,6 +1057,7 @@ struct DenseSolver {
     b.fagg = cv.take<T>(P2 * fitem(p.D));
     b.sagg = cv.take<T>(P2 * sitem(p.D));
     b.scratch = cv.take<T>(std::max<int64_t>(p.P, P2 / 2) * p.chain_elems);
+    b.seq = cv.take<T>(2 * fitem(p.D));
     b.scal = cv.take<SolveScalars>(1);
     b.pd = cv.take<double>(std::max(1, a.pb.n_params));
     b.pt = cv.take<T>(std::max(1, a.pb.n_params));
@@ -1036,23 +1084,30 @@ struct DenseSolver {
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_level<T, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_level<T, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_level<T, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_seq<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_seq<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_dtree_seq<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
     return PIT_OK;
   }
 
+  // Chain-aggregate scan: Brent-Kung up-sweep inside groups of kTreeGroup positions, a
+  // sequential look-back over the group totals (k_dtree_seq), Blelloch down-sweep inside groups.
   template <bool FILTER, bool WITH_L>
-  static int tree(const DenseParams<T>& p, T* items, T* scratch, size_t sm, cudaStream_t s) {
+  static int tree(const DenseParams<T>& p, T* items, T* seq, T* scratch, size_t sm,
+                  cudaStream_t s) {
     const int64_t P2 = pow2_at_least(p.P);
+    const int64_t G = std::min<int64_t>(P2, kTreeGroup);
     const int kc = FILTER ? KC_TREE_FILTER_UP : KC_TREE_SMOOTH_UP;
     const int kd = FILTER ? KC_TREE_FILTER_DOWN : KC_TREE_SMOOTH_DOWN;
     if (P2 > p.P)
       PIT_LAUNCH(kc, s, (k_dtree_neutral<T, FILTER><<<static_cast<unsigned>(std::min<int64_t>(P2 - p.P, 1024)), NT, 0, s>>>(p, items, p.P, P2)));
-    for (int64_t st = 1; st < P2; st *= 2) {
+    for (int64_t st = 1; st < G; st *= 2) {
       const unsigned grid = static_cast<unsigned>(P2 / (2 * st));
       PIT_LAUNCH(kc, s, (k_dtree_level<T, FILTER, true, WITH_L><<<grid, NT, sm, s>>>(p, items, st, scratch)));
     }
-    // root of the down-sweep: the neutral element
-    PIT_LAUNCH(kd, s, (k_dtree_neutral<T, FILTER><<<1, NT, 0, s>>>(p, items, FILTER ? P2 - 1 : (P2 - 1 < p.P ? 0 : P2 - 1), FILTER ? P2 : (P2 - 1 < p.P ? 1 : P2))));
-    for (int64_t st = P2 / 2; st >= 1; st /= 2) {
+    const int64_t fs = fitem(p.D);
+    PIT_LAUNCH(kd, s, (k_dtree_seq<T, FILTER, WITH_L><<<1, NT, sm, s>>>(p, items, G, P2 / G, seq, seq + fs, scratch)));
+    for (int64_t st = G / 2; st >= 1; st /= 2) {
       const unsigned grid = static_cast<unsigned>(P2 / (2 * st));
       PIT_LAUNCH(kd, s, (k_dtree_level<T, FILTER, false, WITH_L><<<grid, NT, sm, s>>>(p, items, st, scratch)));
     }
@@ -1069,12 +1124,12 @@ struct DenseSolver {
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
     PIT_LAUNCH(KC_FILTER_REDUCE, s,
                (k_dreduce<T><<<grid, NT, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg, b.scratch)));
-    int st = tree<true, false>(p, b.fagg, b.scratch, sm, s);
+    int st = tree<true, false>(p, b.fagg, b.seq, b.scratch, sm, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_FILTER_DOWN, s,
                (k_ddown<T, WITH_L><<<grid, NT, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg, b.Es, b.gs,
                                                        b.Ls, b.sagg, b.scal, b.scratch)));
-    st = tree<false, WITH_L>(p, b.sagg, b.scratch, sm, s);
+    st = tree<false, WITH_L>(p, b.sagg, b.seq, b.scratch, sm, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_SMOOTH_DOWN, s,
                (k_dsmooth<T, WITH_L><<<grid, NT, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin, lin_out,

@@ -187,17 +187,18 @@ def test_lorenz96_full_size_kernels(pit, N):
     assert r.sigma2 == pytest.approx(float(g["sigma2"]), rel=1e-9)
 
 
-@pytest.mark.parametrize("N,bar", [(4096, 1e-5), (16384, 1e-3)])
-def test_lorenz96_full_size_parallel_shape(pit, N, bar):
-    """The same first iterate in the benchmark's launch shape (152 chains and the trees).  On this
-    chaotic workload the linearisation at the initial state grows like e^(8 t): the tree combines
-    of chain aggregates spanning most of [0, 5] carry flow maps of that size, and FP64 rounding in
-    them is amplified far beyond the sequential filter's (measured 2.7e-6 at N = 4096, 2.9e-4 at
-    N = 16384; one chain gives 4e-11, test above).  The bars state that conditioning limit."""
+@pytest.mark.parametrize("N", [4096, 16384])
+def test_lorenz96_full_size_parallel_shape(pit, N):
+    """The same first iterate in the benchmark's launch shape (about one chain per SM, the chain
+    aggregates combined by tree levels inside groups of 8 and a sequential look-back across the
+    groups).  On this chaotic workload (linearisation growing like e^(8 t)) a tree over all
+    chains combined elements whose flow maps spanned most of [0, 5] and missed the oracle by
+    2.7e-6 (N = 4096) and 2.9e-4 (N = 16384); with span-limited combines the parallel result
+    keeps the FP64 bar."""
     g = _golden(N)
     p = W.lorenz96(d=64, N=N, q=2)
     r = pit.solve_problem(p, dtype=torch.float64, max_iter=1, atol_delta=0.0, want_cov=False)
     torch.cuda.synchronize()
-    assert rel(_np(r.mean)[g["n"]], g["means"]) < bar
-    assert r.deltas[0] == pytest.approx(float(g["delta"]), rel=bar)
-    assert r.sigma2 == pytest.approx(float(g["sigma2"]), rel=bar)
+    assert rel(_np(r.mean)[g["n"]], g["means"]) < 1e-10
+    assert r.deltas[0] == pytest.approx(float(g["delta"]), rel=1e-10)
+    assert r.sigma2 == pytest.approx(float(g["sigma2"]), rel=1e-9)
