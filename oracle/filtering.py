@@ -49,10 +49,17 @@ def update(m_pred, sP_pred, H, dvec):
     return m_pred - K @ r, Psi22, sS, r
 
 
+def step_matrix(M, n):
+    """Transition quantity of step n (from t_{n-1} to t_n): M itself on a uniform grid, M[n]
+    when M is a per-step list (index 0 unused) on a non-uniform grid."""
+    return M[n] if isinstance(M, (list, tuple)) else M
+
+
 def sequential_filter(mu0, sSigma0, Phi, sQ, Hs, ds):
     """Filter marginals n = 0..N (n = 0 is the initial distribution).
 
-    Hs[n], ds[n] for n = 1..N (index 0 unused).  Returns mf (N+1, D), sPf (N+1, D, D),
+    Hs[n], ds[n] for n = 1..N (index 0 unused); Phi, sQ one matrix each (uniform grid) or
+    per-step lists (Phi[n], sQ[n] for the step into t_n).  Returns mf (N+1, D), sPf (N+1, D, D),
     sS (N+1, d, d) and residuals r (N+1, d) (index 0 unused)."""
     N = len(Hs) - 1
     D = mu0.shape[0]
@@ -64,13 +71,14 @@ def sequential_filter(mu0, sSigma0, Phi, sQ, Hs, ds):
     mf[0] = mu0
     sPf[0] = sSigma0
     for n in range(1, N + 1):
-        mp, sPp = predict(mf[n - 1], sPf[n - 1], Phi, sQ)
+        mp, sPp = predict(mf[n - 1], sPf[n - 1], step_matrix(Phi, n), step_matrix(sQ, n))
         mf[n], sPf[n], sS[n], res[n] = update(mp, sPp, Hs[n], ds[n])
     return mf, sPf, sS, res
 
 
 def rts_smoother(mf, sPf, Phi, sQ):
-    """Square-root Rauch-Tung-Striebel smoother (backward pass over n = N-1..0)."""
+    """Square-root Rauch-Tung-Striebel smoother (backward pass over n = N-1..0); Phi, sQ as in
+    sequential_filter."""
     N = mf.shape[0] - 1
     D = mf.shape[1]
     ms = np.zeros_like(mf)
@@ -78,10 +86,11 @@ def rts_smoother(mf, sPf, Phi, sQ):
     ms[N] = mf[N]
     sPs[N] = sPf[N]
     for n in range(N - 1, -1, -1):
-        Pi = tria(np.block([[Phi @ sPf[n], sQ], [sPf[n], np.zeros((D, D))]]))
+        F, sq = step_matrix(Phi, n + 1), step_matrix(sQ, n + 1)
+        Pi = tria(np.block([[F @ sPf[n], sq], [sPf[n], np.zeros((D, D))]]))
         Pi11, Pi21, Pi22 = Pi[:D, :D], Pi[D:, :D], Pi[D:, D:]
         G = right_solve(Pi21, Pi11)
-        ms[n] = mf[n] + G @ (ms[n + 1] - Phi @ mf[n])
+        ms[n] = mf[n] + G @ (ms[n + 1] - F @ mf[n])
         sPs[n] = tria(np.hstack([G @ sPs[n + 1], Pi22]))
     return ms, sPs
 

@@ -17,26 +17,38 @@ from .taylor import initial_state
 
 
 def dense_posterior(problem):
+    """Works on uniform and non-uniform grids: step k (into t_k) has its own Phi_k, Q_k, and
+    Y_n = Phi_n ... Phi_1 Y_0 + sum_{k <= n} Phi_n ... Phi_{k+1} w_k."""
     d, q, N, D = problem.d, problem.q, problem.N, problem.D
-    Phi, Q = iwp_transition(q, problem.h, d)
+    steps = problem.steps
+    Phis, Qs = [None], [None]
+    for h in steps:
+        Phi, Q = iwp_transition(q, float(h), d)
+        Phis.append(Phi)
+        Qs.append(Q)
     mu0 = initial_state(problem.kind, problem.params, problem.y0, q)
     L = problem.params[: d * d].reshape(d, d)
     c = problem.params[d * d: d * d + d]
     H = projection(1, q, d) - L @ projection(0, q, d)
+
+    def flow(n, k):
+        """Phi_n ... Phi_{k+1} (identity for n == k)."""
+        M = np.eye(D)
+        for j in range(k + 1, n + 1):
+            M = Phis[j] @ M
+        return M
+
     # prior mean and covariance of the stacked state [Y_0, ..., Y_N]
     n_tot = (N + 1) * D
     mean = np.zeros(n_tot)
     cov = np.zeros((n_tot, n_tot))
-    Phip = [np.eye(D)]
-    for k in range(1, N + 1):
-        Phip.append(Phi @ Phip[-1])
     for n in range(N + 1):
-        mean[n * D:(n + 1) * D] = Phip[n] @ mu0
+        mean[n * D:(n + 1) * D] = flow(n, 0) @ mu0
     for n in range(N + 1):
         for m in range(N + 1):
             acc = np.zeros((D, D))
-            for k in range(min(n, m)):
-                acc += Phip[n - 1 - k] @ Q @ Phip[m - 1 - k].T
+            for k in range(1, min(n, m) + 1):
+                acc += flow(n, k) @ Qs[k] @ flow(m, k).T
             cov[n * D:(n + 1) * D, m * D:(m + 1) * D] = acc
     # constraints B Y = rhs
     B = np.zeros((N * d, n_tot))

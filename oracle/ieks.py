@@ -67,7 +67,7 @@ def linearize(kind, params, eta_n, t, q, d, mode: str = "ek1"):
 
 def linearize_all(problem, traj, mode: str = "ek1"):
     d, q = problem.d, problem.q
-    ts = problem.t0 + problem.h * np.arange(problem.N + 1)
+    ts = problem.times
     Hs = [None]
     ds = [None]
     for n in range(1, problem.N + 1):
@@ -78,9 +78,19 @@ def linearize_all(problem, traj, mode: str = "ek1"):
 
 
 def prior_factors(problem):
-    Phi, Q = iwp_transition(problem.q, problem.h, problem.d)
-    sQ = np.linalg.cholesky(Q)
-    return Phi, Q, sQ
+    """Phi, Q, sqrt(Q) of the IWP prior (Section 2.1): one triple on a uniform grid; per-step
+    lists (index n = 1..N for the step into t_n, index 0 unused) on a non-uniform grid."""
+    if problem.uniform:
+        Phi, Q = iwp_transition(problem.q, problem.h, problem.d)
+        sQ = np.linalg.cholesky(Q)
+        return Phi, Q, sQ
+    Phis, Qs, sQs = [None], [None], [None]
+    for h in problem.steps:
+        Phi, Q = iwp_transition(problem.q, float(h), problem.d)
+        Phis.append(Phi)
+        Qs.append(Q)
+        sQs.append(np.linalg.cholesky(Q))
+    return Phis, Qs, sQs
 
 
 def linear_smoother(problem, traj, mu0, Phi, sQ, want_cov=True, mode: str = "ek1"):
@@ -103,9 +113,10 @@ def sigma2_hat(sS, res, N, d):
 
 def objective(traj, Phi, sQ):
     """V(eta_0:N) = 1/2 sum_n || eta_n - Phi eta_{n-1} ||^2_{Q^-1}  (Eq. objective-value)."""
+    from .filtering import step_matrix
     tot = 0.0
     for n in range(1, traj.shape[0]):
-        z = solve_lower(sQ, traj[n] - Phi @ traj[n - 1])
+        z = solve_lower(step_matrix(sQ, n), traj[n] - step_matrix(Phi, n) @ traj[n - 1])
         tot += float(z @ z)
     return 0.5 * tot
 

@@ -49,6 +49,8 @@ class Problem:
     t0, t1  -- time interval
     N       -- number of steps; the grid is t_n = t0 + n (t1 - t0) / N, n = 0..N
     q       -- order of the integrated-Wiener-process prior (the paper's nu)
+    ts      -- optional non-uniform grid t_0 = t0 < t_1 < ... < t_N = t1 (float64, N+1 values);
+               None means the uniform grid above
     """
 
     kind: int
@@ -59,6 +61,25 @@ class Problem:
     t1: float
     N: int
     q: int
+    ts: np.ndarray | None = None
+
+    @property
+    def uniform(self) -> bool:
+        return self.ts is None
+
+    @property
+    def times(self) -> np.ndarray:
+        """Grid points t_0 .. t_N."""
+        if self.ts is not None:
+            return np.asarray(self.ts, dtype=np.float64)
+        return self.t0 + self.h * np.arange(self.N + 1)
+
+    @property
+    def steps(self) -> np.ndarray:
+        """Step lengths h_n = t_n - t_{n-1}, n = 1..N (index 0 of the returned array is h_1)."""
+        if self.ts is not None:
+            return np.diff(np.asarray(self.ts, dtype=np.float64))
+        return np.full(self.N, self.h)
 
     @property
     def D(self) -> int:
@@ -66,6 +87,7 @@ class Problem:
 
     @property
     def h(self) -> float:
+        """Step length of the uniform grid (the mean step of a non-uniform one)."""
         return (self.t1 - self.t0) / self.N
 
     @property
@@ -155,6 +177,24 @@ def lorenz96(d: int = 64, N: int = 16384, q: int = 2, F: float = 8.0, seed: int 
     rng = np.random.Generator(np.random.PCG64(seed))
     y0 = F + 0.01 * rng.standard_normal(d)
     return Problem(LORENZ96, d, _p(F), y0, 0.0, 5.0, int(N), int(q))
+
+
+def graded_grid(t0: float, t1: float, N: int, ratio: float) -> np.ndarray:
+    """Geometrically graded grid on [t0, t1]: N steps whose lengths grow by the constant factor
+    ratio^(1/(N-1)) from the first to the last (the last step is `ratio` times the first)."""
+    if N == 1:
+        return np.array([t0, t1], dtype=np.float64)
+    g = ratio ** (1.0 / (N - 1))
+    w = g ** np.arange(N)
+    ts = t0 + (t1 - t0) * np.concatenate([[0.0], np.cumsum(w) / np.sum(w)])
+    ts[-1] = t1
+    return ts
+
+
+def on_grid(p: Problem, ts) -> Problem:
+    """The same problem on the non-uniform grid ts (t0 and t1 are taken from its ends)."""
+    ts = np.asarray(ts, dtype=np.float64)
+    return dataclasses.replace(p, ts=ts, t0=float(ts[0]), t1=float(ts[-1]), N=len(ts) - 1)
 
 
 def params_array(p: Problem) -> np.ndarray:
