@@ -99,7 +99,10 @@ typedef struct {
   int32_t want_cov;     /* [1]   write square-root covariances (needs `sqrtcov`)            */
   int32_t chain_len;    /* [0]   time steps per sequential chain inside the scans, 0 = auto  */
   int32_t variant;      /* [0]   kernel layout: 0 = one state row per lane; 1 = two rows per
-                                 lane (half the lanes per chain); others PIT_EUNSUPPORTED    */
+                                 lane (half the lanes per chain); 2 = approximate Jacobians as
+                                 d decoupled components; 3 = the large-state kernels (one
+                                 thread block per chain, any d with D <= 256; always used for
+                                 d > 3 with the exact Jacobian); others PIT_EUNSUPPORTED      */
   int32_t linearization;/* [PIT_LIN_EK1] Jacobian of the linearisation (Sec. 3.2.1, remark on
                                  approximate Jacobians): exact, its diagonal, or zero         */
   int32_t objective;    /* [0]   1: evaluate the objective V (Eq. objective-value) of the
@@ -245,6 +248,23 @@ int32_t pit_solve_workspace_size(const pit_ode* ode, const pit_grid* grid, int32
 int32_t pit_solve(const pit_ode* ode, const pit_grid* grid, int32_t q, const double* y0,
                   const pit_opts* opts, const void* init_traj, void* mean, void* sqrtcov,
                   pit_solve_info* info, void* workspace, size_t ws_bytes, void* stream);
+
+/* ParaIEKS (Algorithm 2) on a non-uniform grid t_0 < t_1 < ... < t_N (Section 3.2.2 remarks
+ * that the method is not tied to uniform grids; the IWP transitions of Section 2.1 are taken
+ * for each step length h_n = t_n - t_{n-1}).  Solved by the large-state kernels for any d, with
+ * per-step preconditioning: in coordinates x_n = T(h_n) xbar_n (Section 2.4) the step into t_n
+ * is xbar_n = Phibar diag(T(h_{n-1}) / T(h_n)) xbar_{n-1} + w, w ~ N(0, Qbar), h_0 = h_1.
+ *   t                  host, N+1 grid points, finite and strictly increasing
+ *   other arguments    as pit_solve (grid replaced by t, N); init_traj rows are at the t_n
+ * Workspace size from pit_solve_grid_workspace_size.  Errors: as pit_solve; PIT_EINVAL for a
+ * grid that is not strictly increasing (the message names the first bad index);
+ * PIT_EUNSUPPORTED for init_coarse > 0 or the objective value (uniform grids only). */
+int32_t pit_solve_grid_workspace_size(const pit_ode* ode, const double* t, int64_t N, int32_t q,
+                                      const pit_opts* opts, size_t* bytes);
+int32_t pit_solve_grid(const pit_ode* ode, const double* t, int64_t N, int32_t q,
+                       const double* y0, const pit_opts* opts, const void* init_traj,
+                       void* mean, void* sqrtcov, pit_solve_info* info, void* workspace,
+                       size_t ws_bytes, void* stream);
 
 /* pit_solve for callers that cannot allocate device memory (no counterpart in the paper: this
  * is a deployment convenience).  Code running while a CUDA graph is captured, serving loops

@@ -110,6 +110,10 @@ SIGNATURES = {
                                         ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
     "pit_solve": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                          ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P, _SZ, _P]),
+    "pit_solve_grid_workspace_size": (_I32, [ctypes.POINTER(_Ode), _DP, _I64, _I32,
+                                             ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
+    "pit_solve_grid": (_I32, [ctypes.POINTER(_Ode), _DP, _I64, _I32, _DP, ctypes.POINTER(_Opts),
+                              _P, _P, _P, ctypes.POINTER(_Info), _P, _SZ, _P]),
     "pit_solve_noalloc": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                                  ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P]),
     "pit_eks_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
@@ -392,10 +396,50 @@ def pit_eks_sequential(ode: Ode, y0, t0: float, t1: float, N: int, q: int,
                        is_eks=True)
 
 
+def pit_solve_grid(ode: Ode, y0, ts, q: int, opts: Optional[_Opts] = None, init_traj=None,
+                   device=None, stream=None, workspace=None, out=None,
+                   allow_noconv=True) -> SolveResult:
+    """ParaIEKS on the non-uniform grid ts (N+1 increasing points) through the C ABI."""
+    import torch
+    lib = load()
+    opts = opts or make_opts()
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    N = t.size - 1
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    c = ode.c()
+    sz = ctypes.c_size_t(0)
+    _check(lib.pit_solve_grid_workspace_size(ctypes.byref(c), _dptr(t), N, int(q),
+                                             ctypes.byref(opts), ctypes.byref(sz)),
+           "workspace_size")
+    if workspace is None or workspace.numel() < sz.value:
+        workspace = _workspace(sz.value, device)
+    tdt = _torch_dtype(opts.dtype)
+    D = ode.d * (q + 1)
+    if out is None:
+        mean = torch.empty((N + 1, D), dtype=tdt, device=device)
+        cov = torch.empty((N + 1, D, D), dtype=tdt, device=device) if opts.want_cov else None
+    else:
+        mean, cov = out
+    y = np.ascontiguousarray(y0, dtype=np.float64)
+    info = _Info()
+    st = lib.pit_solve_grid(ctypes.byref(c), _dptr(t), N, int(q), _dptr(y), ctypes.byref(opts),
+                            _tptr(init_traj), _tptr(mean), _tptr(cov), ctypes.byref(info),
+                            _tptr(workspace), workspace.numel(), _stream_ptr(stream))
+    if not (st == 0 or (st == 4 and allow_noconv)):
+        _check(st, "pit_solve_grid")
+    res = SolveResult(mean, cov, info.iterations, bool(info.converged), info.last_delta,
+                      info.sigma2, int(info.kernel_launches), int(st))
+    res.deltas = [float(info.deltas[i]) for i in range(min(info.iterations, 64))]
+    return res
+
+
 def solve_problem(problem, **kw) -> SolveResult:
-    """Convenience wrapper for a workloads.Problem."""
+    """Convenience wrapper for a workloads.Problem (a non-uniform grid goes to pit_solve_grid)."""
     opts = kw.pop("opts", None) or make_opts(**{k: kw.pop(k) for k in list(kw)
                                                 if k in _OPT_KEYS})
+    if getattr(problem, "ts", None) is not None:
+        return pit_solve_grid(ode_from_problem(problem), problem.y0, problem.ts, problem.q, opts,
+                              **kw)
     return pit_solve(ode_from_problem(problem), problem.y0, problem.t0, problem.t1, problem.N,
                      problem.q, opts, **kw)
 

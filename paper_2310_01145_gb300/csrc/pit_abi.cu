@@ -688,6 +688,73 @@ int32_t pit_solve(const pit_ode* ode, const pit_grid* grid, int32_t q, const dou
                       ws_bytes, stream, nullptr, false);
 }
 
+// ParaIEKS on a non-uniform grid: the large-state kernels with per-step preconditioning.
+static int32_t solve_grid_common(const pit_ode* ode, const double* t, int64_t N, int32_t q,
+                                 const double* y0, const pit_opts* opts, const void* init_traj,
+                                 void* mean, void* sqrtcov, pit_solve_info* info,
+                                 void* workspace, size_t ws_bytes, void* stream, size_t* query) {
+  if (!t) {
+    set_error("grid points are NULL");
+    return PIT_EINVAL;
+  }
+  if (!(N >= 1) || N > (int64_t(1) << 31) - 2) {
+    set_error("grid N must be in 1..2^31-2");
+    return PIT_EINVAL;
+  }
+  for (int64_t n = 0; n <= N; ++n) {
+    if (!std::isfinite(t[n]) || (n > 0 && !(t[n] > t[n - 1]))) {
+      set_error("grid points must be finite and strictly increasing (index " +
+                std::to_string(n) + ")");
+      return PIT_EINVAL;
+    }
+  }
+  SolveArgs a;
+  std::memset(&a, 0, sizeof(a));
+  int st = fill_problem(ode, q, y0, a.pb, query == nullptr);
+  if (st != PIT_OK) return st;
+  a.pb.t0 = t[0];
+  a.pb.t1 = t[N];
+  a.pb.N = N;
+  st = check_opts(opts, a.opts);
+  if (st != PIT_OK) return st;
+  SolveFn fn = find_dense_solver(a.opts.dtype);
+  if (!fn) {
+    set_error("large-state kernels not compiled for this dtype");
+    return PIT_EUNSUPPORTED;
+  }
+  a.grid = t;
+  a.init_traj = init_traj;
+  a.mean = mean;
+  a.sqrtcov = sqrtcov;
+  a.info = info;
+  a.workspace = workspace;
+  a.ws_bytes = ws_bytes;
+  a.stream = static_cast<cudaStream_t>(stream);
+  if (query) return fn(a, query, false);
+  if (!mean || (a.opts.want_cov && !sqrtcov) || !workspace) {
+    set_error("null output or workspace buffer");
+    return PIT_EINVAL;
+  }
+  return fn(a, nullptr, false);
+}
+
+int32_t pit_solve_grid_workspace_size(const pit_ode* ode, const double* t, int64_t N, int32_t q,
+                                      const pit_opts* opts, size_t* bytes) {
+  g_err.clear();
+  if (!bytes) return PIT_EINVAL;
+  return solve_grid_common(ode, t, N, q, nullptr, opts, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, 0, nullptr, bytes);
+}
+
+int32_t pit_solve_grid(const pit_ode* ode, const double* t, int64_t N, int32_t q,
+                       const double* y0, const pit_opts* opts, const void* init_traj,
+                       void* mean, void* sqrtcov, pit_solve_info* info, void* workspace,
+                       size_t ws_bytes, void* stream) {
+  g_err.clear();
+  return solve_grid_common(ode, t, N, q, y0, opts, init_traj, mean, sqrtcov, info, workspace,
+                           ws_bytes, stream, nullptr);
+}
+
 int32_t pit_eks_workspace_size(const pit_ode* ode, const pit_grid* grid, int32_t q,
                                const pit_opts* opts, size_t* bytes) {
   g_err.clear();

@@ -70,7 +70,47 @@ struct DenseParams {
   const T* pt;           // device: ODE parameters, arithmetic type
   int n_params;
   const double* mu0d;    // device: preconditioned exact initial state (D)
+  // Non-uniform grid (null on a uniform grid): per grid point n = 0..N, SW = 2 Q1 + 3 values
+  // [T(h_n) (Q1) | T(h_{n-1}) / T(h_n) (Q1) | h_n / q | T_0(h_n) | 1 / T_1(h_n)], h_n the step
+  // into t_n (h_0 = h_1).  In preconditioned coordinates x_n = T(h_n) xbar_n the step into t_n
+  // is xbar_n = Phibar diag(T(h_{n-1}) / T(h_n)) xbar_{n-1} + w, w ~ N(0, Qbar) (Section 2.4's
+  // step-free Phibar, Qbar), and the observation rows are scaled by 1 / T_1(h_n).
+  const double* mu0o;    // device: exact initial state in original coordinates (D)
+  const double* gsd;     // FP64
+  const T* gst;          // arithmetic type
+  int SW;
 };
+
+// ---- per-step quantities (uniform grid: the constants) ------------------------------------------
+template <typename T>
+__device__ __forceinline__ T st_T(const DenseParams<T>& p, int64_t n, int i) {
+  return p.gst ? p.gst[n * p.SW + i] : p.Tdiag[i];
+}
+template <typename T>
+__device__ __forceinline__ double st_Td(const DenseParams<T>& p, int64_t n, int i) {
+  return p.gsd ? p.gsd[n * p.SW + i] : p.Tdiagd[i];
+}
+// scale vector of the step into t_n (null: all ones)
+template <typename T>
+__device__ __forceinline__ const T* st_sc(const DenseParams<T>& p, int64_t n) {
+  return p.gst ? p.gst + n * p.SW + p.Q1 : nullptr;
+}
+template <typename T>
+__device__ __forceinline__ T st_hq(const DenseParams<T>& p, int64_t n) {
+  return p.gst ? p.gst[n * p.SW + 2 * p.Q1] : p.hq;
+}
+template <typename T>
+__device__ __forceinline__ T st_T0(const DenseParams<T>& p, int64_t n) {
+  return p.gst ? p.gst[n * p.SW + 2 * p.Q1 + 1] : p.T0;
+}
+template <typename T>
+__device__ __forceinline__ double st_T0d(const DenseParams<T>& p, int64_t n) {
+  return p.gsd ? p.gsd[n * p.SW + 2 * p.Q1 + 1] : p.T0d;
+}
+template <typename T>
+__device__ __forceinline__ double st_T1invd(const DenseParams<T>& p, int64_t n) {
+  return p.gsd ? p.gsd[n * p.SW + 2 * p.Q1 + 2] : p.T1invd;
+}
 
 // ---- per-step model inputs ------------------------------------------------------------------
 // Component k of the vector field in number type V, the state read through y(j): the affine
@@ -131,11 +171,11 @@ __device__ __forceinline__ T jac_entry(const DenseParams<T>& p, const T* y, int 
 
 // Ft = (h/q) F_y(y) (d x d, row-major) for the scaled observation model Ht = E1 - Ft E0.
 template <typename T>
-__device__ __forceinline__ void cta_jacobian(const DenseParams<T>& p, const T* y, T* Ft) {
+__device__ __forceinline__ void cta_jacobian(const DenseParams<T>& p, const T* y, T* Ft, T hq) {
   const int d = p.d;
   for (int e = threadIdx.x; e < d * d; e += NT) {
     const int i = e / d, j = e - i * d;
-    Ft[e] = p.hq * jac_entry<T>(p, y, i, j);
+    Ft[e] = hq * jac_entry<T>(p, y, i, j);
   }
   __syncthreads();
 }
@@ -180,29 +220,36 @@ __device__ __forceinline__ void cta_solve_small(int d, const T* S, int lds, cons
   __syncthreads();
 }
 
-// y = Phibar x + u   (block upper-triangular, I_d (x) Phibar1); y must not alias x
+// Entry (i, j) of the step's transition Phibar diag(sc) in one dimension block (sc null: Phibar).
 template <typename T>
-__device__ __forceinline__ void cta_phi_vec(const DenseParams<T>& p, const T* x, const T* u, T* y) {
+__device__ __forceinline__ T phi_entry(const DenseParams<T>& p, const T* sc, int i, int j) {
+  return sc ? p.phib[i * kMaxQ1 + j] * sc[j] : p.phib[i * kMaxQ1 + j];
+}
+
+// y = Phibar diag(sc) x + u   (block upper-triangular, I_d (x) Phibar1); y must not alias x
+template <typename T>
+__device__ __forceinline__ void cta_phi_vec(const DenseParams<T>& p, const T* x, const T* u, T* y,
+                                            const T* sc = nullptr) {
   const int Q1 = p.Q1;
   for (int r = threadIdx.x; r < p.D; r += NT) {
     const int ir = r % Q1, b = r - ir;
     T acc = u ? u[r] : T(0);
-    for (int j = ir; j < Q1; ++j) acc += p.phib[ir * kMaxQ1 + j] * x[b + j];
+    for (int j = ir; j < Q1; ++j) acc += phi_entry(p, sc, ir, j) * x[b + j];
     y[r] = acc;
   }
   __syncthreads();
 }
 
-// Y (D x nc) = Phibar X; Y must not alias X
+// Y (D x nc) = Phibar diag(sc) X; Y must not alias X
 template <typename T>
 __device__ __forceinline__ void cta_phi_mat(const DenseParams<T>& p, const T* X, int ldx, int nc,
-                                            T* Y, int ldy) {
+                                            T* Y, int ldy, const T* sc = nullptr) {
   const int Q1 = p.Q1;
   for (int e = threadIdx.x; e < p.D * nc; e += NT) {
     const int r = e / nc, c = e - r * nc;
     const int ir = r % Q1, b = r - ir;
     T acc = T(0);
-    for (int j = ir; j < Q1; ++j) acc += p.phib[ir * kMaxQ1 + j] * X[static_cast<size_t>(b + j) * ldx + c];
+    for (int j = ir; j < Q1; ++j) acc += phi_entry(p, sc, ir, j) * X[static_cast<size_t>(b + j) * ldx + c];
     Y[static_cast<size_t>(r) * ldy + c] = acc;
   }
   __syncthreads();
@@ -211,14 +258,15 @@ __device__ __forceinline__ void cta_phi_mat(const DenseParams<T>& p, const T* X,
 // A <- Phibar A in place (D x nc): each thread owns one (dimension block, column) and updates the
 // block's rows in increasing order, each reading only rows not yet overwritten.
 template <typename T>
-__device__ __forceinline__ void cta_phi_inplace(const DenseParams<T>& p, T* A, int lda, int nc) {
+__device__ __forceinline__ void cta_phi_inplace(const DenseParams<T>& p, T* A, int lda, int nc,
+                                                const T* sc = nullptr) {
   const int Q1 = p.Q1, d = p.d;
   for (int e = threadIdx.x; e < d * nc; e += NT) {
     const int k = e / nc, c = e - k * nc;
     T* col = A + static_cast<size_t>(k * Q1) * lda + c;
     for (int i = 0; i < Q1; ++i) {
       T acc = T(0);
-      for (int j = i; j < Q1; ++j) acc += p.phib[i * kMaxQ1 + j] * col[static_cast<size_t>(j) * lda];
+      for (int j = i; j < Q1; ++j) acc += phi_entry(p, sc, i, j) * col[static_cast<size_t>(j) * lda];
       col[static_cast<size_t>(i) * lda] = acc;
     }
   }
@@ -287,7 +335,13 @@ __global__ void k_dinit_traj(const DenseParams<T> p, const T* __restrict__ init,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % p.D);
-    const double x = init ? static_cast<double>(init[i]) / p.Tdiagd[r % p.Q1] : p.mu0d[r];
+    double x;
+    if (p.gsd) {
+      const int64_t n = i / p.D;
+      x = (init ? static_cast<double>(init[i]) : p.mu0o[r]) / st_Td(p, n, r % p.Q1);
+    } else {
+      x = init ? static_cast<double>(init[i]) / p.Tdiagd[r % p.Q1] : p.mu0d[r];
+    }
     lin[i] = v_from_double<Vt<T>>(x);
   }
 }
@@ -300,20 +354,32 @@ k_dres(const DenseParams<T> p, const Vt<T>* __restrict__ lin, T* __restrict__ U,
        T* __restrict__ R, T* __restrict__ Yv, T* __restrict__ d0) {
   using V = Vt<T>;
   const int d = p.d, Q1 = p.Q1, D = p.D;
-  const V T0v = v_from_double<V>(p.T0d);
-  const V T1iv = v_from_double<V>(p.T1invd);
   const int64_t total = (p.N + 1) * d;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = e / d;
     const int k = static_cast<int>(e - n * d);
+    const V T0v = v_from_double<V>(st_T0d(p, n));
+    const V T1iv = v_from_double<V>(st_T1invd(p, n));
     const V* x = lin + n * D;
     if (n < p.N) {
-      for (int i = 0; i < Q1; ++i) {
-        V acc = x[k * Q1 + i];
-        for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
-        acc = acc - lin[(n + 1) * D + k * Q1 + i];
-        U[n * D + k * Q1 + i] = v_to_T<T>(acc);
+      if (!p.gsd) {
+        for (int i = 0; i < Q1; ++i) {
+          V acc = x[k * Q1 + i];
+          for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+          acc = acc - lin[(n + 1) * D + k * Q1 + i];
+          U[n * D + k * Q1 + i] = v_to_T<T>(acc);
+        }
+      } else {
+        // u_n = Phibar diag(sc_{n+1}) lin_n - lin_{n+1}, the scale factors in extended precision
+        const double* sc = p.gsd + (n + 1) * p.SW + Q1;
+        for (int i = 0; i < Q1; ++i) {
+          V acc = x[k * Q1 + i] * v_from_double<V>(sc[i]);
+          for (int j = i + 1; j < Q1; ++j)
+            acc = acc + x[k * Q1 + j] * v_from_double<V>(static_cast<double>(p.phib[i * kMaxQ1 + j]) * sc[j]);
+          acc = acc - lin[(n + 1) * D + k * Q1 + i];
+          U[n * D + k * Q1 + i] = v_to_T<T>(acc);
+        }
       }
     }
     const V fk = dense_f<V, T>(p.kind, p.pd, d, k, [&](int j) { return T0v * x[j * Q1]; });
@@ -340,7 +406,7 @@ __device__ __forceinline__ void load_step(const DenseParams<T>& p, int64_t n, co
     vec[V_R * D + i] = R[n * d + i];
   }
   __syncthreads();
-  cta_jacobian<T>(p, vec + V_Y * D, Ft);
+  cta_jacobian<T>(p, vec + V_Y * D, Ft, st_hq(p, n));
 }
 
 // Filter reduce: chain c folds leaves n = cL+1 .. min(cL+L, N) into its aggregate (chain 0 from
@@ -387,10 +453,11 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
   for (int64_t n = n0; n <= n1; ++n) {
     load_step<T>(p, n, U, R, Yv, vec, Ft);
     // predict: A' = Phibar A, b' = Phibar b + u, sqrtC- = tria([sqrtQbar | Phibar sqrtC])
-    cta_phi_inplace<T>(p, A, D, D);
-    cta_phi_vec<T>(p, b, vec + V_U * D, bp);
+    const T* sc = st_sc(p, n);
+    cta_phi_inplace<T>(p, A, D, D, sc);
+    cta_phi_vec<T>(p, b, vec + V_U * D, bp, sc);
     T* Pr = Wk + static_cast<size_t>(d) * ldw;  // rows d .. d+D-1
-    cta_phi_mat<T>(p, Csq, ldw, W, Pr + D, ldw);
+    cta_phi_mat<T>(p, Csq, ldw, W, Pr + D, ldw, sc);
     cta_sqrtq<T>(p, Pr, ldw);
     cta_lq<T>(Pr, ldw, D, D, D, D + W, sm, p.wsmax);
     // update: Psi = tria([[Ht sqrtC-], [sqrtC-]]), d reflections
@@ -743,11 +810,12 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
   for (int64_t n = n0; n <= n1; ++n) {
     if (!LOCAL_LIN) load_step<T>(p, n, U, R, Yv, vec, Ft);
     // Pi input: top [sqrtQbar | Phibar sqrtP], bottom [0 | sqrtP]
-    cta_phi_mat<T>(p, psrc, psld, ne, Top + D, ldw);
+    const T* sc = st_sc(p, n);
+    cta_phi_mat<T>(p, psrc, psld, ne, Top + D, ldw, sc);
     cta_copy<T>(D, ne, psrc, psld, Bot + D, ldw);
     cta_sqrtq<T>(p, Top, ldw);
     cta_set<T>(D, D, Bot, ldw, T(0));
-    cta_phi_vec<T>(p, m, LOCAL_LIN ? nullptr : vec + V_U * D, mp);
+    cta_phi_vec<T>(p, m, LOCAL_LIN ? nullptr : vec + V_U * D, mp, sc);
     cta_lq<T>(Top, ldw, 2 * D, D, D, D + ne, sm, p.wsmax);
     // smoothing element n-1: E = Pi21 Pi11^-1, g = m^f - E m-, sqrtL = tria(remainder)
     T* En = Es + (n - 1) * DD;
@@ -775,7 +843,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
       T* rr = vec + V_R * D;
       for (int k = threadIdx.x; k < d; k += NT) y[k] = p.T0 * mp[k * p.Q1];
       __syncthreads();
-      cta_jacobian<T>(p, y, Ft);
+      cta_jacobian<T>(p, y, Ft, p.hq);
       for (int k = threadIdx.x; k < d; k += NT) {
         T acc = dense_f<T, T>(p.kind, p.pd, d, k, [&](int j) { return y[j]; });
         for (int j = 0; j < d; ++j) acc -= jac_entry<T>(p, y, k, j) * y[j];
@@ -885,17 +953,18 @@ k_dsmooth(const DenseParams<T> p, const T* __restrict__ Es, const T* __restrict_
     for (int r = threadIdx.x; r < D; r += NT) {
       const V lnew = v_add_small(lin ? lin[n * D + r] : v_from_zero<V>(), mn[r]);
       if (WITH_L) {
-        const T tr = p.Tdiag[r % Q1];
+        const T tr = st_T(p, n, r % Q1);
         mean_out[n * D + r] = tr * v_to_T<T>(lnew);
         for (int c = 0; c < D; ++c)
           cov_out[n * DD + static_cast<int64_t>(r) * D + c] = sigma * tr * Pw[static_cast<size_t>(r) * 2 * D + c];
       } else {
         lin_new[n * D + r] = lnew;
         if (r % Q1 == 0) {
-          const T dd = fabs(p.T0 * mn[r]);
+          const T t0n = st_T0(p, n);
+          const T dd = fabs(t0n * mn[r]);
           bad = bad || !(dd == dd);
           dmax = fmax(dmax, dd);
-          ymax = fmax(ymax, fabs(p.T0 * v_to_T<T>(lnew)));
+          ymax = fmax(ymax, fabs(t0n * v_to_T<T>(lnew)));
         }
       }
     }
@@ -960,7 +1029,7 @@ __global__ void k_dexport(const DenseParams<T> p, const Vt<T>* __restrict__ lin,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % p.D);
-    mean[i] = p.Tdiag[r % p.Q1] * v_to_T<T>(lin[i]);
+    mean[i] = st_T(p, i / p.D, r % p.Q1) * v_to_T<T>(lin[i]);
   }
 }
 
@@ -978,6 +1047,9 @@ struct DenseSolver {
     double* pd;
     T* pt;
     double* mu0d;
+    double* mu0o;
+    double* gsd;
+    T* gst;
   };
 
   static int default_chain_len(int64_t N) {
@@ -992,7 +1064,33 @@ struct DenseSolver {
     return v;
   }
 
-  static int fill_params(const SolveArgs& a, DenseParams<T>& p, std::vector<double>& mu0pre) {
+  // Per-point step data of a non-uniform grid (see DenseParams::gsd); FP64 on the host.
+  static int grid_steps(const SolveArgs& a, int q, std::vector<double>& gs, int* SW) {
+    const int Q1 = q + 1;
+    *SW = 2 * Q1 + 3;
+    const int64_t N = a.pb.N;
+    gs.assign(static_cast<size_t>(N + 1) * *SW, 0.0);
+    std::vector<double> Tprev(Q1), Tn(Q1);
+    double Phib[64], sqb[64], Td[8];
+    for (int64_t n = 0; n <= N; ++n) {
+      const double h = n == 0 ? a.grid[1] - a.grid[0] : a.grid[n] - a.grid[n - 1];
+      if (prior_blocks(q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
+      double* g = gs.data() + n * *SW;
+      for (int i = 0; i < Q1; ++i) {
+        Tn[i] = Td[i];
+        g[i] = Td[i];
+        g[Q1 + i] = n == 0 ? 1.0 : Tprev[i] / Td[i];
+      }
+      g[2 * Q1] = h / q;
+      g[2 * Q1 + 1] = Td[0];
+      g[2 * Q1 + 2] = 1.0 / Td[1];
+      Tprev = Tn;
+    }
+    return PIT_OK;
+  }
+
+  static int fill_params(const SolveArgs& a, DenseParams<T>& p, std::vector<double>& mu0pre,
+                         std::vector<double>* mu0orig = nullptr) {
     const Problem& pb = a.pb;
     std::memset(&p, 0, sizeof(p));
     p.d = pb.d;
@@ -1014,7 +1112,9 @@ struct DenseSolver {
       set_error("large-state solver: D = d (q+1) must be <= " + std::to_string(kMaxDenseD));
       return PIT_EUNSUPPORTED;
     }
-    const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
+    // uniform grid: its step; non-uniform: the first step (T at t_0, the scale of mu0's
+    // preconditioning); the per-step data come from grid_steps
+    const double h = a.grid ? a.grid[1] - a.grid[0] : (pb.t1 - pb.t0) / static_cast<double>(pb.N);
     double Phib[64], sqb[64], Td[8];
     if (prior_blocks(pb.q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
     for (int i = 0; i < p.Q1; ++i) {
@@ -1034,6 +1134,7 @@ struct DenseSolver {
     if (taylor_init(pb, mu0.data()) != PIT_OK) return PIT_EINVAL;
     mu0pre.resize(p.D);
     for (int r = 0; r < p.D; ++r) mu0pre[r] = mu0[r] / Td[r % p.Q1];
+    if (mu0orig) *mu0orig = mu0;
     const ChainLayout lay(p.d, p.D, p.kJ);
     const TreeLayout tl(p.D);
     p.chain_elems = std::max(lay.total, tl.total);
@@ -1062,6 +1163,15 @@ struct DenseSolver {
     b.pd = cv.take<double>(std::max(1, a.pb.n_params));
     b.pt = cv.take<T>(std::max(1, a.pb.n_params));
     b.mu0d = cv.take<double>(D);
+    b.mu0o = cv.take<double>(D);
+    if (a.grid) {
+      const int64_t SW = 2 * (a.pb.q + 1) + 3;
+      b.gsd = cv.take<double>(N1 * SW);
+      b.gst = cv.take<T>(N1 * SW);
+    } else {
+      b.gsd = nullptr;
+      b.gst = nullptr;
+    }
     return cv.used();
   }
 
@@ -1162,9 +1272,13 @@ struct DenseSolver {
       return PIT_EUNSUPPORTED;
     }
     const bool want_cov = a.opts.want_cov != 0;
+    if (a.grid && (eks || a.opts.init_coarse > 0)) {
+      set_error("the sequential EKS and the coarse-grid start are implemented for uniform grids");
+      return PIT_EUNSUPPORTED;
+    }
     DenseParams<T> p;
-    std::vector<double> mu0pre;
-    int st = fill_params(a, p, mu0pre);
+    std::vector<double> mu0pre, mu0orig;
+    int st = fill_params(a, p, mu0pre, &mu0orig);
     if (st != PIT_OK) return st;
     if (eks) {
       // one chain over all steps (leaves 1..N, owner of b_N)
@@ -1219,6 +1333,22 @@ struct DenseSolver {
     p.pd = b.pd;
     p.pt = b.pt;
     p.mu0d = b.mu0d;
+    std::vector<double> gs;
+    std::vector<T> gst;
+    if (a.grid) {
+      int SW = 0;
+      st = grid_steps(a, p.q, gs, &SW);
+      if (st != PIT_OK) return st;
+      gst.resize(gs.size());
+      for (size_t i = 0; i < gs.size(); ++i) gst[i] = static_cast<T>(gs[i]);
+      PIT_CUDA_TRY(cudaMemcpyAsync(b.gsd, gs.data(), sizeof(double) * gs.size(), cudaMemcpyHostToDevice, s));
+      PIT_CUDA_TRY(cudaMemcpyAsync(b.gst, gst.data(), sizeof(T) * gst.size(), cudaMemcpyHostToDevice, s));
+      p.gsd = b.gsd;
+      p.gst = b.gst;
+      p.SW = SW;
+    }
+    PIT_CUDA_TRY(cudaMemcpyAsync(b.mu0o, mu0orig.data(), sizeof(double) * p.D, cudaMemcpyHostToDevice, s));
+    p.mu0o = b.mu0o;
     const int64_t total = (p.N + 1) * p.D;
     const unsigned eg = elem_grid(total, 256);
     T* mean = static_cast<T*>(a.mean);

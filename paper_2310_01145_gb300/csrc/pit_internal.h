@@ -29,6 +29,7 @@ struct Problem {
 struct SolveArgs {
   Problem pb;
   pit_opts opts;
+  const double* grid;   // host, N+1 grid points of a non-uniform grid (null: uniform)
   const void* init_traj;
   void* mean;
   void* sqrtcov;

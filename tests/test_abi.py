@@ -173,3 +173,24 @@ def test_server_config_validation_on_host(pit):
         assert lib.pit_server_create(ctypes.byref(c), ctypes.byref(h)) == 1, field
         assert not h.value
     assert lib.pit_server_clock() > 0
+
+
+def test_solve_grid_validation(pit):
+    """pit_solve_grid checks its grid on the host: strictly increasing, finite points."""
+    import ctypes
+    lib = pit.load()
+    p = W.lorenz96(d=8, N=10, q=2)
+    c = pit.ode_from_problem(p).c()
+    opts = pit.make_opts()
+    sz = ctypes.c_size_t(0)
+    good = np.linspace(0.0, 1.0, 11)
+    st = lib.pit_solve_grid_workspace_size(ctypes.byref(c), good.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           10, 2, ctypes.byref(opts), ctypes.byref(sz))
+    assert st == 0 and sz.value > 0
+    for bad in (np.r_[0.0, 0.5, 0.5, np.linspace(0.6, 1.0, 8)],
+                np.r_[np.linspace(0.0, 1.0, 10), np.nan]):
+        bad = np.ascontiguousarray(bad)
+        st = lib.pit_solve_grid_workspace_size(ctypes.byref(c), bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               10, 2, ctypes.byref(opts), ctypes.byref(sz))
+        assert st == 1
+        assert b"strictly increasing" in lib.pit_last_error()
