@@ -332,6 +332,7 @@ struct PanelCols {
 template <typename T>
 __device__ __forceinline__ T make_reflection(T (&x)[MAXCH], int j, int ws, int ldv, T* vrow) {
   const int lane = threadIdx.x & 31;
+  const int nch = (ldv + 31) >> 5;  // chunks that hold positions < ldv
   const int cj = j >> 5, lj = j & 31;
   T xa = T(0);
 #pragma unroll
@@ -341,6 +342,7 @@ __device__ __forceinline__ T make_reflection(T (&x)[MAXCH], int j, int ws, int l
   T amax = T(0);
 #pragma unroll
   for (int c = 0; c < MAXCH; ++c) {
+    if (c >= nch) break;
     const int p = lane + 32 * c;
     if (p >= j && p < ws) amax = fmax(amax, fabs(x[c]));
   }
@@ -350,6 +352,7 @@ __device__ __forceinline__ T make_reflection(T (&x)[MAXCH], int j, int ws, int l
   T ssq = T(0);
 #pragma unroll
   for (int c = 0; c < MAXCH; ++c) {
+    if (c >= nch) break;
     const int p = lane + 32 * c;
     if (p > j && p < ws) {
       const T t = ldexp(x[c], -e);
@@ -368,6 +371,7 @@ __device__ __forceinline__ T make_reflection(T (&x)[MAXCH], int j, int ws, int l
   }
 #pragma unroll
   for (int c = 0; c < MAXCH; ++c) {
+    if (c >= nch) break;
     const int p = lane + 32 * c;
     const T v = (p == j) ? T(1) : ((p > j && p < ws) ? ldexp(x[c], -e) * scale : T(0));
     if (p < ldv) vrow[p] = v;
@@ -415,6 +419,7 @@ __device__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* s
         x[s][c] = (i < kb && p < ws) ? M[static_cast<size_t>(k0 + i) * ld + pc.col(p)] : T(0);
       }
     }
+    const int nch = (ldv + 31) >> 5;
     for (int j = 0; j < kb; ++j) {
       if (warp == (j % NWARPS)) {
         const int s_own = j / NWARPS;
@@ -429,27 +434,28 @@ __device__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* s
 #pragma unroll
       for (int c = 0; c < MAXCH; ++c) {
         const int p = lane + 32 * c;
-        vr[c] = p < ldv ? Vs[j * ldv + p] : T(0);
+        vr[c] = (c < nch && p < ldv) ? Vs[j * ldv + p] : T(0);
       }
-      // apply H_j to the panel rows below j held by this warp
-      T acc0 = T(0), acc1 = T(0);
+      // apply H_j to the panel rows below j held by this warp (warp-uniform conditions)
       const int i0 = warp, i1 = warp + NWARPS;
+      const bool a0 = i0 > j && i0 < kb, a1 = i1 > j && i1 < kb;
+      if (a0 || a1) {
+        T acc0 = T(0), acc1 = T(0);
 #pragma unroll
-      for (int c = 0; c < MAXCH; ++c) {
-        acc0 += x[0][c] * vr[c];
-        acc1 += x[1][c] * vr[c];
-      }
-      acc0 = warp_sum(acc0);
-      acc1 = warp_sum(acc1);
-      if (i0 > j && i0 < kb) {
-        const T f = tj * acc0;
+        for (int c = 0; c < MAXCH; ++c) {
+          if (c >= nch) break;
+          if (a0) acc0 += x[0][c] * vr[c];
+          if (a1) acc1 += x[1][c] * vr[c];
+        }
+        acc0 = warp_sum(acc0);
+        acc1 = warp_sum(acc1);
+        const T f0 = tj * acc0, f1 = tj * acc1;
 #pragma unroll
-        for (int c = 0; c < MAXCH; ++c) x[0][c] -= f * vr[c];
-      }
-      if (i1 > j && i1 < kb) {
-        const T f = tj * acc1;
-#pragma unroll
-        for (int c = 0; c < MAXCH; ++c) x[1][c] -= f * vr[c];
+        for (int c = 0; c < MAXCH; ++c) {
+          if (c >= nch) break;
+          if (a0) x[0][c] -= f0 * vr[c];
+          if (a1) x[1][c] -= f1 * vr[c];
+        }
       }
       // Gram entries G[i][j] = v_i . v_j for i < j (rows i = warp, warp + 16)
 #pragma unroll
@@ -459,6 +465,7 @@ __device__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* s
           T g = T(0);
 #pragma unroll
           for (int c = 0; c < MAXCH; ++c) {
+            if (c >= nch) break;
             const int p = lane + 32 * c;
             if (p < ldv) g += Vs[i * ldv + p] * vr[c];
           }
