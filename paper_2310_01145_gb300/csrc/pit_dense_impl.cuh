@@ -45,7 +45,7 @@ __device__ __forceinline__ float v_from_double<float>(double x) {
 namespace dn {
 
 constexpr int kMaxDenseD = 256;
-constexpr int kJBatchDense = 2;  // information rows of kJ steps are folded into sqrtJ at once
+constexpr int kJBatchDense = 3;  // information rows of kJ steps are folded into sqrtJ at once
 constexpr int kTreeGroup = 8;    // chain aggregates combined by tree levels before the look-back
 
 template <typename T>
