@@ -46,7 +46,10 @@ namespace dn {
 
 constexpr int kMaxDenseD = 256;
 constexpr int kJBatchDense = 3;  // information rows of kJ steps are folded into sqrtJ at once
-constexpr int kTreeGroup = 8;    // chain aggregates combined by tree levels before the look-back
+#ifndef PIT_TREE_GROUP
+#define PIT_TREE_GROUP 32
+#endif
+constexpr int kTreeGroup = PIT_TREE_GROUP;  // chain aggregates combined by tree levels before the look-back
 
 template <typename T>
 struct DenseParams {
