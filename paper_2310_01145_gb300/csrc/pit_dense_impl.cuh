@@ -47,7 +47,7 @@ namespace dn {
 constexpr int kMaxDenseD = 256;
 constexpr int kJBatchDense = 3;  // information rows of kJ steps are folded into sqrtJ at once
 #ifndef PIT_TREE_GROUP
-#define PIT_TREE_GROUP 32
+#define PIT_TREE_GROUP 8
 #endif
 constexpr int kTreeGroup = PIT_TREE_GROUP;  // chain aggregates combined by tree levels before the look-back
 

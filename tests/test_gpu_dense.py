@@ -190,7 +190,7 @@ def test_lorenz96_full_size_kernels(pit, N):
 @pytest.mark.parametrize("N", [4096, 16384])
 def test_lorenz96_full_size_parallel_shape(pit, N):
     """The same first iterate in the benchmark's launch shape (about one chain per SM, the chain
-    aggregates combined by tree levels inside groups of 32 and a sequential look-back across the
+    aggregates combined by tree levels inside groups of 8 and a sequential look-back across the
     groups).  On this chaotic workload (linearisation growing like e^(8 t)) a tree over all
     chains combined elements whose flow maps spanned most of [0, 5] and missed the oracle by
     2.7e-6 (N = 4096) and 2.9e-4 (N = 16384); with span-limited combines the parallel result
