@@ -201,7 +201,9 @@ int32_t pit_filter_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, size
  * covariances m^f_n, sqrt(P^f_n).  Output factors C, J are lower-triangular; they are
  * square roots of the same matrices as the paper's but their column signs are not fixed.
  * Asynchronous.  Errors: PIT_EINVAL (N < 1, D < 1, null pointer), PIT_EUNSUPPORTED (D not
- * compiled: 1..16), PIT_ENOMEM (workspace too small). */
+ * 1..256), PIT_ENOMEM (workspace too small).  D in {2, 3, 4, 6, 8} runs on lane-group kernels,
+ * every other D on the large-state kernels (one thread block per chain of elements; chain
+ * aggregates scanned by tree levels inside groups of 8 chains and a look-back across groups). */
 int32_t pit_filter_scan(int64_t N, int32_t D, int32_t dtype, void* A, void* b, void* C,
                         void* eta, void* J, void* workspace, size_t ws_bytes, void* stream);
 

@@ -97,6 +97,7 @@ struct Registry {
   std::mutex mu;
   std::map<int, SolveFn> solvers;  // key variant*100000 + dtype*10000 + d*100 + q
   std::map<int, SolveFn> dense;    // key dtype
+  std::map<int, ScanFn> dense_scans;  // key dtype*2 + (filter ? 1 : 0)
   std::map<int, ScanFn> fscans;    // key dtype*100 + D
   std::map<int, ScanFn> sscans;
 };
@@ -113,6 +114,18 @@ DenseRegistrar::DenseRegistrar(int dtype, SolveFn fn) {
   Registry& r = registry();
   std::lock_guard<std::mutex> lk(r.mu);
   r.dense[dtype] = fn;
+}
+DenseRegistrar::DenseRegistrar(int dtype, ScanFn f, ScanFn sm) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.dense_scans[dtype * 2 + 1] = f;
+  r.dense_scans[dtype * 2] = sm;
+}
+ScanFn find_dense_scan(int dtype, bool filter) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.dense_scans.find(dtype * 2 + (filter ? 1 : 0));
+  return it == r.dense_scans.end() ? nullptr : it->second;
 }
 SolveFn find_dense_solver(int dtype) {
   Registry& r = registry();
@@ -568,11 +581,13 @@ static int32_t scan_common(bool filter, int64_t N, int32_t D, int32_t dtype, voi
     return PIT_EINVAL;
   }
   ScanFn fn = filter ? find_filter_scan(dtype, D) : find_smooth_scan(dtype, D);
+  // other D up to 256: the large-state kernels' block-level operators
+  if (!fn && D <= 256) fn = find_dense_scan(dtype, filter);
   if (!fn) {
-    set_error("scan: D=" + std::to_string(D) + " not compiled (2, 3, 4, 6, 8)");
+    set_error("scan: D=" + std::to_string(D) + " not supported (1..256)");
     return PIT_EUNSUPPORTED;
   }
-  ScanArgs a{N, x0, x1, x2, x3, x4, want_L, ws, wsb, static_cast<cudaStream_t>(stream)};
+  ScanArgs a{N, D, x0, x1, x2, x3, x4, want_L, ws, wsb, static_cast<cudaStream_t>(stream)};
   if (query) return fn(a, query);
   if (!x0 || !x1 || (filter && (!x2 || !x3 || !x4)) || (!filter && want_L && !x2) || !ws) {
     set_error("scan: null buffer");

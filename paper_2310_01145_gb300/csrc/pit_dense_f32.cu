@@ -5,5 +5,8 @@ namespace pit {
 namespace {
 int solve_dense_f32(const SolveArgs& a, size_t* w, bool e) { return dn::DenseSolver<float>::run(a, w, e); }
 DenseRegistrar reg_dense_f32(PIT_F32, solve_dense_f32);
+int scan_f_f32(const ScanArgs& a, size_t* w) { return dn::DenseScan<float>::filter(a, a.D, w); }
+int scan_s_f32(const ScanArgs& a, size_t* w) { return dn::DenseScan<float>::smooth(a, a.D, w); }
+DenseRegistrar reg_dense_scan_f32(PIT_F32, scan_f_f32, scan_s_f32);
 }  // namespace
 }  // namespace pit

@@ -5,5 +5,8 @@ namespace pit {
 namespace {
 int solve_dense_f64(const SolveArgs& a, size_t* w, bool e) { return dn::DenseSolver<double>::run(a, w, e); }
 DenseRegistrar reg_dense_f64(PIT_F64, solve_dense_f64);
+int scan_f_f64(const ScanArgs& a, size_t* w) { return dn::DenseScan<double>::filter(a, a.D, w); }
+int scan_s_f64(const ScanArgs& a, size_t* w) { return dn::DenseScan<double>::smooth(a, a.D, w); }
+DenseRegistrar reg_dense_scan_f64(PIT_F64, scan_f_f64, scan_s_f64);
 }  // namespace
 }  // namespace pit

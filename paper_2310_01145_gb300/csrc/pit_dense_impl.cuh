@@ -646,7 +646,9 @@ k_dtree_neutral(const DenseParams<T> p, T* __restrict__ items, int64_t first, in
 // One level of the tree.  UP: item[i] = item[j] (op) item[i]; DOWN: t = item[j], item[j] =
 // item[i], item[i] = item[i] (op) t.  Pair k of the level: i = (k+1) 2 s - 1, j = i - s.
 // Position order op: filter x (x)_f y; smoothing (reversed chains) y (x)_s x.
-template <typename T, bool FILTER, bool UP, bool WITH_L>
+// FULL: the filter's down-sweep forms whole prefixes (A, b, C, eta, J) instead of b and C only
+// (the generic element scan, whose outputs are the prefixes themselves).
+template <typename T, bool FILTER, bool UP, bool WITH_L, bool FULL = false>
 __global__ void __launch_bounds__(NT, 1)
 k_dtree_level(const DenseParams<T> p, T* __restrict__ items, int64_t s, T* __restrict__ scratch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -674,12 +676,12 @@ k_dtree_level(const DenseParams<T> p, T* __restrict__ items, int64_t s, T* __res
       for (int64_t e = threadIdx.x; e < sz; e += NT) xj[e] = xi[e];
       return;
     }
-    if (FILTER) dcombine_f<T, true>(p, xi, xj, res, scr, sm);
+    if (FILTER) dcombine_f<T, !FULL>(p, xi, xj, res, scr, sm);
     else dcombine_s<T, WITH_L>(p, xj, xi, res, scr, sm);
     for (int64_t e = threadIdx.x; e < sz; e += NT) xj[e] = xi[e];
     __syncthreads();
   }
-  if (FILTER && !UP) {
+  if (FILTER && !UP && !FULL) {
     // values-only result: b and C
     const int64_t DD = static_cast<int64_t>(D) * D;
     for (int64_t e = threadIdx.x; e < DD + D; e += NT) xi[DD + e] = res[DD + e];
@@ -695,7 +697,7 @@ k_dtree_level(const DenseParams<T> p, T* __restrict__ items, int64_t s, T* __res
 // to a running prefix is conditioned like the sequential filter; tree levels above the groups
 // would instead form elements whose flow maps span up to the whole interval, whose rounding
 // strongly unstable linearisations amplify.  pre, tot: two item-sized buffers.
-template <typename T, bool FILTER, bool WITH_L>
+template <typename T, bool FILTER, bool WITH_L, bool FULL = false>
 __global__ void __launch_bounds__(NT, 1)
 k_dtree_seq(const DenseParams<T> p, T* __restrict__ items, int64_t G, int64_t ngroups,
             T* __restrict__ pre, T* __restrict__ tot, T* __restrict__ scratch) {
@@ -722,10 +724,13 @@ k_dtree_seq(const DenseParams<T> p, T* __restrict__ items, int64_t G, int64_t ng
     }
     __syncthreads();
     if (pos + 1 >= P) break;      // no later group holds a chain
-    if (FILTER) {
+    if (FILTER && !FULL) {
       dcombine_f<T, true>(p, pre, tot, res, scratch, sm);
       const int64_t DD = static_cast<int64_t>(D) * D;
       for (int64_t e = threadIdx.x; e < DD + D; e += NT) pre[DD + e] = res[DD + e];
+    } else if (FILTER) {
+      dcombine_f<T, false>(p, pre, tot, res, scratch, sm);
+      for (int64_t e = threadIdx.x; e < sz; e += NT) pre[e] = res[e];
     } else {
       dcombine_s<T, WITH_L>(p, tot, pre, res, scratch, sm);
       for (int64_t e = threadIdx.x; e < sz; e += NT) pre[e] = res[e];
@@ -1205,7 +1210,7 @@ struct DenseSolver {
 
   // Chain-aggregate scan: Brent-Kung up-sweep inside groups of kTreeGroup positions, a
   // sequential look-back over the group totals (k_dtree_seq), Blelloch down-sweep inside groups.
-  template <bool FILTER, bool WITH_L>
+  template <bool FILTER, bool WITH_L, bool FULL = false>
   static int tree(const DenseParams<T>& p, T* items, T* seq, T* scratch, size_t sm,
                   cudaStream_t s) {
     const int64_t P2 = pow2_at_least(p.P);
@@ -1216,13 +1221,13 @@ struct DenseSolver {
       PIT_LAUNCH(kc, s, (k_dtree_neutral<T, FILTER><<<static_cast<unsigned>(std::min<int64_t>(P2 - p.P, 1024)), NT, 0, s>>>(p, items, p.P, P2)));
     for (int64_t st = 1; st < G; st *= 2) {
       const unsigned grid = static_cast<unsigned>(P2 / (2 * st));
-      PIT_LAUNCH(kc, s, (k_dtree_level<T, FILTER, true, WITH_L><<<grid, NT, sm, s>>>(p, items, st, scratch)));
+      PIT_LAUNCH(kc, s, (k_dtree_level<T, FILTER, true, WITH_L, FULL><<<grid, NT, sm, s>>>(p, items, st, scratch)));
     }
     const int64_t fs = fitem(p.D);
-    PIT_LAUNCH(kd, s, (k_dtree_seq<T, FILTER, WITH_L><<<1, NT, sm, s>>>(p, items, G, P2 / G, seq, seq + fs, scratch)));
+    PIT_LAUNCH(kd, s, (k_dtree_seq<T, FILTER, WITH_L, FULL><<<1, NT, sm, s>>>(p, items, G, P2 / G, seq, seq + fs, scratch)));
     for (int64_t st = G / 2; st >= 1; st /= 2) {
       const unsigned grid = static_cast<unsigned>(P2 / (2 * st));
-      PIT_LAUNCH(kd, s, (k_dtree_level<T, FILTER, false, WITH_L><<<grid, NT, sm, s>>>(p, items, st, scratch)));
+      PIT_LAUNCH(kd, s, (k_dtree_level<T, FILTER, false, WITH_L, FULL><<<grid, NT, sm, s>>>(p, items, st, scratch)));
     }
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
@@ -1443,6 +1448,235 @@ struct DenseSolver {
     info.kernel_launches = launches_total() - launches0;
     if (a.info) *a.info = info;
     return converged ? PIT_OK : PIT_ENOCONV;
+  }
+};
+
+
+// ---- generic element scans (pit_filter_scan / pit_smooth_scan for any D <= 256) -------------
+// Inclusive scans of caller-built elements with the block-level operators of the solver's trees:
+// each block folds its chain of elements, the chain aggregates are scanned (tree inside groups
+// plus look-back, whole prefixes), and each block folds its chain again from its prefix,
+// writing every prefix in place.  Element C (filter) and L (smoothing) are triangularised on
+// load, which the operators need of the operands they take them from.
+template <typename T>
+__device__ __forceinline__ void load_felem(const DenseParams<T>& p, int64_t n, const T* A, const T* b,
+                                           const T* Cm, const T* eta, const T* J, T* el, T* sm) {
+  const int D = p.D;
+  const int64_t DD = static_cast<int64_t>(D) * D;
+  for (int64_t e = threadIdx.x; e < DD; e += NT) {
+    el[e] = A[n * DD + e];
+    el[DD + D + e] = Cm[n * DD + e];
+    el[2 * DD + 2 * D + e] = J[n * DD + e];
+  }
+  for (int i = threadIdx.x; i < D; i += NT) {
+    el[DD + i] = b[n * D + i];
+    el[2 * DD + D + i] = eta[n * D + i];
+  }
+  __syncthreads();
+  cta_lq<T>(el + DD + D, D, D, D, 0, D, sm, p.wsmax);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 1)
+k_dgen_filter(const DenseParams<T> p, int64_t N, T* __restrict__ A, T* __restrict__ b,
+              T* __restrict__ Cm, T* __restrict__ eta, T* __restrict__ J, T* __restrict__ items,
+              int down, T* __restrict__ scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int64_t chain = blockIdx.x;
+  if (chain >= p.P) return;
+  const int D = p.D;
+  const int64_t DD = static_cast<int64_t>(D) * D, sz = fitem(D);
+  const TreeLayout tl(D);
+  T* scr = scratch + chain * p.chain_elems;
+  T* res = scr + tl.out;
+  T* acc = scr + tl.total;
+  T* el = acc + sz;
+  for (int64_t e = threadIdx.x; e < sz; e += NT) {
+    T v = down ? items[chain * sz + e] : T(0);
+    if (!down && e < DD) v = (e / D == e % D) ? T(1) : T(0);
+    acc[e] = v;
+  }
+  __syncthreads();
+  const int64_t n0 = chain * p.L, n1 = min(chain * p.L + p.L, N);
+  for (int64_t n = n0; n < n1; ++n) {
+    load_felem<T>(p, n, A, b, Cm, eta, J, el, sm);
+    dcombine_f<T, false>(p, acc, el, res, scr, sm);
+    for (int64_t e = threadIdx.x; e < sz; e += NT) acc[e] = res[e];
+    __syncthreads();
+    if (down) {
+      for (int64_t e = threadIdx.x; e < DD; e += NT) {
+        A[n * DD + e] = acc[e];
+        Cm[n * DD + e] = acc[DD + D + e];
+        J[n * DD + e] = acc[2 * DD + 2 * D + e];
+      }
+      for (int i = threadIdx.x; i < D; i += NT) {
+        b[n * D + i] = acc[DD + i];
+        eta[n * D + i] = acc[2 * DD + D + i];
+      }
+      __syncthreads();
+    }
+  }
+  if (!down)
+    for (int64_t e = threadIdx.x; e < sz; e += NT) items[chain * sz + e] = acc[e];
+}
+
+template <typename T, bool WITH_L>
+__global__ void __launch_bounds__(NT, 1)
+k_dgen_smooth(const DenseParams<T> p, int64_t N, T* __restrict__ E, T* __restrict__ gv,
+              T* __restrict__ Lm, T* __restrict__ items, int down, T* __restrict__ scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int64_t chain = blockIdx.x;
+  if (chain >= p.P) return;
+  const int D = p.D;
+  const int64_t DD = static_cast<int64_t>(D) * D, sz = sitem(D);
+  const TreeLayout tl(D);
+  T* scr = scratch + chain * p.chain_elems;
+  T* res = scr + tl.out;
+  T* acc = scr + tl.total;
+  T* el = acc + fitem(D);
+  for (int64_t e = threadIdx.x; e < sz; e += NT) {
+    T v = down ? items[chain * sz + e] : T(0);
+    if (!down && e < DD) v = (e / D == e % D) ? T(1) : T(0);
+    acc[e] = v;
+  }
+  __syncthreads();
+  auto load = [&](int64_t n) {
+    for (int64_t e = threadIdx.x; e < DD; e += NT) {
+      el[e] = E[n * DD + e];
+      el[DD + D + e] = WITH_L ? Lm[n * DD + e] : T(0);
+    }
+    for (int i = threadIdx.x; i < D; i += NT) el[DD + i] = gv[n * D + i];
+    __syncthreads();
+    if (WITH_L) cta_lq<T>(el + DD + D, D, D, D, 0, D, sm, p.wsmax);
+  };
+  const int64_t n0 = chain * p.L, n1 = min(chain * p.L + p.L, N);
+  if (!down) {
+    for (int64_t n = n0; n < n1; ++n) {   // acc = b_n0 (x) ... (x) b_{n1-1}
+      load(n);
+      dcombine_s<T, WITH_L>(p, acc, el, res, scr, sm);
+      for (int64_t e = threadIdx.x; e < sz; e += NT) acc[e] = res[e];
+      __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < sz; e += NT) items[chain * sz + e] = acc[e];
+  } else {
+    for (int64_t n = n1 - 1; n >= n0; --n) {  // acc = b_n (x) acc
+      load(n);
+      dcombine_s<T, WITH_L>(p, el, acc, res, scr, sm);
+      for (int64_t e = threadIdx.x; e < sz; e += NT) acc[e] = res[e];
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < DD; e += NT) {
+        E[n * DD + e] = acc[e];
+        if (WITH_L) Lm[n * DD + e] = acc[DD + D + e];
+      }
+      for (int i = threadIdx.x; i < D; i += NT) gv[n * D + i] = acc[DD + i];
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+struct DenseScan {
+  static DenseParams<T> params(int64_t N, int D) {
+    DenseParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    p.D = D;
+    p.N = N;
+    p.L = static_cast<int>(std::max<int64_t>(1, (N + 151) / 152));
+    p.P = (N + p.L - 1) / p.L;
+    p.wsmax = NB + D;
+    const TreeLayout tl(D);
+    p.chain_elems = tl.total + 2 * fitem(D);
+    return p;
+  }
+  struct Bufs {
+    T *items, *seq, *scratch;
+  };
+  static size_t carve(const ScanArgs& a, const DenseParams<T>& p, Bufs& b) {
+    Carver cv(a.workspace, a.ws_bytes);
+    int64_t P2 = 1;
+    while (P2 < p.P) P2 <<= 1;
+    b.items = cv.take<T>(P2 * fitem(p.D));
+    b.seq = cv.take<T>(2 * fitem(p.D));
+    b.scratch = cv.take<T>(std::max<int64_t>(p.P, P2 / 2) * p.chain_elems);
+    return cv.used();
+  }
+  template <class K>
+  static int attr(K k, size_t sm) {
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+    return PIT_OK;
+  }
+  static int check(const ScanArgs& a, int D, size_t need) {
+    if (a.ws_bytes < need) {
+      set_error("workspace too small: need " + std::to_string(need) + " bytes");
+      return PIT_ENOMEM;
+    }
+    if (reinterpret_cast<uintptr_t>(a.workspace) % 256 != 0) {
+      set_error("workspace must be 256-byte aligned");
+      return PIT_EINVAL;
+    }
+    return PIT_OK;
+  }
+  static int filter(const ScanArgs& a, int D, size_t* wsq) {
+    if (D > kMaxDenseD) {
+      set_error("scan: D must be <= " + std::to_string(kMaxDenseD));
+      return PIT_EUNSUPPORTED;
+    }
+    DenseParams<T> p = params(a.N, D);
+    Bufs b;
+    const size_t need = carve(a, p, b);
+    if (wsq) {
+      *wsq = need;
+      return PIT_OK;
+    }
+    int st = check(a, D, need);
+    if (st != PIT_OK) return st;
+    const size_t sm = lq_smem_elems<T>(p.wsmax) * sizeof(T);
+    if ((st = attr(k_dgen_filter<T>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_level<T, true, true, false, true>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_level<T, true, false, false, true>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_seq<T, true, false, true>, sm)) != PIT_OK) return st;
+    T *A = (T*)a.x0, *bb = (T*)a.x1, *Cm = (T*)a.x2, *eta = (T*)a.x3, *J = (T*)a.x4;
+    const unsigned grid = static_cast<unsigned>(p.P);
+    PIT_LAUNCH(KC_SCAN_FILTER, a.stream, (k_dgen_filter<T><<<grid, NT, sm, a.stream>>>(p, a.N, A, bb, Cm, eta, J, b.items, 0, b.scratch)));
+    st = DenseSolver<T>::template tree<true, false, true>(p, b.items, b.seq, b.scratch, sm, a.stream);
+    if (st != PIT_OK) return st;
+    PIT_LAUNCH(KC_SCAN_FILTER, a.stream, (k_dgen_filter<T><<<grid, NT, sm, a.stream>>>(p, a.N, A, bb, Cm, eta, J, b.items, 1, b.scratch)));
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+  template <bool WITH_L>
+  static int smooth_t(const ScanArgs& a, int D, size_t* wsq) {
+    if (D > kMaxDenseD) {
+      set_error("scan: D must be <= " + std::to_string(kMaxDenseD));
+      return PIT_EUNSUPPORTED;
+    }
+    DenseParams<T> p = params(a.N, D);
+    Bufs b;
+    const size_t need = carve(a, p, b);
+    if (wsq) {
+      *wsq = need;
+      return PIT_OK;
+    }
+    int st = check(a, D, need);
+    if (st != PIT_OK) return st;
+    const size_t sm = lq_smem_elems<T>(p.wsmax) * sizeof(T);
+    if ((st = attr(k_dgen_smooth<T, WITH_L>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_level<T, false, true, WITH_L>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_level<T, false, false, WITH_L>, sm)) != PIT_OK) return st;
+    if ((st = attr(k_dtree_seq<T, false, WITH_L>, sm)) != PIT_OK) return st;
+    T *E = (T*)a.x0, *g = (T*)a.x1, *Lm = (T*)a.x2;
+    const unsigned grid = static_cast<unsigned>(p.P);
+    PIT_LAUNCH(KC_SCAN_SMOOTH, a.stream, (k_dgen_smooth<T, WITH_L><<<grid, NT, sm, a.stream>>>(p, a.N, E, g, Lm, b.items, 0, b.scratch)));
+    st = DenseSolver<T>::template tree<false, WITH_L>(p, b.items, b.seq, b.scratch, sm, a.stream);
+    if (st != PIT_OK) return st;
+    PIT_LAUNCH(KC_SCAN_SMOOTH, a.stream, (k_dgen_smooth<T, WITH_L><<<grid, NT, sm, a.stream>>>(p, a.N, E, g, Lm, b.items, 1, b.scratch)));
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+  static int smooth(const ScanArgs& a, int D, size_t* wsq) {
+    return a.want_L ? smooth_t<true>(a, D, wsq) : smooth_t<false>(a, D, wsq);
   }
 };
 

@@ -41,6 +41,7 @@ struct SolveArgs {
 
 struct ScanArgs {
   int64_t N;
+  int D;       // state dimension of the elements
   void* x0;  // A or E
   void* x1;  // b or g
   void* x2;  // C or L
@@ -105,7 +106,10 @@ struct Registrar {
 };
 struct DenseRegistrar {
   DenseRegistrar(int dtype, SolveFn fn);
+  DenseRegistrar(int dtype, ScanFn filter_fn, ScanFn smooth_fn);  // generic element scans
 };
+// Element scans of the large-state kernels (any D <= 256; ScanArgs::D gives D).
+ScanFn find_dense_scan(int dtype, bool filter);
 struct ScanRegistrar {
   ScanRegistrar(int dtype, int D, ScanFn filter_fn, ScanFn smooth_fn);
 };

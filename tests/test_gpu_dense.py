@@ -202,3 +202,51 @@ def test_lorenz96_full_size_parallel_shape(pit, N):
     assert rel(_np(r.mean)[g["n"]], g["means"]) < 1e-10
     assert r.deltas[0] == pytest.approx(float(g["delta"]), rel=1e-10)
     assert r.sigma2 == pytest.approx(float(g["sigma2"]), rel=1e-9)
+
+
+# ---- generic element scans on the large-state kernels (D outside the lane-group set) -----------
+def _elements(p):
+    from oracle import filtering
+    from oracle.taylor import initial_state
+    D, q, N = p.D, p.q, p.N
+    Phi, Q, sQ = ieks.prior_factors(p)
+    mu0 = initial_state(p.kind, p.params, p.y0, q)
+    Hs, ds = ieks.linearize_all(p, np.tile(mu0, (N + 1, 1)))
+    el = filtering.filtering_elements(mu0, np.zeros((D, D)), Phi, sQ, Hs, ds)
+    mf, sPf, _, _ = filtering.sequential_filter(mu0, np.zeros((D, D)), Phi, sQ, Hs, ds)
+    ms, sPs = filtering.rts_smoother(mf, sPf, Phi, sQ)
+    be = filtering.smoothing_elements(mf, sPf, Phi, sQ)
+    return el, mf, sPf, be, ms, sPs
+
+
+@pytest.mark.parametrize("p,dtype,tm,tc", [
+    (W.lorenz96(d=8, N=300, q=2), torch.float64, 1e-10, 1e-10),
+    (W.lorenz96(d=16, N=77, q=2), torch.float64, 1e-10, 1e-10),
+    (W.affine([[-1.0, 0.3, 0.0, 0.2, 0.1], [0.1, -0.5, 0.2, 0.0, 0.0], [0.0, 0.1, -0.7, 0.3, 0.0],
+               [0.0, 0.0, 0.2, -0.4, 0.1], [0.2, 0.0, 0.0, 0.1, -0.9]],
+              [0.1, -0.2, 0.3, 0.0, 0.5], [1.0, 0.5, -0.5, 0.2, 0.0], t1=3.0, N=500, q=2),
+     torch.float64, 1e-10, 1e-10),
+    (W.lorenz96(d=8, N=300, q=2, F=0.5), torch.float32, 1e-4, 1e-4),
+], ids=["l96_d8_f64", "l96_d16_f64", "affine_d5_f64", "l96_d8_F05_f32"])
+def test_filter_and_smooth_scans_large_state(pit, p, dtype, tm, tc):
+    """pit_filter_scan / pit_smooth_scan for D = 24, 48, 15 (the large-state kernels) on
+    elements the oracle builds (Eqs. sqrt-filtering-elements, sqrt-smoothing-elements): the
+    prefixes are the oracle's sequential filter and smoother marginals."""
+    el, mf, sPf, be, ms, sPs = _elements(p)
+    dev = "cuda"
+    T = lambda k: torch.tensor(np.stack([e[k] for e in el[1:]]), dtype=dtype, device=dev)
+    A, b, C, eta, J = (T(k) for k in range(5))
+    pit.pit_filter_scan(A, b, C, eta, J)
+    torch.cuda.synchronize()
+    assert rel(_np(b), mf[1:]) < tm
+    assert rel(cov(_np(C)), cov(sPf[1:])) < tc
+    U = lambda k: torch.tensor(np.stack([x[k] for x in be]), dtype=dtype, device=dev)
+    E, g, L = U(0), U(1), U(2)
+    pit.pit_smooth_scan(E, g, L)
+    torch.cuda.synchronize()
+    assert rel(_np(g), ms) < tm
+    assert rel(cov(_np(L)), cov(sPs)) < tc
+    E2, g2 = U(0), U(1)
+    pit.pit_smooth_scan(E2, g2, None)
+    torch.cuda.synchronize()
+    assert rel(_np(g2), ms) < tm
