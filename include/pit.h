@@ -185,7 +185,8 @@ int32_t pit_init_state(const pit_ode* ode, int32_t q, const double* y0, double* 
  *   H_n = E1 - F_y(E0 traj_n, t_n) E0,   d_n = f(E0 traj_n, t_n) - F_y(E0 traj_n, t_n) E0 traj_n
  * for n = 1..N.  traj: device, (N+1) x D, original coordinates (row n = linearisation point at
  * t_n; row 0 is not read).  H: device, N x d x D (row n-1 holds H_n); dvec: device, N x d.
- * Asynchronous.  Errors: PIT_EINVAL for bad sizes/pointers, PIT_EUNSUPPORTED if d > 16. */
+ * Asynchronous.  Errors: PIT_EINVAL for bad sizes/pointers, PIT_EUNSUPPORTED for a family with
+ * more than 32 parameters (the affine family beyond d = 5; pit_solve linearises it itself). */
 int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
                       const void* traj, void* H, void* dvec, void* stream);
 

@@ -568,8 +568,8 @@ int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32
     case 3: return f64 ? launch_linearize<double, 3>(pb, traj, H, dvec, s)
                        : launch_linearize<float, 3>(pb, traj, H, dvec, s);
     default:
-      set_error("pit_linearize: compiled for d <= 3");
-      return PIT_EUNSUPPORTED;
+      return f64 ? dense_linearize_f64(pb, traj, H, dvec, s)
+                 : dense_linearize_f32(pb, traj, H, dvec, s);
   }
 }
 

@@ -9,4 +9,7 @@ int scan_f_f32(const ScanArgs& a, size_t* w) { return dn::DenseScan<float>::filt
 int scan_s_f32(const ScanArgs& a, size_t* w) { return dn::DenseScan<float>::smooth(a, a.D, w); }
 DenseRegistrar reg_dense_scan_f32(PIT_F32, scan_f_f32, scan_s_f32);
 }  // namespace
+int dense_linearize_f32(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
+  return dn::dense_linearize<float>(pb, traj, H, dv, s);
+}
 }  // namespace pit

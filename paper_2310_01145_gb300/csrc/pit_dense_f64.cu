@@ -9,4 +9,7 @@ int scan_f_f64(const ScanArgs& a, size_t* w) { return dn::DenseScan<double>::fil
 int scan_s_f64(const ScanArgs& a, size_t* w) { return dn::DenseScan<double>::smooth(a, a.D, w); }
 DenseRegistrar reg_dense_scan_f64(PIT_F64, scan_f_f64, scan_s_f64);
 }  // namespace
+int dense_linearize_f64(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
+  return dn::dense_linearize<double>(pb, traj, H, dv, s);
+}
 }  // namespace pit

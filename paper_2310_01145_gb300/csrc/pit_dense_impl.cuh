@@ -1680,5 +1680,74 @@ struct DenseScan {
   }
 };
 
+
+// ---- linearisation for any d (pit_linearize beyond the lane-group families) -------------------
+// H_n = E1 - F_y(E0 traj_n) E0 and d_n = f - F_y y at every n = 1..N (Section 3.2.1), one thread
+// per (n, component); the family's parameters travel in the kernel argument.
+struct LinArgs {
+  int kind, d, Q1, n_params;
+  double pd[kMaxParams];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dlinearize(const LinArgs a, int64_t N, const T* __restrict__ traj, T* __restrict__ H,
+             T* __restrict__ dv) {
+  double pd[kMaxParams];
+  T pt[kMaxParams];
+  for (int i = 0; i < kMaxParams; ++i) {
+    pd[i] = a.pd[i];
+    pt[i] = static_cast<T>(a.pd[i]);
+  }
+  DenseParams<T> p{};
+  p.kind = a.kind;
+  p.d = a.d;
+  p.Q1 = a.Q1;
+  p.D = a.d * a.Q1;
+  p.n_params = a.n_params;
+  p.lin_mode = 0;
+  p.pd = pd;
+  p.pt = pt;
+  const int d = a.d, Q1 = a.Q1, D = d * Q1;
+  const int64_t total = N * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = 1 + e / d;
+    const int k = static_cast<int>(e % d);
+    T y[kMaxOdeDim];
+    for (int m = 0; m < d; ++m) y[m] = traj[n * D + m * Q1];
+    T* Hr = H + ((n - 1) * d + k) * D;
+    for (int c = 0; c < D; ++c) Hr[c] = T(0);
+    Hr[k * Q1 + 1] = T(1);
+    T acc = dense_f<T, T>(a.kind, pd, d, k, [&](int j) { return y[j]; });
+    for (int m = 0; m < d; ++m) {
+      const T F = jac_entry<T>(p, y, k, m);
+      Hr[m * Q1] -= F;
+      acc -= F * y[m];
+    }
+    dv[(n - 1) * d + k] = acc;
+  }
+}
+
+template <typename T>
+int dense_linearize(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
+  if (pb.n_params > kMaxParams) {
+    set_error("pit_linearize: families with more than " + std::to_string(kMaxParams) +
+              " parameters (affine beyond d = 5) are linearised inside pit_solve only");
+    return PIT_EUNSUPPORTED;
+  }
+  LinArgs a{};
+  a.kind = pb.kind;
+  a.d = pb.d;
+  a.Q1 = pb.q + 1;
+  a.n_params = pb.n_params;
+  for (int i = 0; i < pb.n_params; ++i) a.pd[i] = pb.params[i];
+  const int64_t total = pb.N * pb.d;
+  const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16)));
+  PIT_LAUNCH(KC_LINEARIZE, s, (k_dlinearize<T><<<grid, 256, 0, s>>>(a, pb.N, static_cast<const T*>(traj), static_cast<T*>(H), static_cast<T*>(dv))));
+  PIT_CUDA_TRY(cudaGetLastError());
+  return PIT_OK;
+}
+
 }  // namespace dn
 }  // namespace pit

@@ -108,6 +108,9 @@ struct DenseRegistrar {
   DenseRegistrar(int dtype, SolveFn fn);
   DenseRegistrar(int dtype, ScanFn filter_fn, ScanFn smooth_fn);  // generic element scans
 };
+// pit_linearize for any d (families with at most 32 parameters).
+int dense_linearize_f32(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);
+int dense_linearize_f64(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);
 // Element scans of the large-state kernels (any D <= 256; ScanArgs::D gives D).
 ScanFn find_dense_scan(int dtype, bool filter);
 struct ScanRegistrar {

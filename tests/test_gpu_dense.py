@@ -250,3 +250,21 @@ def test_filter_and_smooth_scans_large_state(pit, p, dtype, tm, tc):
     pit.pit_smooth_scan(E2, g2, None)
     torch.cuda.synchronize()
     assert rel(_np(g2), ms) < tm
+
+
+@pytest.mark.parametrize("p", [W.lorenz96(d=8, N=50, q=2), W.lorenz96(d=64, N=20, q=2),
+                               W.affine([[-1.0, 0.2, 0.0, 0.1], [0.3, -0.5, 0.1, 0.0],
+                                         [0.0, 0.2, -0.3, 0.1], [0.1, 0.0, 0.2, -0.8]],
+                                        [0.1, 0.2, -0.1, 0.0], [1.0, 0.0, 0.5, -0.5], N=30, q=3)],
+                         ids=["l96_d8", "l96_d64", "affine_d4"])
+def test_linearize_any_d(pit, p):
+    """pit_linearize for d > 3 (H_n = E1 - F E0, d_n = f - F y; Section 3.2.1) against the
+    oracle's, at a random trajectory."""
+    rng = np.random.default_rng(1)
+    traj = rng.standard_normal((p.N + 1, p.D))
+    Hs, ds = ieks.linearize_all(p, traj)
+    H, dv = pit.pit_linearize(pit.ode_from_problem(p), p.t0, p.t1, p.N, p.q,
+                              torch.tensor(traj, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(H.cpu().numpy(), np.stack(Hs[1:]), rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(dv.cpu().numpy(), np.stack(ds[1:]), rtol=1e-13, atol=1e-13)
