@@ -252,9 +252,9 @@ int32_t pit_solve(const pit_ode* ode, const pit_grid* grid, int32_t q, const dou
                   const pit_opts* opts, const void* init_traj, void* mean, void* sqrtcov,
                   pit_solve_info* info, void* workspace, size_t ws_bytes, void* stream);
 
-/* ParaIEKS (Algorithm 2) on a non-uniform grid t_0 < t_1 < ... < t_N (Section 3.2.2 remarks
- * that the method is not tied to uniform grids; the IWP transitions of Section 2.1 are taken
- * for each step length h_n = t_n - t_{n-1}).  Solved by the large-state kernels for any d, with
+/* ParaIEKS (Algorithm 2) on a non-uniform grid t_0 < t_1 < ... < t_N (the method is stated on a
+ * general grid: Sections 2.3 and 3.1 take the IWP transitions Phi(t_{n+1} - t_n),
+ * Q(t_{n+1} - t_n) of Section 2.1 per step, Algorithm 2 a time grid).  Solved by the large-state kernels for any d, with
  * per-step preconditioning: in coordinates x_n = T(h_n) xbar_n (Section 2.4) the step into t_n
  * is xbar_n = Phibar diag(T(h_{n-1}) / T(h_n)) xbar_{n-1} + w, w ~ N(0, Qbar), h_0 = h_1.
  *   t                  host, N+1 grid points, finite and strictly increasing

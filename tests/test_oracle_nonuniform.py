@@ -1,5 +1,5 @@
-"""Pins of the oracle on non-uniform grids (Section 3.2.2 remark on other grids; the IWP
-transitions of Section 2.1 for each step length)."""
+"""Pins of the oracle on non-uniform grids (Sections 2.3 and 3.1 state the method on a general
+grid, with the IWP transitions of Section 2.1 for each step length)."""
 import math
 
 import numpy as np
