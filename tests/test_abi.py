@@ -196,3 +196,17 @@ def test_solve_grid_validation(pit):
                                                10, 2, ctypes.byref(opts), ctypes.byref(sz))
         assert st == 1
         assert b"strictly increasing" in lib.pit_last_error()
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: the binding raises when libpit.so is absent (fresh process)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2310_01145_gb300 as P\n"
+            "try:\n"
+            "    P.load('/nonexistent/libpit.so')\n"
+            "except ImportError as e:\n"
+            "    print('raised', e)\n") % ROOT
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised" in out.stdout, out.stdout + out.stderr
