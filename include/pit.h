@@ -355,7 +355,9 @@ int32_t pit_solve_batched(int32_t B, const pit_ode* odes, const pit_grid* grids,
  * parallel filter and smoother of Algorithm 1, as pit_solve_batched) over every request in
  * flight -- each class on its own CUDA stream, so the classes' kernels overlap -- and retires
  * the requests whose stopping rule holds (as pit_solve: max|change of E0 mean| <= atol + rtol
- * max|E0 mean|, or max_iter iterations, or divergence as in pit_solve_batched).  A request's
+ * max|E0 mean|, or max_iter iterations, or divergence as in pit_solve_batched).  Classes with
+ * d > 3 (e.g. Lorenz-96) run on the large-state kernels: each such request has its own workspace
+ * in the budget and takes one iteration per step on its class's stream.  A request's
  * trajectory stays in device memory from admission to retirement; the host reads back only
  * the per-request change statistics once per step.  Retired requests deliver their smoothing
  * means (original coordinates) and diffusion estimate; covariances are not served.
@@ -401,7 +403,8 @@ int32_t pit_server_create(const pit_server_config* cfg, pit_server** out);
  * the server's dtype, written when the request retires; the caller keeps it alive until then.
  * request_id (host, may be NULL) receives the request's id.  The first request of a class sets
  * up its kernels and workspace.  Errors: PIT_EINVAL (arguments, N + 1 above max_points),
- * PIT_EUNSUPPORTED (no compiled kernels), PIT_ENOMEM (budget cannot hold another class). */
+ * PIT_EUNSUPPORTED (no compiled kernels), PIT_ENOMEM (budget cannot hold another class, or a
+ * d > 3 request needs more device memory than the whole budget). */
 int32_t pit_server_submit(pit_server* server, const pit_ode* ode, const pit_grid* grid,
                           int32_t q, const double* y0, void* mean_out, uint64_t tag,
                           int64_t* request_id);

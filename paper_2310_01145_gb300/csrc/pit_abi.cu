@@ -98,6 +98,7 @@ struct Registry {
   std::map<int, SolveFn> solvers;  // key variant*100000 + dtype*10000 + d*100 + q
   std::map<int, SolveFn> dense;    // key dtype
   std::map<int, ScanFn> dense_scans;  // key dtype*2 + (filter ? 1 : 0)
+  std::map<int, LargeSessionFactory> sessions;  // key dtype
   std::map<int, ScanFn> fscans;    // key dtype*100 + D
   std::map<int, ScanFn> sscans;
 };
@@ -126,6 +127,22 @@ ScanFn find_dense_scan(int dtype, bool filter) {
   std::lock_guard<std::mutex> lk(r.mu);
   auto it = r.dense_scans.find(dtype * 2 + (filter ? 1 : 0));
   return it == r.dense_scans.end() ? nullptr : it->second;
+}
+LargeSessionRegistrar::LargeSessionRegistrar(int dtype, LargeSessionFactory f) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  r.sessions[dtype] = f;
+}
+LargeSessionFactory find_large_session(int dtype) {
+  Registry& r = registry();
+  std::lock_guard<std::mutex> lk(r.mu);
+  auto it = r.sessions.find(dtype);
+  return it == r.sessions.end() ? nullptr : it->second;
+}
+size_t large_session_bytes_f32(const Problem& pb, const pit_opts& o);
+size_t large_session_bytes_f64(const Problem& pb, const pit_opts& o);
+size_t large_session_bytes(int dtype, const Problem& pb, const pit_opts& o) {
+  return dtype == PIT_F64 ? large_session_bytes_f64(pb, o) : large_session_bytes_f32(pb, o);
 }
 SolveFn find_dense_solver(int dtype) {
   Registry& r = registry();

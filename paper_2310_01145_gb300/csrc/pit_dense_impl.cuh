@@ -1187,8 +1187,12 @@ struct DenseSolver {
     return lq_smem_elems<T>(p.wsmax) * sizeof(T);
   }
 
-  static int set_attrs(size_t sm) {
-    const int s = static_cast<int>(sm);
+  // The attribute is a per-kernel cap shared by every solve, session and scan in the process,
+  // so it is always raised to the largest panel width the engine accepts: a call with a smaller
+  // D must not lower it under another (e.g. a serving class with larger D) still launching.
+  static size_t max_smem_bytes() { return lq_smem_elems<T>(MAXWS) * sizeof(T); }
+  static int set_attrs(size_t) {
+    const int s = static_cast<int>(max_smem_bytes());
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_dreduce<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_ddown<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_ddown<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));
@@ -1452,6 +1456,90 @@ struct DenseSolver {
 };
 
 
+// ---- a serving-loop request on the large-state kernels (see LargeSession) ----------------------
+template <typename T>
+class DenseSession final : public LargeSession {
+ public:
+  using S = DenseSolver<T>;
+  using V = Vt<T>;
+  static SolveArgs args(const Problem& pb, const pit_opts& o, void* ws, size_t bytes,
+                        cudaStream_t s) {
+    SolveArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pb = pb;
+    a.opts = o;
+    a.opts.want_cov = 0;
+    a.opts.init_coarse = 0;
+    a.opts.objective = 0;
+    a.opts.atol_objective = a.opts.rtol_objective = 0;
+    a.workspace = ws;
+    a.ws_bytes = bytes;
+    a.stream = s;
+    return a;
+  }
+  static size_t bytes(const Problem& pb, const pit_opts& o) {
+    size_t need = 0;
+    const SolveArgs a = args(pb, o, nullptr, 0, nullptr);
+    if (S::run(a, &need, false) != PIT_OK) return 0;
+    return need;
+  }
+  int start(const Problem& pb, const pit_opts& o, void* ws, size_t nbytes,
+            cudaStream_t s) override {
+    a_ = args(pb, o, ws, nbytes, s);
+    std::vector<double> mu0pre, mu0orig;
+    int st = S::fill_params(a_, p_, mu0pre, &mu0orig);
+    if (st != PIT_OK) return st;
+    const size_t need = S::carve(a_, p_, false, b_);
+    if (nbytes < need) {
+      set_error("large-state session: workspace too small");
+      return PIT_ENOMEM;
+    }
+    sm_ = S::smem_bytes(p_);
+    st = S::set_attrs(sm_);
+    if (st != PIT_OK) return st;
+    std::vector<T> pt(std::max(1, pb.n_params));
+    for (int i = 0; i < pb.n_params; ++i) pt[i] = static_cast<T>(pb.params[i]);
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.pd, pb.params, sizeof(double) * std::max(1, pb.n_params),
+                                 cudaMemcpyHostToDevice, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.pt, pt.data(), sizeof(T) * pt.size(), cudaMemcpyHostToDevice, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.mu0d, mu0pre.data(), sizeof(double) * p_.D, cudaMemcpyHostToDevice, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.mu0o, mu0orig.data(), sizeof(double) * p_.D, cudaMemcpyHostToDevice, s));
+    p_.pd = b_.pd;
+    p_.pt = b_.pt;
+    p_.mu0d = b_.mu0d;
+    p_.mu0o = b_.mu0o;
+    const int64_t total = (p_.N + 1) * p_.D;
+    PIT_LAUNCH(KC_INIT, s, (k_dinit_traj<T><<<S::elem_grid(total, 256), 256, 0, s>>>(p_, nullptr, b_.linA)));
+    PIT_CUDA_TRY(cudaGetLastError());
+    cur_ = b_.linA;
+    nxt_ = b_.linB;
+    return PIT_OK;
+  }
+  int iterate(LargeScalars* host, cudaStream_t s) override {
+    static_assert(sizeof(LargeScalars) == sizeof(SolveScalars), "scalar layouts differ");
+    PIT_LAUNCH(KC_RESIDUALS, s, (k_dres<T><<<S::elem_grid((p_.N + 1) * p_.d, 256), 256, 0, s>>>(p_, cur_, b_.U, b_.R, b_.Yv, b_.d0)));
+    int st = S::template pass<false>(p_, b_, cur_, nxt_, nullptr, nullptr, false, sm_, s);
+    if (st != PIT_OK) return st;
+    PIT_CUDA_TRY(cudaMemcpyAsync(host, b_.scal, sizeof(SolveScalars), cudaMemcpyDeviceToHost, s));
+    return PIT_OK;
+  }
+  void advance() override { std::swap(cur_, nxt_); }
+  int export_means(void* mean, bool diverged, cudaStream_t s) override {
+    const int64_t total = (p_.N + 1) * p_.D;
+    PIT_LAUNCH(KC_EXPORT, s, (k_dexport<T><<<S::elem_grid(total, 256), 256, 0, s>>>(p_, diverged ? cur_ : nxt_, static_cast<T*>(mean))));
+    PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+ private:
+  SolveArgs a_{};
+  DenseParams<T> p_{};
+  typename S::Buffers b_{};
+  size_t sm_ = 0;
+  V* cur_ = nullptr;
+  V* nxt_ = nullptr;
+};
+
 // ---- generic element scans (pit_filter_scan / pit_smooth_scan for any D <= 256) -------------
 // Inclusive scans of caller-built elements with the block-level operators of the solver's trees:
 // each block folds its chain of elements, the chain aggregates are scanned (tree inside groups
@@ -1603,8 +1691,9 @@ struct DenseScan {
     return cv.used();
   }
   template <class K>
-  static int attr(K k, size_t sm) {
-    PIT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  static int attr(K k, size_t) {
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(DenseSolver<T>::max_smem_bytes())));
     return PIT_OK;
   }
   static int check(const ScanArgs& a, int D, size_t need) {

@@ -108,6 +108,34 @@ struct DenseRegistrar {
   DenseRegistrar(int dtype, SolveFn fn);
   DenseRegistrar(int dtype, ScanFn filter_fn, ScanFn smooth_fn);  // generic element scans
 };
+// One request of the serving loop on the large-state kernels (d > 3): its workspace (from the
+// server's pool) holds the trajectory and all scratch between iterations; each iterate() enqueues
+// one IEKS iteration (residuals + filter and smoother passes) and the read-back of its
+// reductions into `host` (page-locked, LargeScalars layout); advance() makes the new iterate the
+// linearisation trajectory; export_means writes the means of the last iterate (or, after a
+// diverged pass, of the one before) in original coordinates.
+struct LargeScalars {
+  double sigma2_sum, delta_max, y_max;
+  unsigned int flags, pad;
+  double objective;
+};
+class LargeSession {
+ public:
+  virtual ~LargeSession() {}
+  virtual int start(const Problem& pb, const pit_opts& o, void* ws, size_t bytes,
+                    cudaStream_t s) = 0;
+  virtual int iterate(LargeScalars* host, cudaStream_t s) = 0;
+  virtual void advance() = 0;
+  virtual int export_means(void* mean, bool diverged, cudaStream_t s) = 0;
+};
+using LargeSessionFactory = LargeSession* (*)();
+struct LargeSessionRegistrar {
+  LargeSessionRegistrar(int dtype, LargeSessionFactory f);
+};
+LargeSessionFactory find_large_session(int dtype);
+// Workspace bytes of a large-state session (0 with the error set when the problem is invalid).
+size_t large_session_bytes(int dtype, const Problem& pb, const pit_opts& o);
+
 // pit_linearize for any d (families with at most 32 parameters).
 int dense_linearize_f32(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);
 int dense_linearize_f64(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);

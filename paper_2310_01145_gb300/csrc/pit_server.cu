@@ -92,10 +92,15 @@ struct Request {
   int cur = 0;
   int iters = 0;
   double last_delta = 0, sigma2 = 1;
+  // large-state request (d > 3): its own session and workspace in the pool
+  std::unique_ptr<LargeSession> sess;
 };
 
 struct ClassState {
   int kind = 0, d = 0, q = 0;
+  // large: requests run on the large-state kernels, one session each (no segmented engine)
+  bool large = false;
+  LargeScalars* hres = nullptr;  // page-locked, one slot per request in flight
   std::unique_ptr<SegEngine> eng;
   cudaStream_t stream = nullptr;
   size_t ws_off = 0, ws_bytes = 0;
@@ -135,6 +140,30 @@ int ensure_class(pit_server* sv, const Problem& pb, ClassState** out) {
     return PIT_OK;
   }
   SegFactory fac = find_seg_engine(sv->cfg.dtype, pb.d, pb.q);
+  if (!fac && pb.d > 3 && find_large_session(sv->cfg.dtype)) {
+    // large-state class: per-request sessions, one stream, page-locked reductions
+    ClassState cs;
+    cs.kind = pb.kind;
+    cs.d = pb.d;
+    cs.q = pb.q;
+    cs.large = true;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&cs.hres),
+                      sizeof(LargeScalars) * static_cast<size_t>(sv->cfg.max_requests),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaHostAlloc of the reduction buffer failed");
+      return PIT_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&cs.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaFreeHost(cs.hres);
+      set_error("cudaStreamCreateWithFlags failed");
+      return PIT_ECUDA;
+    }
+    for (int i = sv->cfg.max_requests - 1; i >= 0; --i) cs.free_slots.push_back(i);
+    auto res = sv->classes.emplace(key, std::move(cs));
+    *out = &res.first->second;
+    return PIT_OK;
+  }
   if (!fac) {
     set_error("no compiled segmented kernels for this (dtype, d, q)");
     return PIT_EUNSUPPORTED;
@@ -169,8 +198,57 @@ int ensure_class(pit_server* sv, const Problem& pb, ClassState** out) {
   return PIT_OK;
 }
 
+pit_opts session_opts(const pit_server* sv) {
+  pit_opts o;
+  pit_opts_default(&o);
+  o.dtype = sv->cfg.dtype;
+  o.calibrate = sv->cfg.calibrate;
+  o.chain_len = sv->cfg.chain_len;
+  o.want_cov = 0;
+  return o;
+}
+
+// Large-state class: admit (FIFO, by slots, points and pool memory), then enqueue one IEKS
+// iteration of every request in flight on the class stream.
+int begin_large(pit_server* sv, ClassState& cs) {
+  const pit_opts o = session_opts(sv);
+  while (!cs.queue.empty()) {
+    Request& r = sv->reqs[cs.queue.front()];
+    const int64_t pts = r.pb.N + 1;
+    if (cs.free_slots.empty() || cs.active_points + pts > sv->cfg.max_points) break;
+    const size_t bytes = large_session_bytes(sv->cfg.dtype, r.pb, o);
+    if (bytes == 0) return PIT_EINVAL;
+    size_t off = 0;
+    if (!sv->alloc.alloc(bytes, &off)) break;
+    std::unique_ptr<LargeSession> ss(find_large_session(sv->cfg.dtype)());
+    const int st = ss->start(r.pb, o, static_cast<char*>(sv->pool) + off, round256(bytes), cs.stream);
+    if (st != PIT_OK) {
+      sv->alloc.release(off, bytes);
+      return st;
+    }
+    r.sess = std::move(ss);
+    r.lin_off = off;
+    r.lin_bytes = bytes;
+    r.slot = cs.free_slots.back();
+    cs.free_slots.pop_back();
+    r.t_admit = now_s();
+    cs.active.push_back(r.id);
+    cs.active_points += pts;
+    cs.queue.pop_front();
+  }
+  if (cs.active.empty()) return PIT_OK;
+  for (int64_t id : cs.active) {
+    Request& r = sv->reqs[id];
+    const int st = r.sess->iterate(cs.hres + r.slot, cs.stream);
+    if (st != PIT_OK) return st;
+  }
+  cs.begun = true;
+  return PIT_OK;
+}
+
 // Admit queued requests of one class (FIFO; the head blocks until it fits) and start its pass.
 int begin_class(pit_server* sv, ClassState& cs) {
+  if (cs.large) return begin_large(sv, cs);
   std::vector<SegSlot> fresh;
   while (!cs.queue.empty()) {
     Request& r = sv->reqs[cs.queue.front()];
@@ -212,10 +290,58 @@ int begin_class(pit_server* sv, ClassState& cs) {
   return PIT_OK;
 }
 
+// Wait for a large-state class's iteration, apply the stopping rules, retire finished requests.
+int end_large(pit_server* sv, ClassState& cs) {
+  PIT_CUDA_TRY(cudaStreamSynchronize(cs.stream));
+  std::vector<int64_t> keep;
+  for (int64_t id : cs.active) {
+    Request& r = sv->reqs[id];
+    const LargeScalars& a = cs.hres[r.slot];
+    r.iters += 1;
+    r.last_delta = a.delta_max;
+    r.sigma2 = sv->cfg.calibrate ? a.sigma2_sum / (static_cast<double>(r.pb.N) * r.pb.d) : 1.0;
+    int status = -1;
+    if ((a.flags & 1u) || !(a.delta_max <= kDiverged)) {
+      status = PIT_ENONFINITE;
+    } else if (a.delta_max <= sv->cfg.atol_delta + sv->cfg.rtol_delta * a.y_max) {
+      status = PIT_OK;
+    } else if (r.iters >= sv->cfg.max_iter) {
+      status = PIT_ENOCONV;
+    }
+    if (status < 0) {
+      r.sess->advance();
+      keep.push_back(id);
+      continue;
+    }
+    const int st = r.sess->export_means(r.mean_out, status == PIT_ENONFINITE, cs.stream);
+    if (st != PIT_OK) return st;
+    PIT_CUDA_TRY(cudaStreamSynchronize(cs.stream));
+    pit_server_result out;
+    std::memset(&out, 0, sizeof(out));
+    out.request_id = r.id;
+    out.tag = r.tag;
+    out.status = status;
+    out.iterations = r.iters;
+    out.last_delta = r.last_delta;
+    out.sigma2 = r.sigma2;
+    out.t_submit = r.t_submit;
+    out.t_admit = r.t_admit;
+    out.t_done = now_s();
+    sv->done.push_back(out);
+    sv->alloc.release(r.lin_off, r.lin_bytes);
+    cs.free_slots.push_back(r.slot);
+    cs.active_points -= r.pb.N + 1;
+    sv->reqs.erase(id);
+  }
+  cs.active.swap(keep);
+  return PIT_OK;
+}
+
 // Wait for a class's pass, apply each request's stopping rule, retire the finished ones.
 int end_class(pit_server* sv, ClassState& cs) {
   if (!cs.begun) return PIT_OK;
   cs.begun = false;
+  if (cs.large) return end_large(sv, cs);
   cs.res.resize(cs.slots.size());
   int st = cs.eng->pass_end(cs.res.data(), cs.stream);
   if (st != PIT_OK) return st;
@@ -345,14 +471,25 @@ int32_t pit_server_submit(pit_server* sv, const pit_ode* ode, const pit_grid* gr
   ClassState* cs = nullptr;
   st = ensure_class(sv, r.pb, &cs);
   if (st != PIT_OK) return st;
+  if (cs->large) {
+    // a request whose workspace can never fit the budget would block its queue for good
+    const size_t bytes = large_session_bytes(sv->cfg.dtype, r.pb, session_opts(sv));
+    if (bytes == 0) return PIT_EINVAL;
+    if (bytes > sv->cfg.hbm_budget_bytes) {
+      set_error("request needs " + std::to_string(bytes) + " bytes of device memory, more than the "
+                "server's budget of " + std::to_string(sv->cfg.hbm_budget_bytes));
+      return PIT_ENOMEM;
+    }
+  }
   r.id = sv->next_id++;
   r.tag = tag;
   r.mean_out = mean_out;
   r.key = class_key(r.pb.kind, r.pb.d, r.pb.q);
   r.t_submit = now_s();
-  cs->queue.push_back(r.id);
-  sv->reqs.emplace(r.id, r);
-  if (request_id) *request_id = r.id;
+  const int64_t rid = r.id;
+  cs->queue.push_back(rid);
+  sv->reqs.emplace(rid, std::move(r));
+  if (request_id) *request_id = rid;
   return PIT_OK;
 }
 
@@ -415,6 +552,7 @@ void pit_server_destroy(pit_server* sv) {
         cudaStreamSynchronize(kv.second.stream);
         cudaStreamDestroy(kv.second.stream);
       }
+      if (kv.second.hres) cudaFreeHost(kv.second.hres);
       kv.second.eng.reset();
     }
     if (sv->pool) cudaFree(sv->pool);

@@ -126,3 +126,55 @@ def test_server_rejects_oversized_request(pit):
         sv.submit(W.logistic(N=200))
     assert ei.value.status == 1
     sv.close()
+
+
+def test_server_large_state_requests(pit):
+    """Lorenz-96 requests (d = 8, 16: the large-state kernels, one session per request, one
+    iteration per server step) served next to small-state classes and admitted while other
+    requests are in flight: each result equals the problem solved alone, FP64."""
+    reqs = [W.lorenz96(d=8, N=40, q=2), W.logistic_paper(N=200, q=2),
+            W.lorenz96(d=16, N=50, q=2, seed=3), W.van_der_pol(N=150, q=2),
+            W.lorenz96(d=8, N=70, q=2, seed=5)]
+    sv = pit.Server(dtype="f64", max_iter=40, atol_delta=1e-10, rtol_delta=0.0,
+                    hbm_budget_bytes=2 << 30, max_points=1 << 16, max_requests=16)
+    ids = [sv.submit(p, tag=i) for i, p in enumerate(reqs[:3])]
+    sv.step()
+    ids += [sv.submit(p, tag=i + 3) for i, p in enumerate(reqs[3:])]
+    done = _drain(sv)
+    assert set(done) == set(ids)
+    assert sv.stats()["classes"] == 4
+    for rid in ids:
+        r = done[rid]
+        p = reqs[r["tag"]]
+        single = pit.solve_problem(p, dtype=torch.float64, max_iter=40, atol_delta=1e-10,
+                                   want_cov=False)
+        torch.cuda.synchronize()
+        assert r["status"] == 0, r
+        assert r["iterations"] == single.iterations, (r["tag"], r["iterations"], single.iterations)
+        assert rel(r["mean"].cpu().numpy(), single.mean.cpu().numpy()) < 1e-10, r["tag"]
+        assert abs(r["sigma2"] - single.sigma2) <= 1e-9 * single.sigma2
+    sv.close()
+
+
+def test_server_large_state_fp32_vs_oracle(pit):
+    p = W.lorenz96(d=8, N=60, q=2, seed=7)
+    sv = pit.Server(dtype="f32", max_iter=30, atol_delta=1e-10, rtol_delta=1e-6,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16)
+    rid = sv.submit(p)
+    done = _drain(sv)
+    r = done[rid]
+    orc = ieks.ieks(p, fixed_iters=r["iterations"], want_cov=False, calibrate=False)
+    y = r["mean"].double().cpu().numpy()[:, 0::p.q + 1]
+    assert r["status"] == 0
+    assert rel(y, orc.means[:, 0::p.q + 1]) < 1e-5
+    sv.close()
+
+
+def test_server_rejects_large_request_beyond_budget(pit):
+    """A d > 3 request whose workspace exceeds the whole device budget is refused at submission
+    (it could never be admitted and would block its queue)."""
+    sv = pit.Server(dtype="f32", hbm_budget_bytes=64 << 20, max_points=1 << 16)
+    with pytest.raises(pit.PitError) as ei:
+        sv.submit(W.lorenz96(d=64, N=4096, q=2))
+    assert ei.value.status == 2
+    sv.close()
