@@ -33,51 +33,104 @@ __global__ void k_init_traj(const IeksParams<typename C::Tp> p,
 // Inputs of the increment model of one iteration, in extended precision (double-float for the
 // FP32 solver): u_n = Phibar lin_n - lin_{n+1} (n < N), r_n = f(y_n)/T_1 - xbar_{1,n} (n >= 1)
 // with y_n = T_0 xbar_{0,n} (the solution components of lin_n, also stored in T for the
-// Jacobian), and delta_0 = mu0 - lin_0.  One thread per time step.
+// Jacobian), and delta_0 = mu0 - lin_0.  One thread per time step.  A block takes a tile of
+// consecutive steps and stages their trajectory rows (and the row after them) and its outputs
+// in shared memory, so that every global load and store is a contiguous run: a thread reading
+// its own row of D 8-byte values from global memory would make each warp load touch 32 rows.
+// Shared rows use odd strides, which keeps the per-thread row accesses free of bank conflicts;
+// the tile is 256 steps, or 128 where that staging would not fit 48 KB.
 template <class C>
-__global__ void __launch_bounds__(256)
+struct ResTile {
+  using T = typename C::Tp;
+  static constexpr int SV = C::D | 1, SU = C::D | 1, SR = C::DD | 1;
+  static constexpr int lin_bytes(int tile) { return (tile + 1) * SV * 8; }
+  static constexpr int u_bytes(int tile) { return tile * SU * static_cast<int>(sizeof(T)); }
+  static constexpr int r_bytes(int tile) { return tile * SR * static_cast<int>(sizeof(T)); }
+  static constexpr int bytes(int tile) { return lin_bytes(tile) + u_bytes(tile) + 2 * r_bytes(tile); }
+  static constexpr int size = bytes(256) <= 48 * 1024 ? 256 : 128;
+};
+
+__device__ __forceinline__ void bits_to(uint2 w, df32& v) {
+  v.hi = __uint_as_float(w.x);
+  v.lo = __uint_as_float(w.y);
+}
+__device__ __forceinline__ void bits_to(uint2 w, double& v) { v = __hiloint2double(w.y, w.x); }
+
+template <class C>
+__global__ void __launch_bounds__(ResTile<C>::size)
 k_residuals(const IeksParams<typename C::Tp> p,
             const typename TrajType<typename C::Tp>::type* __restrict__ lin,
             typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
             typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0) {
   using T = typename C::Tp;
   using V = typename TrajType<T>::type;
+  using RT = ResTile<C>;
+  static_assert(sizeof(V) == sizeof(uint2), "trajectory values are 8 bytes");
   constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  constexpr int TILE = RT::size, SV = RT::SV, SU = RT::SU, SR = RT::SR;
+  __shared__ __align__(16) unsigned char s_raw[RT::bytes(TILE)];
+  uint2* s_lin = reinterpret_cast<uint2*>(s_raw);
+  T* s_u = reinterpret_cast<T*>(s_raw + RT::lin_bytes(TILE));
+  T* s_r = reinterpret_cast<T*>(s_raw + RT::lin_bytes(TILE) + RT::u_bytes(TILE));
+  T* s_y = reinterpret_cast<T*>(s_raw + RT::lin_bytes(TILE) + RT::u_bytes(TILE) + RT::r_bytes(TILE));
+  const uint2* lin_w = reinterpret_cast<const uint2*>(lin);
+
   OdeConstsV<V> oc;
   ode_consts_v<V, T, DD>(p.ode, p.pd, oc);
   const V T0v = v_from_double<V>(p.T0d);
   const V T1iv = v_from_double<V>(p.T1invd);
-  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= p.N;
-       n += (int64_t)gridDim.x * blockDim.x) {
-    V x[D];
+  const int t = threadIdx.x;
+  const int64_t tiles = (p.N + TILE) / TILE;  // ceil((N + 1) / TILE)
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t n0 = tile * TILE;
+    // rows n0 .. n0 + rows - 1 (the last one is the next tile's first when it exists)
+    const int64_t left = p.N + 1 - n0;
+    const int rows = left < TILE + 1 ? static_cast<int>(left) : TILE + 1;
+    const int steps = rows < TILE ? rows : TILE;
+    const int usteps = left - 1 < steps ? static_cast<int>(left - 1) : steps;  // steps with u_n
+    for (int i = t; i < rows * D; i += TILE) s_lin[(i / D) * SV + i % D] = lin_w[n0 * D + i];
+    __syncthreads();
+    if (t < steps) {
+      V x[D];
 #pragma unroll
-    for (int r = 0; r < D; ++r) x[r] = lin[n * D + r];
-    if (n < p.N) {
+      for (int r = 0; r < D; ++r) bits_to(s_lin[t * SV + r], x[r]);
+      if (t < usteps) {
 #pragma unroll
-      for (int k = 0; k < DD; ++k) {
+        for (int k = 0; k < DD; ++k) {
 #pragma unroll
-        for (int i = 0; i < Q1; ++i) {
-          V acc = x[k * Q1 + i];
+          for (int i = 0; i < Q1; ++i) {
+            V acc = x[k * Q1 + i];
 #pragma unroll
-          for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
-          acc = acc - lin[(n + 1) * D + k * Q1 + i];
-          U[n * D + k * Q1 + i] = v_to_T<T>(acc);
+            for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+            V next;
+            bits_to(s_lin[(t + 1) * SV + k * Q1 + i], next);
+            acc = acc - next;
+            s_u[t * SU + k * Q1 + i] = v_to_T<T>(acc);
+          }
         }
       }
-    }
-    V y[DD], f[DD];
+      V y[DD], f[DD];
 #pragma unroll
-    for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
-    ode_f_v<V, DD>(oc, y, f);
+      for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
+      ode_f_v<V, DD>(oc, y, f);
 #pragma unroll
-    for (int k = 0; k < DD; ++k) {
-      Yv[n * DD + k] = v_to_T<T>(y[k]);
-      R[n * DD + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
-    }
-    if (n == 0) {
+      for (int k = 0; k < DD; ++k) {
+        s_y[t * SR + k] = v_to_T<T>(y[k]);
+        s_r[t * SR + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
+      }
+      if (n0 + t == 0) {
 #pragma unroll
-      for (int r = 0; r < D; ++r) d0[r] = v_to_T<T>(v_from_double<V>(p.mu0d[r]) - x[r]);
+        for (int r = 0; r < D; ++r) d0[r] = v_to_T<T>(v_from_double<V>(p.mu0d[r]) - x[r]);
+      }
     }
+    __syncthreads();
+    for (int i = t; i < usteps * D; i += TILE) U[n0 * D + i] = s_u[(i / D) * SU + i % D];
+    for (int i = t; i < steps * DD; i += TILE) {
+      const int o = (i / DD) * SR + i % DD;
+      R[n0 * DD + i] = s_r[o];
+      Yv[n0 * DD + i] = s_y[o];
+    }
+    __syncthreads();  // the next tile restages the shared buffers
   }
 }
 
@@ -508,7 +561,7 @@ struct SolverImpl {
   // Residuals of the increment model at trajectory `lin` (once per iteration).
   static int residuals(const IeksParams<T>& p, const Buffers& b, const V* lin, cudaStream_t s) {
     PIT_LAUNCH(KC_RESIDUALS, s, 
-               k_residuals<C><<<elem_grid(p.N + 1, 256), 256, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0););
+               k_residuals<C><<<elem_grid(p.N + 1, ResTile<C>::size), ResTile<C>::size, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
