@@ -146,6 +146,31 @@ def test_solve_edge_sizes(pit, N, L):
     assert rel(cov(r.sqrtcov.cpu().numpy()), cov(ref.sqrtcovs)) < 1e-8
 
 
+@pytest.mark.parametrize("p", [W.van_der_pol(N=255, q=2), W.van_der_pol(N=256, q=2),
+                               W.van_der_pol(N=511, q=2), W.van_der_pol(N=127, q=3),
+                               W.van_der_pol(N=128, q=3), W.van_der_pol(N=385, q=3)],
+                         ids=lambda x: f"{x.name}-{x.N}-q{x.q}")
+def test_residual_tile_boundaries(pit, p):
+    """The residual kernel works on tiles of 256 time points (128 for FP64 with D = 8): N + 1
+    exactly one or two tiles, a last tile holding only the final point, a ragged last tile.
+    The bar is ten times the oracle's own sensitivity to a 1e-15 relative perturbation of its
+    initial trajectory (at least 1e-10, at most 1e-9): the second Gauss-Newton iterate of the
+    q = 3 model on the finest of these grids moves by ~2e-11 under that perturbation."""
+    ref = ieks.ieks(p, fixed_iters=2)
+    rng = np.random.default_rng(0)
+    pert = np.tile(ref.mu0, (p.N + 1, 1)) * (1 + 1e-15 * rng.standard_normal((p.N + 1, p.D)))
+    sens = rel(ieks.ieks(p, fixed_iters=2, init_traj=pert).means, ref.means)
+    bar = min(1e-9, max(1e-10, 10 * sens))
+    r = solve(pit, p, torch.float64, fixed_iters=2)
+    assert rel(r.mean.cpu().numpy(), ref.means) < bar
+    assert rel(cov(r.sqrtcov.cpu().numpy()), cov(ref.sqrtcovs)) < 1e-8
+    if p.q == 2:
+        conv = ieks.ieks(p, max_iter=60)
+        r32 = solve(pit, p, torch.float32, fixed_iters=conv.iterations)
+        m = r32.mean.cpu().double().numpy()
+        assert rel(m[:, ysl(p)], conv.means[:, ysl(p)]) < 1e-5
+
+
 def test_logistic_config_converges_like_oracle(pit):
     """logistic r = 3, y0 = 0.01, [0, 10], q = 2, N = 1024, FP64, stop at max|dy| < 1e-10 or
     20 iterations.  From the constant initial trajectory both reach the same fixed point."""
