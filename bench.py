@@ -301,13 +301,14 @@ def run_pit(args):
         else:
             fl = roofline.residuals_flops(D, prob.d, prob.q + 1)
         achieved = fl * steps_per_launch / (avg_ms / 1e3) / 1e12
-        peak = roofline.fp32_alu_peak_tflops()
+        sms, mhz = _device_geometry(dev)
+        peak = roofline.fp32_alu_peak_tflops(sms, mhz)
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": _traffic(dom, steps_per_launch, D, args.dtype),
                 "traffic_source": "ncu dram bytes read+written per launch, scaled from N=2^19 "
                                   "by time steps (profiles/); null if the kernels changed",
-                "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "peak_source": f"nominal: {sms} SMs x 128 FP32 lanes x 2 x {mhz:g} MHz",
                 "algorithmic_flops_per_step": fl}
     else:
         by = roofline.bytes_per_step("smooth_down", D, prob.d, esz, traj_elem)
@@ -494,15 +495,15 @@ def run_lv_batch(args):
         dist.destroy_process_group()
 
 
-# DRAM traffic per time step of the chain kernels, from the ncu capture summarised in
-# profiles/k_filter_chain_kernels_fhn_q3_N524288_full.md (dram bytes read + written per launch /
-# time steps, FitzHugh-Nagumo IWP(3), FP32).  Valid only for the kernel sources it was taken on:
+# DRAM traffic per time step of the chain kernels, from one ncu --set full capture of both
+# kernels at N = 2^19 (dram bytes read + written per launch / time steps, FitzHugh-Nagumo
+# IWP(3), FP32).  Valid only for the kernel sources it was taken on:
 # KERNEL_SOURCES_HASH is the hash of those sources, and the roofline's traffic is null when the
 # current sources differ.
 NCU_TRAFFIC_PER_STEP = {"filter_down": 135.792384e6 / 524288, "filter_reduce": 25.232128e6 / 524288}
 KERNEL_SOURCES_HASH = "056fbf6970c9c4bd"
-# The same for the large-state kernels of the Lorenz-96 workload (FP64, ncu at N = 2048;
-# profiles/k_ddown_k_dreduce_lorenz96_d64_N2048_f64_full.md).
+# The same for the large-state kernels of the Lorenz-96 workload (FP64, one ncu --set full
+# capture at N = 2048).
 NCU_TRAFFIC_PER_STEP_L96 = {"filter_down": 11.983929e9 / 2048, "filter_reduce": 6.537382e9 / 2048}
 DENSE_SOURCES_HASH = "904a24ce51373fe8"
 
@@ -532,6 +533,18 @@ def _traffic(kernel: str, steps: int, D: int, dtype: str):
             or kernel_sources_hash() != KERNEL_SOURCES_HASH):
         return None
     return NCU_TRAFFIC_PER_STEP[kernel] * steps
+
+
+def _device_geometry(dev):
+    """(SM count of the device, maximum SM clock in MHz): the clock from MEASURED_PEAKS.json,
+    else GB300's 2070 MHz."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return sms, mhz
 
 
 def _measured_hbm():
@@ -864,14 +877,16 @@ def run_l96(args):
     fl = (roofline.filter_down_flops(D, d, Q1) if dom == "filter_down"
           else roofline.filter_reduce_flops(D, d, Q1))
     achieved = fl * prob.N / (dom_ms / dom_n / 1e3) / 1e12
-    peak = roofline.fp64_alu_peak_tflops() if f64 else roofline.fp32_alu_peak_tflops()
+    sms, mhz = _device_geometry(dev)
+    peak = (roofline.fp64_alu_peak_tflops(sms, mhz) if f64
+            else roofline.fp32_alu_peak_tflops(sms, mhz))
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": _traffic("l96_" + dom, prob.N, D, args.l96_dtype),
             "traffic_source": "ncu dram bytes read+written per launch (profiles/); null if the "
                               "kernels changed",
-            "peak_source": ("nominal: 152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz" if f64 else
-                            "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+            "peak_source": (f"nominal: {sms} SMs x 2 FP64 FMA/clk x 2 x {mhz:g} MHz" if f64 else
+                            f"nominal: {sms} SMs x 128 FP32 lanes x 2 x {mhz:g} MHz"),
             "algorithmic_flops_per_step": fl}
     kernel_shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                          "share": v[0] / total_ms} for k, v in shares.items()}

@@ -22,6 +22,29 @@ void set_error(const std::string& msg) { g_err = msg; }
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
+// ---- device geometry ---------------------------------------------------------------------------
+// Streaming multiprocessors of the current device, queried once per device.  Launch shapes
+// (chain lengths, grid caps) are derived from it.  Without a queryable device (a workspace-size
+// query on a host with no GPU) GB300's count is assumed; the solve itself then fails at its
+// first CUDA call.
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 152;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 // ---- opt-in launch profiler ------------------------------------------------------------------
 // When enabled, every kernel launch is bracketed by two CUDA events recorded on its stream;
 // pit_profile_read() waits for the pending events and accumulates elapsed device time per
@@ -457,7 +480,7 @@ static int launch_linearize(const Problem& pb, const void* traj, void* H, void* 
   op.d = pb.d;
   for (int i = 0; i < pb.n_params; ++i) op.p[i] = static_cast<T>(pb.params[i]);
   const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
-  const unsigned grid = static_cast<unsigned>(std::min<int64_t>((pb.N + 255) / 256, 152 * 16));
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>((pb.N + 255) / 256, int64_t(sm_count()) * 16));
   PIT_LAUNCH(KC_LINEARIZE, s, 
              k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h,
                                            static_cast<const T*>(traj), static_cast<T*>(H),

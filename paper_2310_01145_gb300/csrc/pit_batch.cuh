@@ -196,7 +196,7 @@ class SegEngineImpl final : public SegEngine {
     if (chain_len > 0) return (max_points - 1) / chain_len + 1;
     // default chain length (SolverImpl::default_chain_len) gives at most target + 1 chains, or
     // max_points / 512 + 1 when the length is clamped at 512
-    const int64_t target = 152LL * 8 * NG;
+    const int64_t target = int64_t(sm_count()) * 8 * NG;
     return std::max<int64_t>(target + 2, max_points / 512 + 2);
   }
 

@@ -1062,7 +1062,8 @@ struct DenseSolver {
 
   static int default_chain_len(int64_t N) {
     // about one chain per SM
-    const int64_t L = (N + 151) / 152;
+    const int64_t sms = sm_count();
+    const int64_t L = (N + sms - 1) / sms;
     return static_cast<int>(std::max<int64_t>(1, L));
   }
 
@@ -1275,7 +1276,7 @@ struct DenseSolver {
   }
 
   static unsigned elem_grid(int64_t count, int threads) {
-    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, 152 * 16)));
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, int64_t(sm_count()) * 16)));
   }
 
   static int run(const SolveArgs& a, size_t* wsq, bool eks) {
@@ -1671,7 +1672,7 @@ struct DenseScan {
     std::memset(&p, 0, sizeof(p));
     p.D = D;
     p.N = N;
-    p.L = static_cast<int>(std::max<int64_t>(1, (N + 151) / 152));
+    p.L = static_cast<int>(std::max<int64_t>(1, (N + sm_count() - 1) / sm_count()));
     p.P = (N + p.L - 1) / p.L;
     p.wsmax = NB + D;
     const TreeLayout tl(D);
@@ -1832,7 +1833,7 @@ int dense_linearize(const Problem& pb, const void* traj, void* H, void* dv, cuda
   a.n_params = pb.n_params;
   for (int i = 0; i < pb.n_params; ++i) a.pd[i] = pb.params[i];
   const int64_t total = pb.N * pb.d;
-  const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16)));
+  const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 16)));
   PIT_LAUNCH(KC_LINEARIZE, s, (k_dlinearize<T><<<grid, 256, 0, s>>>(a, pb.N, static_cast<const T*>(traj), static_cast<T*>(H), static_cast<T*>(dv))));
   PIT_CUDA_TRY(cudaGetLastError());
   return PIT_OK;

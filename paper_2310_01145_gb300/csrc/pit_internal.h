@@ -57,6 +57,8 @@ struct ScanArgs {
 void set_error(const std::string& msg);
 void count_launches(int64_t n);
 int64_t launches_total();
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
 
 // Kernel classes for the opt-in launch profiler (pit_profile_enable / pit_profile_read).
 enum KernelClass {

@@ -443,7 +443,7 @@ struct SolverImpl {
 
   static int default_chain_len(int64_t N) {
     // enough chains to fill every SM with several resident groups
-    const int64_t target_chains = 152LL * 8 * NG;
+    const int64_t target_chains = int64_t(sm_count()) * 8 * NG;
     int64_t L = (N + target_chains - 1) / target_chains;
     L = std::max<int64_t>(L, 4);
     L = std::min<int64_t>(L, 512);
@@ -555,7 +555,7 @@ struct SolverImpl {
   static size_t chain_smem() { return static_cast<size_t>(NG) * C::SCR * sizeof(T); }
 
   static unsigned elem_grid(int64_t count, int threads) {
-    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, 152 * 16)));
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, int64_t(sm_count()) * 16)));
   }
 
   // Residuals of the increment model at trajectory `lin` (once per iteration).
@@ -806,7 +806,8 @@ struct ScanImpl {
   using C = Cfg<T, 1, D, G, RL>;
   static constexpr int NG = kThreads / G;
   static int chain_len(int64_t N) {
-    int64_t L = (N + 152LL * 4 * NG - 1) / (152LL * 4 * NG);
+    const int64_t per = int64_t(sm_count()) * 4 * NG;
+    int64_t L = (N + per - 1) / per;
     return static_cast<int>(std::max<int64_t>(4, std::min<int64_t>(L, 256)));
   }
   static int filter(const ScanArgs& a, size_t* wsq) {

@@ -110,14 +110,13 @@ def bytes_per_step(kernel: str, D: int, d: int, elem: int, traj_elem: int,
     raise ValueError(kernel)
 
 
-def fp32_alu_peak_tflops(sm_count: int = 152, fp32_lanes_per_sm: int = 128,
-                         clock_mhz: float = 2070.0) -> float:
-    """Nominal FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock."""
+def fp32_alu_peak_tflops(sm_count: int, clock_mhz: float, fp32_lanes_per_sm: int = 128) -> float:
+    """Nominal FP32 FMA peak: SMs x FP32 lanes x 2 flops x clock (the SM count is the device's,
+    the clock its maximum)."""
     return sm_count * fp32_lanes_per_sm * 2.0 * clock_mhz * 1e6 / 1e12
 
 
-def fp64_alu_peak_tflops(sm_count: int = 152, fma_per_clk_per_sm: int = 2,
-                         clock_mhz: float = 2070.0) -> float:
-    """Nominal FP64 peak of GB300 (its FP64 rate is cut to 1.25 TFLOP/s): SMs x FP64 FMA per
-    clock x 2 flops x clock."""
+def fp64_alu_peak_tflops(sm_count: int, clock_mhz: float, fma_per_clk_per_sm: int = 2) -> float:
+    """Nominal FP64 peak of GB300 (its FP64 rate is cut to 1.25 TFLOP/s at 152 SMs): SMs x FP64
+    FMA per clock x 2 flops x clock."""
     return sm_count * fma_per_clk_per_sm * 2.0 * clock_mhz * 1e6 / 1e12
