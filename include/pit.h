@@ -270,17 +270,20 @@ int32_t pit_solve_grid(const pit_ode* ode, const double* t, int64_t N, int32_t q
                        size_t ws_bytes, void* stream);
 
 /* pit_solve for callers that cannot allocate device memory (no counterpart in the paper: this
- * is a deployment convenience).  Code running while a CUDA graph is captured, serving loops
- * with a fixed memory budget and plug-ins inside another framework's memory manager may be
- * unable to call cudaMalloc for a workspace; this entry point takes no workspace and uses a
- * fixed 64 MiB scratch array in device memory that the library defines instead (held by every
- * GPU that loads the library until the process exits).  It allocates nothing itself.
- * Arguments and outputs are those of pit_solve without workspace/ws_bytes.  The first call on a
- * device looks up the array's address on that device; make it outside any stream capture.
- * Every call shares the array (the solver initialises all scratch it reads, so the previous
- * call's contents are harmless); calls whose device work overlaps race on it and must be
- * serialised by the caller.  Errors: as pit_solve, plus PIT_ENOMEM (with a message giving both
- * sizes) when the problem needs more scratch than the array holds. */
+ * is a deployment convenience).  Serving loops whose device memory budget is fixed at start-up,
+ * plug-ins that run inside another framework's memory manager and have no device allocator of
+ * their own, and real-time hosts that forbid allocation (and the synchronisation cudaMalloc may
+ * bring) after initialisation cannot obtain a workspace for pit_solve; this entry point takes
+ * none and uses a fixed 64 MiB scratch array in device memory that the library defines instead
+ * (held by every GPU that loads the library until the process exits).  It allocates nothing
+ * itself.  Arguments and outputs are those of pit_solve without workspace/ws_bytes.  The first
+ * call on a device looks up the array's address on that device (with that device current) and
+ * keeps it for the life of the process; make that first call before any stream capture, and do
+ * not reset the device (cudaDeviceReset) after it.  Every call shares the array (the solver
+ * initialises all scratch it reads, so the previous call's contents are harmless); calls whose
+ * device work overlaps race on it and must be serialised by the caller.  Errors: as pit_solve,
+ * plus PIT_ENOMEM (with a message giving both sizes) when the problem needs more scratch than
+ * the array holds. */
 int32_t pit_solve_noalloc(const pit_ode* ode, const pit_grid* grid, int32_t q, const double* y0,
                           const pit_opts* opts, const void* init_traj, void* mean,
                           void* sqrtcov, pit_solve_info* info, void* stream);

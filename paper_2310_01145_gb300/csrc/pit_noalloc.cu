@@ -1,21 +1,21 @@
 // pit_solve_noalloc: pit_solve for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc (or have torch or another allocator do it) at the point
-// where they want a solve: code that runs while a CUDA graph is being captured (allocation
-// calls are not capturable), real-time or serving loops whose memory budget is fixed up front
-// and that must not take the allocator's implicit synchronisation, and plug-ins that run
-// inside another framework's memory manager with no device allocator of their own.  For them
-// this entry point runs the same solver with its scratch space in a fixed, file-scope device
-// array instead of a caller-provided workspace.
+// where they want a solve: serving loops whose device memory budget is fixed when they start,
+// plug-ins that run inside another framework's memory manager with no device allocator of their
+// own, and real-time hosts that forbid allocation -- and the device synchronisation cudaMalloc
+// can bring -- once initialised.  For them this entry point runs the same solver with its
+// scratch space in a fixed, file-scope device array instead of a caller-provided workspace.
 //
 // The array is kStaticScratchBytes (64 MiB) and, like any __device__ variable, every GPU that
 // loads the library holds it until the process exits.  Its device address is obtained once per
-// device (cudaGetSymbolAddress with that device current) on the first call made on that device;
-// make that first call outside any stream capture.  All calls share the one array and it keeps
-// the previous call's contents; the solver initialises every scratch region it reads (the
-// trajectory, residuals, aggregates and its scalar accumulators), so nothing has to start at
-// zero.  Calls whose device work overlaps -- on different streams, or from different host
-// threads -- race on the array: serialise them.
+// device (cudaGetSymbolAddress with that device current) on the first call made on that device
+// and kept for the life of the process: make that first call before any stream capture, and do
+// not reset the device after it (a new context could place the array elsewhere).  All calls
+// share the one array and it keeps the previous call's contents; the solver initialises every
+// scratch region it reads (the trajectory, residuals, aggregates and its scalar accumulators),
+// so nothing has to start at zero.  Calls whose device work overlaps -- on different streams,
+// or from different host threads -- race on the array: serialise them.
 #include <cuda_runtime.h>
 
 #include <mutex>

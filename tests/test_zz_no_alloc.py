@@ -1,7 +1,8 @@
 """pit_solve_noalloc: the solver for callers that cannot allocate device memory.
 
-Code inside a CUDA graph capture, serving loops with a fixed memory budget or plug-ins running
-under another framework's memory manager may be unable to call cudaMalloc for a workspace.
+Serving loops with a device memory budget fixed at start-up, plug-ins running under another
+framework's memory manager and real-time hosts that forbid allocation after initialisation may
+be unable to call cudaMalloc for a workspace.
 pit_solve_noalloc runs the same solver on a fixed scratch array that the library holds in
 device memory.  This test calls it through the C ABI twice in a row (the second call finds the
 first call's leftovers in the shared array) and checks both results against pit_solve with a
@@ -34,16 +35,22 @@ def _noalloc(pit, p, opts, mean, cov):
     return st, info
 
 
-@pytest.mark.parametrize("p,dtype,tol", [
-    (W.van_der_pol(N=1000, q=2), torch.float64, 1e-10),
-    (W.fitzhugh_nagumo(N=3000, q=3), torch.float32, 1e-5),
+@pytest.mark.parametrize("p,dtype,tol,extra", [
+    (W.van_der_pol(N=1000, q=2), torch.float64, 1e-10, {}),
+    (W.fitzhugh_nagumo(N=3000, q=3), torch.float32, 1e-5, {}),
+    # coarse-grid start: the coarse solve's workspace is carved out of the same array
+    (W.fitzhugh_nagumo(N=4000, q=3), torch.float64, 1e-10, {"init_coarse": 128}),
+    # d > 3 goes to the large-state solver, whose scratch also lives in the array
+    (W.lorenz96(d=8, N=1000, q=2), torch.float64, 1e-10, {"max_iter": 8}),
 ], ids=lambda x: getattr(x, "name", str(x)))
-def test_noalloc_matches_workspace_solve_twice(p, dtype, tol):
+def test_noalloc_matches_workspace_solve_twice(p, dtype, tol, extra):
     import paper_2310_01145_gb300 as pit
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required")
     pit.load()
-    opts = pit.make_opts(dtype=dtype, max_iter=60, atol_delta=1e-10)
+    kw = dict(max_iter=60, atol_delta=1e-10)
+    kw.update(extra)
+    opts = pit.make_opts(dtype=dtype, **kw)
     ref = pit.pit_solve(pit.ode_from_problem(p), p.y0, p.t0, p.t1, p.N, p.q, opts)
     torch.cuda.synchronize()
     ref_mean = ref.mean.double().cpu().numpy()
