@@ -1,4 +1,4 @@
-// Large-state solver, FP32 arithmetic (double-float trajectory).
+// Large-state solver, FP32 arithmetic (FP64 trajectory).
 #include "pit_dense_impl.cuh"
 
 namespace pit {

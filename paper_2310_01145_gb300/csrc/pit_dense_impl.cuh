@@ -4,7 +4,7 @@
 //
 // Same method, model and conventions as the small-state solver (pit_solve_impl.cuh): the scans
 // run in preconditioned coordinates on the Gauss-Newton increment delta = Y - lin of each
-// iteration (trajectory and residuals in double-float / double), time steps are cut into chains
+// iteration (trajectory and residuals in FP64), time steps are cut into chains
 // of L consecutive steps, each chain is walked sequentially, and the chain aggregates are
 // combined with the full square-root operators of Eqs. sqrt-associative-filtering and
 // sqrt-associative-smoothing in a work-efficient (Brent-Kung up-sweep, Blelloch down-sweep)

@@ -115,100 +115,30 @@ __device__ __forceinline__ void ode_eval(const OdeParams<T>& P, const T (&y)[DD]
 }  // namespace pit
 
 // ---------------------------------------------------------------------------------------------
-// Double-float arithmetic (a value is hi + lo, two FP32 numbers, about 48 significant bits),
-// after the error-free transformations of Knuth (TwoSum), Dekker (Fast2Sum) and the fused
-// multiply-add form of TwoProd.  Used for the linearisation trajectory and the residuals of the
-// FP32 solver, where FP32 rounding of large, slowly varying values would otherwise accumulate.
+// Trajectory arithmetic.  The linearisation trajectory and the residuals of the increment model
+// are kept in FP64 for both solvers (the FP32 solver runs only its scans in FP32).  The helpers
+// below are the conversions the kernels use between the trajectory type V and the arithmetic
+// type T of the scans.
 // ---------------------------------------------------------------------------------------------
 namespace pit {
 
-struct df32 {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-__device__ __forceinline__ df32 operator+(df32 x, df32 y) {
-  float s, e, t, f;
-  two_sum(x.hi, y.hi, s, e);
-  two_sum(x.lo, y.lo, t, f);
-  e += t;
-  fast_two_sum(s, e, s, e);
-  e += f;
-  fast_two_sum(s, e, s, e);
-  return {s, e};
-}
-__device__ __forceinline__ df32 operator-(df32 x) { return {-x.hi, -x.lo}; }
-__device__ __forceinline__ df32 operator-(df32 x, df32 y) { return x + (-y); }
-__device__ __forceinline__ df32 operator*(df32 x, df32 y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  float s;
-  fast_two_sum(p, e, s, e);
-  return {s, e};
-}
-__device__ __forceinline__ df32 operator*(df32 x, float b) {
-  const float p = x.hi * b;
-  float e = fmaf(x.hi, b, -p);
-  e = fmaf(x.lo, b, e);
-  float s;
-  fast_two_sum(p, e, s, e);
-  return {s, e};
-}
-__device__ __forceinline__ df32 operator+(df32 x, float b) {
-  float s, e;
-  two_sum(x.hi, b, s, e);
-  e += x.lo;
-  fast_two_sum(s, e, s, e);
-  return {s, e};
-}
-
-// conversions
 template <typename V>
 __device__ __forceinline__ V v_from_double(double x);
 template <>
 __device__ __forceinline__ double v_from_double<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ df32 v_from_double<df32>(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - static_cast<double>(h))};
-}
-__device__ __forceinline__ float v_to_float(df32 x) { return x.hi + x.lo; }
-__device__ __forceinline__ double v_to_double(df32 x) {
-  return static_cast<double>(x.hi) + static_cast<double>(x.lo);
-}
 __device__ __forceinline__ double v_to_double(double x) { return x; }
-__device__ __forceinline__ df32 v_add_small(df32 x, float d) { return x + d; }
 __device__ __forceinline__ double v_add_small(double x, double d) { return x + d; }
 template <typename V>
 __device__ __forceinline__ V v_from_zero() {
   return v_from_double<V>(0.0);
 }
-template <>
-__device__ __forceinline__ df32 v_from_zero<df32>() {
-  return {0.f, 0.f};
-}
 // round a trajectory value to the arithmetic type T of the scans
-template <typename T>
-__device__ __forceinline__ T v_to_T(df32 x) {
-  return static_cast<T>(x.hi + x.lo);
-}
 template <typename T>
 __device__ __forceinline__ T v_to_T(double x) {
   return static_cast<T>(x);
 }
-__device__ __forceinline__ df32 operator*(df32 x, double) = delete;
 
-// Constants of the vector field in the trajectory number type V (double or df32).
+// Constants of the vector field in the trajectory number type V.
 template <typename V>
 struct OdeConstsV {
   int kind;

@@ -83,8 +83,16 @@ def smooth_down_flops(D: int, with_cov: bool = False) -> float:
 
 
 def residuals_flops(D: int, d: int, Q1: int) -> float:
-    # double-float arithmetic, counted as the FP64-equivalent operations it represents
+    # FP64 arithmetic of the increment model's inputs
     return 2.0 * _phi_fma(D, d, Q1, 1) + D + 12 * d
+
+
+def iteration_flops(D: int, d: int, Q1: int, with_cov: bool = False) -> float:
+    """One time step of a whole IEKS iteration in the single-launch kernel: filter fold, Kalman
+    step with the smoothing element, smoothing step.  The residuals are FP64 work and the scans
+    over chain aggregates add a few combines per chain; neither is counted here."""
+    return (filter_reduce_flops(D, d, Q1) + filter_down_flops(D, d, Q1, with_cov)
+            + smooth_down_flops(D, with_cov))
 
 
 # ---- bytes (algorithmic: each array element moved once per kernel) -------------------------
