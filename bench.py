@@ -48,6 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--chain-len", type=int, default=-1,
                     help="chain length of the scans; -1 (default) takes the autotuner's table "
                          "(paper_2310_01145_gb300/tuning.json), 0 the library default")
+    ap.add_argument("--scan", type=int, default=0, choices=(0, 1),
+                    help="0: one cooperative launch per IEKS iteration (default); 1: one launch "
+                         "per scan phase with block-level scan trees")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="time steps in the oracle's bounded CPU sample")
@@ -67,6 +70,10 @@ def parse_args(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="serve: arrival window per rate")
     ap.add_argument("--instances", type=int, default=4096)
+    ap.add_argument("--batch-max-iter", type=int, default=64,
+                    help="lv_batch (and the default line's batched key): iteration cap")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the accuracy, batched and serving keys")
     ap.add_argument("--no-eks", action="store_true", help="skip the sequential-EKS comparison")
     return ap.parse_args(argv)
 
@@ -187,6 +194,44 @@ print(json.dumps({{"seconds": el, "steps": {N_sample}, "iters": {iters}}}))
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+# ---- accuracy of a result against the FP64 solve on the same grid ------------------------------
+def accuracy_vs_f64(prob, ode, mean, cov, sigma2, tdt, dev):
+    """Relative errors of a FitzHugh-Nagumo result (mean, sqrt covariances, sigma^2) against the
+    FP64 parallel solve on the same grid (coarse-grid start, stop at 1e-10): the solution
+    estimate over all points, every derivative order, the covariances S S^T on 1025 sampled
+    points and sigma^2.  The FP64 solver itself is tied to the FP64 oracle at N = 2^12 .. 2^20 by
+    the accuracy tests."""
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+
+    o = pit.make_opts(dtype=torch.float64, max_iter=60, atol_delta=1e-10, init_coarse=256)
+    r64 = pit.pit_solve(ode, prob.y0, prob.t0, prob.t1, prob.N, prob.q, o, device=dev)
+    torch.cuda.synchronize()
+    q1 = prob.q + 1
+    m = mean.double()
+
+    def rel(a, b):
+        return float((a - b).abs().max() / b.abs().max())
+
+    orders = [rel(m[:, i::q1], r64.mean[:, i::q1]) for i in range(q1)]
+    idx = torch.arange(0, prob.N + 1, max(1, prob.N // 1024), device=m.device)
+    S = cov[idx].double()
+    S64 = r64.sqrtcov[idx]
+    C = S @ S.transpose(1, 2)
+    C64 = S64 @ S64.transpose(1, 2)
+    out = {"reference": "FP64 parallel solve on the same grid (coarse-grid start, stop at "
+                        "max|dy| <= 1e-10), itself checked against the FP64 oracle at "
+                        "N = 2^12..2^20",
+           "dtype": "f32" if tdt == torch.float32 else "f64",
+           "solution_rel_err": orders[0], "per_order_rel_err": orders,
+           "cov_rel_err": rel(C, C64), "sigma2_rel_err": abs(sigma2 - r64.sigma2) / r64.sigma2,
+           "f64_iterations": r64.iterations}
+    del r64
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---- our arm ----------------------------------------------------------------------------------
 def run_pit(args):
     import numpy as np
@@ -211,7 +256,7 @@ def run_pit(args):
         from paper_2310_01145_gb300 import autotune
         variant, chain_len = autotune.lookup(prob, args.dtype)
     opts = pit.make_opts(dtype=tdt, max_iter=args.max_iter, atol_delta=args.atol,
-                         chain_len=chain_len, variant=variant)
+                         chain_len=chain_len, variant=variant, scan=args.scan)
     ode = pit.ode_from_problem(prob)
     D = prob.D
     mean = torch.empty((prob.N + 1, D), dtype=tdt, device=dev)
@@ -284,6 +329,11 @@ def run_pit(args):
     work_e2e = reduce_sum(float(work_e2e), world, dev)
     e2e_value = work_e2e / t_e2e
 
+    # ---- accuracy of the timed result against the FP64 solve on the same grid ----
+    accuracy = None
+    if rank == 0 and not args.no_extras:
+        accuracy = accuracy_vs_f64(prob, ode, mean, cov, r.sigma2, tdt, dev)
+
     # ---- roofline of the dominant kernel ----
     k_iters = statistics.mean(iters)
     shares = {k: v for k, v in prof.items() if v[1] > 0}
@@ -293,8 +343,10 @@ def run_pit(args):
     avg_ms = dom_ms / dom_n
     steps_per_launch = prob.N  # every chain kernel covers all N time steps
     traj_elem = 8
-    if dom in ("filter_down", "filter_reduce", "residuals"):
-        if dom == "filter_down":
+    if dom in ("filter_down", "filter_reduce", "residuals", "iteration"):
+        if dom == "iteration":
+            fl = roofline.iteration_flops(D, prob.d, prob.q + 1)
+        elif dom == "filter_down":
             fl = roofline.filter_down_flops(D, prob.d, prob.q + 1)
         elif dom == "filter_reduce":
             fl = roofline.filter_reduce_flops(D, prob.d, prob.q + 1)
@@ -341,6 +393,13 @@ def run_pit(args):
                "parallel_ms_per_solve": ms_local / args.steps,
                "speedup_time_to_solution": eks_ms / (ms_local / args.steps)}
 
+    # ---- batched and served FP32 solves next to single-instance FP64 (time-bounded) ----
+    batched = serving = None
+    if rank == 0 and not args.no_extras:
+        batched, _ = measure_lv_batch(4096, steps=3, warmup=2, seed=0,
+                                      max_iter=args.batch_max_iter, single=32, dev=dev)
+        serving = measure_serving([100.0, 1000.0], 2.0, 0, 32, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -364,10 +423,13 @@ def run_pit(args):
                                f"calibrated covariances",
                    "iterations_per_solve": iters, "parallelism": f"replicas x{world}",
                    "launch_shape": {"variant": variant, "chain_len": chain_len,
+                                    "scan": "single launch per iteration" if args.scan == 0
+                                    else "launch per scan phase",
                                     "source": "autotuner table" if args.chain_len < 0
                                     else "command line"},
                    "l2": "working set (E, g, trajectories: >300 MB) exceeds the 129 MB L2; "
-                         "no flush between steps"},
+                         "no flush between steps",
+                   "accuracy": accuracy},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -376,6 +438,8 @@ def run_pit(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "sequential_eks_gpu": eks,
+        "batched": batched,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -385,46 +449,45 @@ def run_pit(args):
 
 
 # ---- batched Lotka-Volterra (segmented scans over 4096 instances) ------------------------------
-def run_lv_batch(args):
+def measure_lv_batch(instances: int, steps: int, warmup: int, seed: int, max_iter: int,
+                     single: int, world: int = 1, dev=None):
+    """Batched FP32 Lotka-Volterra solves: steps*iterations/s over all instances and over the
+    instances that met the stop rule, converged and diverged fractions, end-to-end rate, and
+    the same instances (the first `single`) one at a time through the single-problem FP64
+    parallel solver.  Returns (result dict, device kernel profile)."""
     import numpy as np
     import torch
 
     import paper_2310_01145_gb300 as pit
     import workloads as W
 
-    rank, local_rank, world = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    pit.load()
-    probs = W.lotka_volterra_batch(count=args.instances, seed=rank)
+    probs = W.lotka_volterra_batch(count=instances, seed=seed)
     Ns = np.array([p.N for p in probs])
-    opts = pit.make_opts(dtype=torch.float32, max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
-                         want_cov=False, calibrate=True)
+    opts = pit.make_opts(dtype=torch.float32, max_iter=max_iter, atol_delta=1e-10,
+                         rtol_delta=1e-6, want_cov=False, calibrate=True)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        return pit.solve_problems_batched(probs, opts=opts, stream=stream,
-                                          allow_diverged=True)
+        return pit.solve_problems_batched(probs, opts=opts, stream=stream, allow_diverged=True)
 
-    for _ in range(args.warmup):
+    r = None
+    for _ in range(warmup):
         r = step()
     torch.cuda.synchronize()
     pit.pit_profile_reset()
     pit.pit_profile_enable(True)
     launches0 = pit.pit_launch_count()
-    work = 0.0
+    work = work_conv = 0.0
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             r = step()
             work += float(np.sum(Ns * r.iterations))
+            work_conv += float(np.sum((Ns * r.iterations)[r.converged]))
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
@@ -433,60 +496,91 @@ def run_lv_batch(args):
     prof = pit.pit_profile_read()
     ms = reduce_max(e0.elapsed_time(e1), world, dev)
     value = reduce_sum(work, world, dev) / (ms / 1e3)
+    value_conv = reduce_sum(work_conv, world, dev) / (ms / 1e3)
     clocks = clk.summary()
     # end to end: means copied back to pinned host memory every step
     host = torch.empty(r.mean.shape, dtype=torch.float32, pin_memory=True)
     t0 = time.perf_counter()
     work_e2e = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         r = step()
         host.copy_(r.mean, non_blocking=True)
         torch.cuda.synchronize()
         work_e2e += float(np.sum(Ns * r.iterations))
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     e2e = reduce_sum(work_e2e, world, dev) / t_e2e
-    # the same instances one at a time through the single-problem FP64 solver (first 32)
-    single = None
-    if rank == 0:
-        sub = probs[:32]
-        o64 = pit.make_opts(dtype=torch.float64, max_iter=20, atol_delta=1e-10, want_cov=False)
-        for p in sub[:2]:
-            pit.solve_problem(p, opts=o64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        w = 0
-        for p in sub:
-            rr = pit.solve_problem(p, opts=o64)
-            w += p.N * rr.iterations
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        single = {"value": w / el, "unit": UNIT, "what": "single-instance FP64 parallel solves, "
-                  "one after another, of the first 32 instances (same stop rule in FP64: "
-                  "max|dy| <= 1e-10 or 20 iterations)"}
+    # the same instances one at a time through the single-problem FP64 solver
+    sub = probs[:single]
+    o64 = pit.make_opts(dtype=torch.float64, max_iter=max_iter, atol_delta=1e-10,
+                        want_cov=False)
+    for p in sub[:2]:
+        pit.solve_problem(p, opts=o64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w = wc = 0
+    for p in sub:
+        rr = pit.solve_problem(p, opts=o64)
+        w += p.N * rr.iterations
+        wc += p.N * rr.iterations if rr.converged else 0
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    res = {
+        "value": value, "unit": UNIT, "ms_per_batched_solve": ms / steps, "batched_solves": steps,
+        "converged_only_value": value_conv,
+        "workload": f"batched Lotka-Volterra: {instances} instances, (al,be,ga,de)="
+                    f"(1.5,1,3,1)*U[0.8,1.2], y0~U[0.5,2]^2, t in [0,10], N log-uniform in "
+                    f"[256,16384] (sum N = {int(Ns.sum())}), IWP(2), FP32, one batched solve "
+                    f"per step, stop per instance at max|dy|<=1e-10+1e-6 max|y| or {max_iter} "
+                    f"iterations, means + sigma^2",
+        "iterations_mean": float(np.mean(r.iterations)),
+        "converged_fraction": float(np.mean(r.converged)),
+        "diverged_fraction": float(np.mean(r.status == 6)),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(instances * 8 * 9),
+                "d2h_bytes_per_step": int(host.numel() * 4)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "single_instance_f64": {
+            "value": w / el, "converged_only_value": wc / el, "unit": UNIT,
+            "instances": len(sub),
+            "what": f"single-instance FP64 parallel solves, one after another, of the first "
+                    f"{len(sub)} instances (same stop rule in FP64)"},
+    }
+    return res, prof
+
+
+def run_lv_batch(args):
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    res, prof = measure_lv_batch(args.instances, args.steps, args.warmup, seed=rank,
+                                 max_iter=args.batch_max_iter, single=32, world=world, dev=dev)
     shares = {k: v for k, v in prof.items() if v[1] > 0}
     total_ms = sum(v[0] for v in shares.values())
     out = {
-        "metric": "IEKS steps*iterations/s, batched Lotka-Volterra (FP32, IWP(2))", "value": value,
-        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched Lotka-Volterra: {args.instances} instances, (al,be,ga,de)"
-                               f"=(1.5,1,3,1)*U[0.8,1.2], y0~U[0.5,2]^2, t in [0,10], N "
-                               f"log-uniform in [256,16384] (sum N = {int(Ns.sum())}), IWP(2), "
-                               f"one batched solve per step, stop per instance at max|dy|<="
-                               f"1e-10+1e-6 max|y| or 20 iterations, means + sigma^2",
-                   "iterations_mean": float(np.mean(r.iterations)),
-                   "converged_fraction": float(np.mean(r.converged)),
-                   "diverged": int(np.sum(r.status == 6)),
-                   "diverged_examples": [int(i) for i in np.nonzero(r.status == 6)[0][:8]],
+        "metric": "IEKS steps*iterations/s, batched Lotka-Volterra (FP32, IWP(2))",
+        "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_batched_solve"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": res["workload"], "iterations_mean": res["iterations_mean"],
+                   "converged_fraction": res["converged_fraction"],
+                   "diverged_fraction": res["diverged_fraction"],
+                   "converged_only_value": res["converged_only_value"],
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(args.instances * 8 * 9),
-                "d2h_bytes_per_step": int(host.numel() * 4)},
-        "gpu_launches": launches,
+        "e2e": res["e2e"],
+        "gpu_launches": res["gpu_launches"],
         "kernel_shares": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
                               "share": v[0] / total_ms} for k, v in shares.items()},
-        "clocks": clocks,
-        "single_instance_f64": single,
+        "clocks": res["clocks"],
+        "single_instance_f64": res["single_instance_f64"] if rank == 0 else None,
     }
     if rank == 0:
         print(json.dumps(out))
@@ -589,24 +683,20 @@ def _percentile(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
 
 
-def run_serve(args):
+def measure_serving(rates, seconds: float, seed: int, single: int, dev=None):
+    """Poisson request streams through the continuous-batching server (FP32) at each rate:
+    solves/s, p50/p99 latency, steps*iterations/s; next to it the same requests served one at
+    a time by the single-problem FP64 parallel solver (FIFO, latencies from measured service
+    times)."""
     import numpy as np
     import torch
 
     import paper_2310_01145_gb300 as pit
     import workloads as W
 
-    rank, local_rank, world = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    pit.load()
-    rates = [float(x) for x in args.rates.split(",") if x]
-    n_max_req = int(max(rates) * args.serve_seconds) + 8
-    reqs = W.serving_requests(n_max_req, seed=1000 + rank)
-    rng = np.random.Generator(np.random.PCG64(2000 + rank))
+    n_max_req = int(max(rates) * seconds) + 8
+    reqs = W.serving_requests(n_max_req, seed=1000 + seed)
+    rng = np.random.Generator(np.random.PCG64(2000 + seed))
     unit_gaps = rng.exponential(1.0, size=n_max_req)
     sv = pit.Server(dtype="f32", max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
                     max_points=1 << 22, max_requests=2048, hbm_budget_bytes=24 << 30,
@@ -626,7 +716,7 @@ def run_serve(args):
     per_rate = []
     with ClockSampler(torch.cuda.current_device()) as clk:
         for rate in rates:
-            n = max(8, int(rate * args.serve_seconds))
+            n = max(8, int(rate * seconds))
             arr = np.cumsum(unit_gaps[:n]) / rate
             lat = {}
             iters = {}
@@ -653,9 +743,11 @@ def run_serve(args):
                              "steps_iterations_per_s": work / wall,
                              "mean_iterations": float(np.mean(list(iters.values())))})
     launches = pit.pit_launch_count() - launches0
+    clocks = clk.summary()
+    sv.close()
     # plain single-instance FP64 parallel solves, one request at a time in arrival order
     o64 = pit.make_opts(dtype=torch.float64, max_iter=20, atol_delta=1e-10, want_cov=False)
-    K = min(48, n_max_req)
+    K = min(single, n_max_req)
     for p in reqs[:3]:
         pit.solve_problem(p, opts=o64)
     torch.cuda.synchronize()
@@ -669,34 +761,56 @@ def run_serve(args):
     for rate in rates:
         arr = np.cumsum(unit_gaps[:K]) / rate
         t_free, lats = 0.0, []
-        for a, s in zip(arr, service):
+        for a, s_ in zip(arr, service):
             start = max(a, t_free)
-            t_free = start + s
+            t_free = start + s_
             lats.append(t_free - a)
         base.append({"rate": rate, "requests": K, "solves_per_s": K / t_free,
-                     "p50_ms": 1e3 * _percentile(lats, 50), "p99_ms": 1e3 * _percentile(lats, 99)})
-    top = per_rate[-1]
+                     "p50_ms": 1e3 * _percentile(lats, 50),
+                     "p99_ms": 1e3 * _percentile(lats, 99)})
+    return {
+        "workload": "Poisson request streams; family uniform over logistic, FitzHugh-Nagumo, "
+                    "Lotka-Volterra; q ~ U{1,2,3}; N log-uniform in [256, 65536]; per-request "
+                    "stop max|dy| <= 1e-10 + 1e-6 max|y| or 20 iterations; means + sigma^2 "
+                    "returned; FP32 with continuous batching",
+        "window_s": seconds, "per_rate": per_rate,
+        "plain_single_instance_f64": {"per_rate": base,
+                                      "what": f"the first {K} requests solved one at a time by "
+                                              f"the single-problem FP64 parallel solver in "
+                                              f"arrival order (FIFO queue; latency from "
+                                              f"measured service times)"},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2310_01145_gb300 as pit
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pit.load()
+    rates = [float(x) for x in args.rates.split(",") if x]
+    res = measure_serving(rates, args.serve_seconds, rank, 48, dev)
+    top = res["per_rate"][-1]
     out = {
         "metric": "served solves/s with p50/p99 latency (mixed logistic/FHN/LV requests, FP32, "
                   "continuous batching)",
         "value": top["solves_per_s"], "unit": "solves/s", "n_gpus": world,
         "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "Poisson request streams; family uniform over logistic, "
-                               "FitzHugh-Nagumo, Lotka-Volterra; q ~ U{1,2,3}; N log-uniform in "
-                               "[256, 65536]; per-request stop max|dy| <= 1e-10 + 1e-6 max|y| or "
-                               "20 iterations; means + sigma^2 returned",
-                   "window_s": args.serve_seconds, "rates": rates},
-        "per_rate": per_rate,
-        "plain_single_instance_f64": {"per_rate": base,
-                                      "what": "the first 48 requests solved one at a time by the "
-                                              "single-problem FP64 parallel solver in arrival "
-                                              "order (FIFO queue; latency from measured service "
-                                              "times)"},
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "config": {"workload": res["workload"], "window_s": args.serve_seconds,
+                   "rates": rates},
+        "per_rate": res["per_rate"],
+        "plain_single_instance_f64": res["plain_single_instance_f64"],
+        "gpu_launches": res["gpu_launches"],
+        "clocks": res["clocks"],
     }
-    sv.close()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -114,7 +114,11 @@ typedef struct {
                                  uniform grid of this many steps (<= N) over the same interval,
                                  the prior mean Phi(t - t_k) m_k between coarse nodes (Sec.
                                  3.2.2, remark on the initial trajectory); 0: constant mu0     */
-  int32_t pad_;
+  int32_t scan;         /* [0]   0: each IEKS iteration of a single-problem solve is one
+                                 cooperative launch (residuals, chain folds, decoupled
+                                 cross-block scans, down-sweeps) when the layout is variant 0,
+                                 d <= 3 and the chains fit one resident wave, else as 1;
+                                 1: one launch per scan phase with block-level scan trees     */
 } pit_opts;
 
 /* Linearisation of the vector field (pit_opts.linearization). */
@@ -268,6 +272,14 @@ int32_t pit_solve_grid(const pit_ode* ode, const double* t, int64_t N, int32_t q
                        const double* y0, const pit_opts* opts, const void* init_traj,
                        void* mean, void* sqrtcov, pit_solve_info* info, void* workspace,
                        size_t ws_bytes, void* stream);
+
+/* Check of the bounded wait that the single-launch iterations (pit_opts.scan = 0) use between
+ * thread blocks (no counterpart in the paper).  Launches one thread group that polls the flag
+ * words[0] (device memory, 3 x uint32, 4-byte aligned: flag, status, result) until it is >=
+ * target, at most poll_limit times.  Returns PIT_OK when the flag was seen, PIT_ETIMEOUT when
+ * the wait gave up and set its timeout bit (a flag that nothing sets), PIT_EINVAL for bad
+ * arguments.  words[1..2] are overwritten.  Synchronises `stream`. */
+int32_t pit_check_wait(int64_t poll_limit, uint32_t target, void* words, void* stream);
 
 /* pit_solve for callers that cannot allocate device memory (no counterpart in the paper: this
  * is a deployment convenience).  Serving loops whose device memory budget is fixed at start-up,

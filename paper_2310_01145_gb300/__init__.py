@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("linearization", ctypes.c_int32),
                 ("objective", ctypes.c_int32), ("atol_objective", ctypes.c_double),
                 ("rtol_objective", ctypes.c_double), ("init_coarse", ctypes.c_int32),
-                ("pad_", ctypes.c_int32)]
+                ("scan", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -59,7 +59,7 @@ class _Info(ctypes.Structure):
 LINEARIZATIONS = {"ek1": 0, "diag": 1, "diagonal_ek1": 1, "ek0": 2}
 _OPT_KEYS = ("dtype", "max_iter", "fixed_iters", "atol_delta", "rtol_delta", "calibrate",
              "want_cov", "chain_len", "variant", "linearization", "objective", "atol_objective",
-             "rtol_objective", "init_coarse")
+             "rtol_objective", "init_coarse", "scan")
 
 
 class _BatchInfo(ctypes.Structure):
@@ -116,6 +116,7 @@ SIGNATURES = {
                               _P, _P, _P, ctypes.POINTER(_Info), _P, _SZ, _P]),
     "pit_solve_noalloc": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                                  ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P]),
+    "pit_check_wait": (_I32, [_I64, ctypes.c_uint32, _P, _P]),
     "pit_eks_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
                                       ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
     "pit_eks_sequential": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
@@ -215,7 +216,7 @@ def pit_opts_default() -> _Opts:
 def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
               calibrate=True, want_cov=True, chain_len=0, variant=0, linearization="ek1",
               objective=False, atol_objective=0.0, rtol_objective=0.0,
-              init_coarse=0) -> _Opts:
+              init_coarse=0, scan=0) -> _Opts:
     o = pit_opts_default()
     o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
     o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
@@ -227,6 +228,7 @@ def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_
     o.objective = int(bool(objective))
     o.atol_objective, o.rtol_objective = float(atol_objective), float(rtol_objective)
     o.init_coarse = int(init_coarse)
+    o.scan = int(scan)
     return o
 
 
@@ -384,6 +386,13 @@ def pit_solve(ode: Ode, y0, t0: float, t1: float, N: int, q: int, opts: Optional
     return _solve_like(lib.pit_solve_workspace_size, lib.pit_solve, ode, y0, t0, t1, N, q,
                        opts or make_opts(), init_traj, device, stream, workspace, out,
                        allow_noconv)
+
+
+def pit_check_wait(poll_limit: int, target: int, words, stream=None) -> int:
+    """Run the bounded cross-block wait once on words[0] (a torch int32 tensor of >= 3 entries
+    on the device); returns the status (PIT_OK: flag seen, PIT_ETIMEOUT: gave up)."""
+    return int(load().pit_check_wait(int(poll_limit), int(target), _tptr(words),
+                                     _stream_ptr(stream)))
 
 
 def pit_eks_sequential(ode: Ode, y0, t0: float, t1: float, N: int, q: int,

@@ -53,7 +53,7 @@ static const char* kClassNames[KC_COUNT] = {
     "init_traj",       "residuals",        "filter_reduce",    "filter_down",
     "smooth_down",     "tree_filter_up",   "tree_filter_down", "tree_smooth_up",
     "tree_smooth_down", "export_mean",     "scan_filter",      "scan_smooth",
-    "linearize",       "eks_filter",       "eks_smooth"};
+    "linearize",       "eks_filter",       "eks_smooth",       "iteration"};
 struct Profiler {
   std::atomic<bool> on{false};
   std::mutex mu;
@@ -440,7 +440,7 @@ int check_opts(const pit_opts* in, pit_opts& o) {
   if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||
       (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20) ||
       o.variant < 0 || o.variant > 9 || o.linearization < 0 || o.linearization > 2 ||
-      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0) || o.init_coarse < 0) {
+      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0) || o.init_coarse < 0 || o.scan < 0 || o.scan > 1) {
     set_error("invalid pit_opts");
     return PIT_EINVAL;
   }
@@ -563,7 +563,7 @@ void pit_opts_default(pit_opts* o) {
   o->atol_objective = 0.0;
   o->rtol_objective = 0.0;
   o->init_coarse = 0;
-  o->pad_ = 0;
+  o->scan = 0;
 }
 
 int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,

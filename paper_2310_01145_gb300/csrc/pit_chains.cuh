@@ -23,7 +23,7 @@ __device__ __forceinline__ int64_t chain_index(int grp_in_block) {
 
 // ---------------------------------------------------------------------------------------------
 // Per-step model inputs.  The IEKS solves for the Gauss-Newton increment delta = Y - lin of
-// iteration k (lin = the linearisation trajectory, kept in double or double-float):
+// iteration k (lin = the linearisation trajectory, kept in FP64):
 //   delta_0 = mu0 - lin_0,   delta_n = Phibar delta_{n-1} + u_{n-1} + w,   u_{n-1} = Phibar lin_{n-1} - lin_n,
 //   Htilde_n delta_n = r_n,  r_n = (f(E0 lin_n) - E1 lin_n) / T_1      (scaled preconditioned form)
 // which is the linearised model of Section 3.2.1 shifted by lin (its posterior mean is
@@ -118,21 +118,14 @@ constexpr int kJBatch = PIT_JBATCH;  // leaves whose information rows are folded
 // lower-triangular.
 // ---------------------------------------------------------------------------------------------
 template <class C, bool SEG = false>
-__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
-k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
-                const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
-                const typename C::Tp* __restrict__ d0, typename C::Tp* __restrict__ agg) {
+__device__ __forceinline__ void filter_reduce_chain(
+    const typename C::GR& g, const IeksParams<typename C::Tp>& p,
+    const typename C::Tp* __restrict__ U, const typename C::Tp* __restrict__ R,
+    const typename C::Tp* __restrict__ Yv, const typename C::Tp* __restrict__ d0, int64_t chain,
+    typename C::Tp* scr, typename C::Tp* out) {
   using T = typename C::Tp;
   using GR = typename C::GR;
   constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  GR g;
-  g.init();
-  const int grp = threadIdx.x / C::G;
-  const int64_t chain = chain_index<C>(grp);
-  if (chain >= p.P) return;
-  T* scr = smem + grp * C::SCR;
   LaneConst<C> lc;
   lc.init(g, p);
 
@@ -288,7 +281,6 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
 #pragma unroll
     for (int c = 0; c < D; ++c) Cfull[0][l][c] = (c < W) ? sC[l][c] : T(0);
   lq_dense<GR, 1, D, 0, D, 0>(g, Cfull, scr + C::PIV);
-  T* out = agg + chain * C::FA;
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     if (!g.valid(l)) continue;
@@ -302,6 +294,23 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
     out[C::F_B + r] = b[l];
     out[C::F_ETA + r] = eta[l];
   }
+  g.sync();
+}
+
+template <class C, bool SEG = false>
+__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
+k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
+                const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
+                const typename C::Tp* __restrict__ d0, typename C::Tp* __restrict__ agg) {
+  using T = typename C::Tp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  filter_reduce_chain<C, SEG>(g, p, U, R, Yv, d0, chain, smem + grp * C::SCR, agg + chain * C::FA);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -314,31 +323,22 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
 // LOCAL_LIN: the sequential EKS; linearise at the predicted mean (plain model, no increment).
 // ---------------------------------------------------------------------------------------------
 template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false>
-__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
-k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
-              const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
-              const typename C::Tp* __restrict__ d0,
-              const typename C::Tp* __restrict__ fprefix, typename C::Tp* __restrict__ Es,
-              typename C::Tp* __restrict__ gs, typename C::Tp* __restrict__ Ls,
-              typename C::Tp* __restrict__ sagg, SolveScalars* __restrict__ scal) {
+__device__ __forceinline__ void filter_down_chain(
+    const typename C::GR& g, const IeksParams<typename C::Tp>& p,
+    const typename C::Tp* __restrict__ U, const typename C::Tp* __restrict__ R,
+    const typename C::Tp* __restrict__ Yv, const typename C::Tp* __restrict__ d0,
+    const typename C::Tp* pre, typename C::Tp* __restrict__ Es, typename C::Tp* __restrict__ gs,
+    typename C::Tp* __restrict__ Ls, typename C::Tp* sout, SolveScalars* __restrict__ scal,
+    int64_t chain, typename C::Tp* scr) {
   using T = typename C::Tp;
   using GR = typename C::GR;
   constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  GR g;
-  g.init();
-  const int grp = threadIdx.x / C::G;
-  const int64_t chain = chain_index<C>(grp);
-  if (chain >= p.P) return;
-  T* scr = smem + grp * C::SCR;
   LaneConst<C> lc;
   lc.init(g, p);
 
   // filter state (m, sqrtP) with sqrtP kept D wide (zero-padded)
   T m[RL], sP[RL][D];
   {
-    const T* pre = fprefix + chain * C::FA;
     const T* d0c = first_d0<C, SEG>(p, d0);
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
@@ -585,7 +585,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   // the chain owning n = N emits b_N
   if (chain == p.N / p.L) emit_end(p.N);
   // write the chain's smoothing aggregate
-  T* out = sagg + chain * C::SA;
+  T* out = sout;
 #pragma unroll
   for (int l = 0; l < RL; ++l) {
     if (!g.valid(l)) continue;
@@ -598,6 +598,28 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
     out[C::S_G + r] = xa[l];
   }
   flush_s2();
+  g.sync();
+}
+
+template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false>
+__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
+k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
+              const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
+              const typename C::Tp* __restrict__ d0,
+              const typename C::Tp* __restrict__ fprefix, typename C::Tp* __restrict__ Es,
+              typename C::Tp* __restrict__ gs, typename C::Tp* __restrict__ Ls,
+              typename C::Tp* __restrict__ sagg, SolveScalars* __restrict__ scal) {
+  using T = typename C::Tp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  filter_down_chain<C, WITH_L, LOCAL_LIN, SEG>(g, p, U, R, Yv, d0, fprefix + chain * C::FA, Es,
+                                               gs, Ls, sagg + chain * C::SA, scal, chain,
+                                               smem + grp * C::SCR);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -609,26 +631,18 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 // trajectory (the sequential EKS).
 // ---------------------------------------------------------------------------------------------
 template <class C, bool WITH_L, bool SEG = false>
-__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
-k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
-              const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
-              const typename C::Tp* __restrict__ sprefix,
-              const typename TrajType<typename C::Tp>::type* __restrict__ lin,
-              typename TrajType<typename C::Tp>::type* __restrict__ lin_new,
-              typename C::Tp* __restrict__ mean_out, typename C::Tp* __restrict__ cov_out,
-              SolveScalars* __restrict__ scal) {
+__device__ __forceinline__ void smooth_down_chain(
+    const typename C::GR& g, const IeksParams<typename C::Tp>& p,
+    const typename C::Tp* __restrict__ Es, const typename C::Tp* __restrict__ gs,
+    const typename C::Tp* __restrict__ Ls, const typename C::Tp* pre,
+    const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+    typename TrajType<typename C::Tp>::type* __restrict__ lin_new,
+    typename C::Tp* __restrict__ mean_out, typename C::Tp* __restrict__ cov_out,
+    SolveScalars* __restrict__ scal, int64_t chain, typename C::Tp* scr) {
   using T = typename C::Tp;
   using V = typename TrajType<T>::type;
   using GR = typename C::GR;
   constexpr int D = C::D, RL = C::RL, LDM = C::LDM;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* smem = reinterpret_cast<T*>(smem_raw);
-  GR g;
-  g.init();
-  const int grp = threadIdx.x / C::G;
-  const int64_t chain = chain_index<C>(grp);
-  if (chain >= p.P) return;
-  T* scr = smem + grp * C::SCR;
   int rr[RL];
   bool vv[RL];
   T Trow[RL];
@@ -641,7 +655,6 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   const bool last = (chain == p.N / p.L);
   T m[RL], sPs[RL][D];
   {
-    const T* pre = sprefix + chain * C::SA;
 #pragma unroll
     for (int l = 0; l < RL; ++l) {
       m[l] = (!last && vv[l]) ? pre[C::S_G + rr[l]] : T(0);
@@ -654,7 +667,7 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   bool bad = false;
   // quasi-MLE diffusion of this (final) pass: sigma^2 = sum / (N d)
   T sigma = static_cast<T>(
-      (!SEG && WITH_L && p.calibrate) ? sqrt(scal->sigma2_sum / (static_cast<double>(p.N) * C::DD))
+      (!SEG && WITH_L && p.calibrate) ? sqrt(__ldcg(&scal->sigma2_sum) / (static_cast<double>(p.N) * C::DD))
                                       : 1.0);
   T T0 = p.T0;
   // segmented: the instance being written (outputs, scalings, reductions) ...
@@ -828,6 +841,28 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   }
   // groups past the last chain have returned; every lane of a live group reaches here
   if (!SEG || sid >= 0) flush();
+  g.sync();
+}
+
+template <class C, bool WITH_L, bool SEG = false>
+__global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
+k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
+              const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
+              const typename C::Tp* __restrict__ sprefix,
+              const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+              typename TrajType<typename C::Tp>::type* __restrict__ lin_new,
+              typename C::Tp* __restrict__ mean_out, typename C::Tp* __restrict__ cov_out,
+              SolveScalars* __restrict__ scal) {
+  using T = typename C::Tp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  const int64_t chain = chain_index<C>(grp);
+  if (chain >= p.P) return;
+  smooth_down_chain<C, WITH_L, SEG>(g, p, Es, gs, Ls, sprefix + chain * C::SA, lin, lin_new,
+                                    mean_out, cov_out, scal, chain, smem + grp * C::SCR);
 }
 // ---------------------------------------------------------------------------------------------
 // Tree scans over items (filter: FA elements, smoothing: SA elements) in blocks of B items.

@@ -65,7 +65,7 @@ enum KernelClass {
   KC_INIT = 0, KC_RESIDUALS, KC_FILTER_REDUCE, KC_FILTER_DOWN, KC_SMOOTH_DOWN,
   KC_TREE_FILTER_UP, KC_TREE_FILTER_DOWN, KC_TREE_SMOOTH_UP, KC_TREE_SMOOTH_DOWN,
   KC_EXPORT, KC_SCAN_FILTER, KC_SCAN_SMOOTH, KC_LINEARIZE, KC_EKS_FILTER, KC_EKS_SMOOTH,
-  KC_COUNT
+  KC_ITERATION, KC_COUNT
 };
 // Brackets one kernel launch: counts it and, when profiling is on, records CUDA events on the
 // launch stream around it.

@@ -3,12 +3,14 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
 #include "pit_chains.cuh"
+#include "pit_fused.cuh"
 #include "pit_internal.h"
 
 namespace pit {
@@ -30,8 +32,7 @@ __global__ void k_init_traj(const IeksParams<typename C::Tp> p,
   }
 }
 
-// Inputs of the increment model of one iteration, in extended precision (double-float for the
-// FP32 solver): u_n = Phibar lin_n - lin_{n+1} (n < N), r_n = f(y_n)/T_1 - xbar_{1,n} (n >= 1)
+// Inputs of the increment model of one iteration, in FP64: u_n = Phibar lin_n - lin_{n+1} (n < N), r_n = f(y_n)/T_1 - xbar_{1,n} (n >= 1)
 // with y_n = T_0 xbar_{0,n} (the solution components of lin_n, also stored in T for the
 // Jacobian), and delta_0 = mu0 - lin_0.  One thread per time step.  A block takes a tile of
 // consecutive steps and stages their trajectory rows (and the row after them) and its outputs
@@ -50,11 +51,6 @@ struct ResTile {
   static constexpr int size = bytes(256) <= 48 * 1024 ? 256 : 128;
 };
 
-__device__ __forceinline__ void bits_to(uint2 w, df32& v) {
-  v.hi = __uint_as_float(w.x);
-  v.lo = __uint_as_float(w.y);
-}
-__device__ __forceinline__ void bits_to(uint2 w, double& v) { v = __hiloint2double(w.y, w.x); }
 
 template <class C>
 __global__ void __launch_bounds__(ResTile<C>::size)
@@ -450,7 +446,41 @@ struct SolverImpl {
     return static_cast<int>(L);
   }
 
-  static int fill_params(const SolveArgs& a, IeksParams<T>& p, int want_cov) {
+  // Single-launch iterations (k_iteration) exist for the one-row-per-lane layout only.
+  static constexpr bool kFusable = (G == GT) && (RL == RLT);
+  static constexpr long long kSpinLimit = 1LL << 23;  // polls (~1-2 s) per cross-block wait
+
+  // Chains that one cooperative launch of k_iteration can hold (all blocks resident), or 0
+  // when it cannot run here (shared memory, no device).
+  static int64_t fused_capacity() {
+    if constexpr (!kFusable) {
+      return 0;
+    } else {
+      static std::atomic<int64_t> cached{0};
+      const int64_t c = cached.load(std::memory_order_relaxed);
+      if (c > 0) return c;
+      using FS = FusedShape<C>;
+      const int smem = static_cast<int>(FS::smem);
+      int n0 = 0, n1 = 0;
+      if (cudaFuncSetAttribute(k_iteration<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem) != cudaSuccess ||
+          cudaFuncSetAttribute(k_iteration<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_iteration<C, false>, FS::NT,
+                                                        smem) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_iteration<C, true>, FS::NT,
+                                                        smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      const int64_t cap = static_cast<int64_t>(std::min(n0, n1)) * sm_count() * FS::NGB;
+      cached.store(cap, std::memory_order_relaxed);
+      return cap;
+    }
+  }
+
+  static int fill_params(const SolveArgs& a, IeksParams<T>& p, int want_cov,
+                         bool allow_fused = false) {
     const Problem& pb = a.pb;
     std::memset(&p, 0, sizeof(p));
     p.ode.kind = pb.kind;
@@ -462,8 +492,17 @@ struct SolverImpl {
     p.N = pb.N;
     p.lin_mode = a.opts.linearization;
     p.want_sigma = 1;
-    p.L = a.opts.chain_len > 0 ? a.opts.chain_len : default_chain_len(pb.N);
+    const int64_t cap = (allow_fused && a.opts.scan == 0) ? fused_capacity() : 0;
+    if (a.opts.chain_len > 0) {
+      p.L = a.opts.chain_len;
+    } else if (cap > 0) {
+      // the shortest chains whose count fits one resident wave of the fused kernel
+      p.L = static_cast<int>(std::max<int64_t>(4, (pb.N + 1 + cap - 1) / cap));
+    } else {
+      p.L = default_chain_len(pb.N);
+    }
     p.P = pb.N / p.L + 1;
+    p.fused = (cap > 0 && p.P <= cap) ? 1 : 0;
     p.want_cov = want_cov;
     p.calibrate = a.opts.calibrate;
     const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
@@ -494,11 +533,24 @@ struct SolverImpl {
     return PIT_OK;
   }
 
+  // Scalars of a solve: the per-pass reductions (cleared before every pass) followed by the
+  // status word of the single-launch iterations (cleared once per solve), read back together.
+  struct ScalBlock {
+    SolveScalars s;
+    unsigned status;
+    unsigned pad[3];
+  };
+
   struct Buffers {
     V *linA, *linB;
     T *U, *R, *Yv, *d0;
     T *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
     SolveScalars* scal;
+    ScalBlock* sblock;
+    // single-launch iterations: cross-block scan values and flags
+    T *xf, *xs;
+    unsigned* xflags;  // 2 x NB
+    int xNB, xK;
     T* coarse_mean;       // coarse-grid initialisation: EKS means and its workspace
     char* coarse_ws;
     size_t coarse_ws_bytes;
@@ -538,7 +590,20 @@ struct SolverImpl {
     const size_t sup_bytes = std::max(Tree<CT, false, false, true>::upper_bytes(p.P),
                                       Tree<CT, false, true, true>::upper_bytes(p.P));
     b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
-    b.scal = cv.take<SolveScalars>(1);
+    b.sblock = cv.take<ScalBlock>(1);
+    b.scal = b.sblock ? &b.sblock->s : nullptr;
+    b.xNB = 0;
+    b.xK = 0;
+    b.xf = b.xs = nullptr;
+    b.xflags = nullptr;
+    if (p.fused) {
+      b.xNB = static_cast<int>((p.P + FusedShape<C>::NGB - 1) / FusedShape<C>::NGB);
+      while ((1 << b.xK) < b.xNB) ++b.xK;
+      const size_t lv = static_cast<size_t>(b.xK + 1) * b.xNB;
+      b.xf = cv.take<T>(lv * C::FA);
+      b.xs = cv.take<T>(lv * C::SA);
+      b.xflags = cv.take<unsigned>(2 * static_cast<size_t>(b.xNB) + 1);  // + calibration barrier
+    }
     b.coarse_mean = nullptr;
     b.coarse_ws = nullptr;
     b.coarse_ws_bytes = 0;
@@ -594,6 +659,57 @@ struct SolverImpl {
     return PIT_OK;
   }
 
+  // One IEKS iteration (or the covariance pass) as a single cooperative launch of k_iteration:
+  // residuals at `lin`, both scans and both down-sweeps.  `epoch` must differ for every launch
+  // since the exchange flags were cleared.
+  template <bool WITH_L>
+  static int fused_pass(const IeksParams<T>& p_in, const Buffers& b, const V* lin, V* lin_out,
+                        T* mean_out, T* cov_out, unsigned epoch, unsigned cov_launch,
+                        cudaStream_t s) {
+    if constexpr (!kFusable) {
+      set_error("single-launch iterations are not compiled for this layout");
+      return PIT_EINTERNAL;
+    } else {
+      using FS = FusedShape<C>;
+      IeksParams<T> p = p_in;
+      p.want_sigma = (WITH_L || !p.want_cov) ? 1 : 0;
+      PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
+      FusedXchg<T> x;
+      x.fbuf = b.xf;
+      x.sbuf = b.xs;
+      x.fflag = b.xflags;
+      x.sflag = b.xflags + b.xNB;
+      x.status = &b.sblock->status;
+      x.barrier = b.xflags + 2 * b.xNB;
+      x.bar_target = cov_launch * static_cast<unsigned>(b.xNB);
+      x.epoch = epoch;
+      x.K = b.xK;
+      x.NB = b.xNB;
+      x.spin_limit = kSpinLimit;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(static_cast<unsigned>(b.xNB));
+      cfg.blockDim = dim3(FS::NT);
+      cfg.dynamicSmemBytes = FS::smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaError_t e = cudaSuccess;
+      PIT_LAUNCH(KC_ITERATION, s,
+                 e = cudaLaunchKernelEx(&cfg, k_iteration<C, WITH_L>, p, lin, lin_out, b.U, b.R,
+                                        b.Yv, b.d0, b.Es, b.gs, b.Ls, mean_out, cov_out, b.scal,
+                                        x));
+      if (e != cudaSuccess) {
+        set_error(std::string("cooperative launch of the iteration kernel: ") +
+                  cudaGetErrorString(e));
+        return PIT_ECUDA;
+      }
+      return PIT_OK;
+    }
+  }
+
   static int set_smem_attrs() {
     const int sm = static_cast<int>(chain_smem());
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_reduce<C>,
@@ -632,7 +748,7 @@ struct SolverImpl {
   static int run(const SolveArgs& a, size_t* wsq, bool eks) {
     const bool want_cov = a.opts.want_cov != 0;
     IeksParams<T> p;
-    int st = fill_params(a, p, want_cov ? 1 : 0);
+    int st = fill_params(a, p, want_cov ? 1 : 0, !eks);
     if (st != PIT_OK) return st;
     Buffers b;
     const size_t need = carve(a, p, want_cov, b);
@@ -659,8 +775,14 @@ struct SolverImpl {
     pit_solve_info info;
     std::memset(&info, 0, sizeof(info));
     const int64_t launches0 = launches_total();
-    SolveScalars hs;
-    std::memset(&hs, 0, sizeof(hs));
+    ScalBlock hb;
+    std::memset(&hb, 0, sizeof(hb));
+    SolveScalars& hs = hb.s;
+    unsigned epoch = 0;  // single-launch iterations: launches since the flags were cleared
+    if (p.fused) {
+      PIT_CUDA_TRY(cudaMemsetAsync(b.xflags, 0, (2 * b.xNB + 1) * sizeof(unsigned), s));
+      PIT_CUDA_TRY(cudaMemsetAsync(&b.sblock->status, 0, sizeof(unsigned), s));
+    }
 
     if (eks) {
       // sequential EKS: one chain, local linearisation at the predicted mean, plain model
@@ -740,16 +862,25 @@ struct SolverImpl {
     bool converged = fixed > 0;
     int k = 0;
     while (k < limit) {
-      st = residuals(p, b, cur, s);
-      if (st != PIT_OK) return st;
-      st = pass<false>(p, b, cur, nxt, nullptr, nullptr, s);
+      if (p.fused) {
+        st = fused_pass<false>(p, b, cur, nxt, nullptr, nullptr, ++epoch, 0, s);
+      } else {
+        st = residuals(p, b, cur, s);
+        if (st != PIT_OK) return st;
+        st = pass<false>(p, b, cur, nxt, nullptr, nullptr, s);
+      }
       if (st != PIT_OK) return st;
       if (want_obj) PIT_LAUNCH(KC_EXPORT, s, k_objective<C><<<og, 256, 0, s>>>(p, nxt, b.scal););
       ++k;
       bool stop = (k == limit);
       if (fixed <= 0 || want_obj) {
-        PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        PIT_CUDA_TRY(cudaMemcpyAsync(&hb, b.sblock, sizeof(hb), cudaMemcpyDeviceToHost, s));
         PIT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hb.status & kStatusTimeout) {
+          set_error("a cross-block wait of the iteration kernel ran out at iteration " +
+                    std::to_string(k + 1));
+          return PIT_ETIMEOUT;
+        }
         if (hs.flags & 1u) {
           set_error("non-finite value in the smoothing means at iteration " + std::to_string(k));
           return PIT_ENONFINITE;
@@ -780,16 +911,22 @@ struct SolverImpl {
     // the same linearisation trajectory (cur, whose residuals are still in U, R, Yv); that pass
     // reproduces the same means.
     if (want_cov) {
-      st = pass<true>(p, b, cur, nullptr, mean, cov, s);
+      st = p.fused ? fused_pass<true>(p, b, cur, nullptr, mean, cov, ++epoch, 1, s)
+                   : pass<true>(p, b, cur, nullptr, mean, cov, s);
       if (st != PIT_OK) return st;
     } else {
       PIT_LAUNCH(KC_EXPORT, s, 
                  k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean););
     }
     PIT_CUDA_TRY(cudaGetLastError());
-    SolveScalars hs2;
-    PIT_CUDA_TRY(cudaMemcpyAsync(&hs2, b.scal, sizeof(hs2), cudaMemcpyDeviceToHost, s));
+    ScalBlock hb2;
+    PIT_CUDA_TRY(cudaMemcpyAsync(&hb2, b.sblock, sizeof(hb2), cudaMemcpyDeviceToHost, s));
     PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    const SolveScalars& hs2 = hb2.s;
+    if (p.fused && (hb2.status & kStatusTimeout)) {
+      set_error("a cross-block wait of the iteration kernel ran out");
+      return PIT_ETIMEOUT;
+    }
     if (fixed > 0 && !want_cov) info.last_delta = hs2.delta_max;
     info.iterations = k;
     info.converged = converged ? 1 : 0;

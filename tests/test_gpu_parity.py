@@ -30,6 +30,7 @@ def pit():
 
 
 DEV = "cuda"
+U32 = 2.0 ** -24   # unit roundoff of FP32
 
 
 def rel(a, b):
@@ -68,11 +69,17 @@ def _elements(p):
 @pytest.mark.parametrize("p,dtype,tm,tc", [
     (W.logistic(N=37, q=2), torch.float64, 1e-12, 1e-12),
     (W.logistic_paper(N=2500, q=2), torch.float64, 1e-10, 1e-10),
-    (W.fitzhugh_nagumo(N=301, q=3), torch.float64, 1e-9, 1e-10),
+    (W.fitzhugh_nagumo(N=301, q=3), torch.float64, 1e-10, 1e-10),
     (W.van_der_pol(N=777, q=2), torch.float64, 1e-10, 1e-10),
-    (W.van_der_pol(N=777, q=1), torch.float32, 2e-4, 1e-4),
+    (W.van_der_pol(N=777, q=1), torch.float32, 2 * 777 * U32, 2 * 777 * U32),
+    (W.van_der_pol(N=3000, q=2), torch.float32, 2 * 3000 * U32, 2 * 3000 * U32),
 ], ids=lambda x: getattr(x, "name", str(x)))
 def test_filter_and_smooth_scans(pit, p, dtype, tm, tc):
+    """The element scans on caller-built elements in original coordinates.  FP64: 1e-10.  FP32:
+    2 N u32 (u32 = 2^-24): these entry points have no preconditioning and no increment
+    formulation, each of the ~2N combines rounds at u32, and the error grows linearly in N
+    (measured on GB300 for Van der Pol IWP(1)/IWP(2): 6e-6 / 3e-5 at N = 1000, 3e-5 / 3e-4 at
+    N = 10^4)."""
     el, mf, sPf, be, ms, sPs = _elements(p)
     T = lambda k: torch.tensor(np.stack([e[k] for e in el[1:]]), dtype=dtype, device=DEV)
     A, b, C, eta, J = (T(k) for k in range(5))
