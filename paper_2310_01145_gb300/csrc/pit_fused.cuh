@@ -44,6 +44,13 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kWaitNs = 4000000000ull;  // a wait gives up after 4 s
 
 // A trajectory value (FP64) from its 8-byte bit pattern.
 __device__ __forceinline__ void bits_to(uint2 w, double& v) { v = __hiloint2double(w.y, w.x); }
@@ -56,6 +63,7 @@ struct FusedXchg {
   unsigned* fflag;     // per position: epoch * 64 + (highest level posted + 1)
   unsigned* sflag;
   unsigned* status;    // timeout bit (cleared once per solve)
+  unsigned* where;     // first wait that ran out: wait_tag() code (cleared once per solve)
   unsigned* barrier;   // arrivals at the calibration barrier (cleared once per solve)
   unsigned bar_target; // arrivals to wait for in this launch (NB x covariance launches so far)
   unsigned epoch;      // >= 1, distinct for every launch since the flags were cleared
@@ -64,19 +72,29 @@ struct FusedXchg {
   long long spin_limit;  // polls per wait before giving up
 };
 
+// Identifies a wait for the error report: the phase (0 filter scan, 1 smoothing scan,
+// 2 calibration barrier), the scan position of the waiting block and the level it waited for.
+__device__ __forceinline__ unsigned wait_tag(unsigned phase, unsigned pos, unsigned level) {
+  return 0x80000000u | (phase << 28) | ((level & 0xffu) << 16) | (pos & 0xffffu);
+}
+
 // Every lane of the group polls `flag` until it reaches `target` (all lanes agree on the
-// result).  False when the poll limit ran out or another wait already did.
+// result).  A wait gives up after `limit` polls or kWaitNs of wall time, whichever comes
+// first, or as soon as another wait has given up; the first wait that gives up records `tag`
+// in *where.  Returns false when it gave up.
 template <class GR>
 __device__ bool group_wait(const GR& g, const unsigned* flag, unsigned target, unsigned* status,
-                           long long limit) {
+                           long long limit, unsigned* where = nullptr, unsigned tag = 0) {
   bool ok = false;
+  const unsigned long long t0 = global_ns();
   for (long long it = 0;; ++it) {
     if (ld_acquire_u32(flag) >= target) {
       ok = true;
       break;
     }
     if (ld_acquire_u32(status) & kStatusTimeout) break;
-    if (it >= limit) {
+    if (it >= limit || global_ns() - t0 > kWaitNs) {
+      if (where) atomicCAS(where, 0u, tag);
       atomicOr(status, kStatusTimeout);
       break;
     }
@@ -112,7 +130,8 @@ __device__ __forceinline__ void fetch_item(const typename C::GR& g, const typena
 template <class C, class OPS, bool REVERSE>
 __device__ bool cross_block_scan(const typename C::GR& g, int pos, typename C::Tp* cur,
                                  typename C::Tp* xpre, typename C::Tp* tmp, typename C::Tp* scr,
-                                 typename C::Tp* buf, unsigned* flags, const FusedXchg<typename C::Tp>& x) {
+                                 typename C::Tp* buf, unsigned* flags,
+                                 const FusedXchg<typename C::Tp>& x, unsigned phase) {
   constexpr int SZ = OPS::SZ;
   const unsigned base = x.epoch * 64u;
   const size_t lvl = static_cast<size_t>(x.NB) * SZ;
@@ -121,7 +140,8 @@ __device__ bool cross_block_scan(const typename C::GR& g, int pos, typename C::T
   for (int k = 0; k < x.K; ++k) {
     const int s = 1 << k;
     if (pos >= s) {
-      ok = ok && group_wait(g, flags + (pos - s), base + k + 1, x.status, x.spin_limit);
+      ok = ok && group_wait(g, flags + (pos - s), base + k + 1, x.status, x.spin_limit, x.where,
+                            wait_tag(phase, pos, k));
       if (ok) {
         fetch_item<C, SZ>(g, buf + k * lvl + static_cast<size_t>(pos - s) * SZ, tmp);
         OPS::template op<REVERSE>(g, tmp, cur, cur, scr);
@@ -131,7 +151,8 @@ __device__ bool cross_block_scan(const typename C::GR& g, int pos, typename C::T
                      base + k + 2);
   }
   if (pos > 0) {
-    ok = ok && group_wait(g, flags + (pos - 1), base + x.K + 1, x.status, x.spin_limit);
+    ok = ok && group_wait(g, flags + (pos - 1), base + x.K + 1, x.status, x.spin_limit, x.where,
+                          wait_tag(phase, pos, x.K + 1));
     if (ok) fetch_item<C, SZ>(g, buf + x.K * lvl + static_cast<size_t>(pos - 1) * SZ, xpre);
   }
   return ok;
@@ -274,7 +295,7 @@ k_iteration(const IeksParams<typename C::Tp> p,
   block_tree<C, OPF, false>(items, NGB, nv, tmp, scr, g, grp, NGB, true, false, nullptr);
   if (grp == 0)
     cross_block_scan<C, OPF, false>(g, blockIdx.x, items + (NGB - 1) * FA, xpre, tmp, scr,
-                                    x.fbuf, x.fflag, x);
+                                    x.fbuf, x.fflag, x, 0u);
   __syncthreads();
   block_tree<C, OPF, false>(items, NGB, nv, tmp, scr, g, grp, NGB, false, true,
                             blockIdx.x > 0 ? xpre : nullptr);
@@ -294,7 +315,7 @@ k_iteration(const IeksParams<typename C::Tp> p,
   block_tree<C, OPS, true>(items, NGB, nv, tmp, scr, g, grp, NGB, true, false, nullptr);
   if (grp == 0)
     cross_block_scan<C, OPS, true>(g, rpos, items + (NGB - 1) * SA, xpre, tmp, scr, x.sbuf,
-                                   x.sflag, x);
+                                   x.sflag, x, 1u);
   __syncthreads();
   block_tree<C, OPS, true>(items, NGB, nv, tmp, scr, g, grp, NGB, false, true,
                            rpos > 0 ? xpre : nullptr);
@@ -309,7 +330,9 @@ k_iteration(const IeksParams<typename C::Tp> p,
         __threadfence();
         atomicAdd(x.barrier, 1u);
       }
-      if (grp == 0) group_wait(g, x.barrier, x.bar_target, x.status, x.spin_limit);
+      if (grp == 0)
+        group_wait(g, x.barrier, x.bar_target, x.status, x.spin_limit, x.where,
+                   wait_tag(2u, blockIdx.x, 0u));
       __syncthreads();
     }
   }

@@ -448,7 +448,8 @@ struct SolverImpl {
 
   // Single-launch iterations (k_iteration) exist for the one-row-per-lane layout only.
   static constexpr bool kFusable = (G == GT) && (RL == RLT);
-  static constexpr long long kSpinLimit = 1LL << 23;  // polls (~1-2 s) per cross-block wait
+  static constexpr long long kSpinLimit = 1LL << 30;  // polls per cross-block wait (the 4 s
+                                                      // wall-time bound comes first)
 
   // Chains that one cooperative launch of k_iteration can hold (all blocks resident), or 0
   // when it cannot run here (shared memory, no device).
@@ -538,8 +539,14 @@ struct SolverImpl {
   struct ScalBlock {
     SolveScalars s;
     unsigned status;
-    unsigned pad[3];
+    unsigned where;  // first cross-block wait that ran out (wait_tag code), or 0
+    unsigned pad[2];
   };
+  static std::string wait_report(unsigned w) {
+    static const char* phases[] = {"filter scan", "smoothing scan", "calibration barrier", "?"};
+    return std::string(" (") + phases[(w >> 28) & 3u] + ", block position " +
+           std::to_string(w & 0xffffu) + ", level " + std::to_string((w >> 16) & 0xffu) + ")";
+  }
 
   struct Buffers {
     V *linA, *linB;
@@ -680,6 +687,7 @@ struct SolverImpl {
       x.fflag = b.xflags;
       x.sflag = b.xflags + b.xNB;
       x.status = &b.sblock->status;
+      x.where = &b.sblock->where;
       x.barrier = b.xflags + 2 * b.xNB;
       x.bar_target = cov_launch * static_cast<unsigned>(b.xNB);
       x.epoch = epoch;
@@ -779,10 +787,10 @@ struct SolverImpl {
     std::memset(&hb, 0, sizeof(hb));
     SolveScalars& hs = hb.s;
     unsigned epoch = 0;  // single-launch iterations: launches since the flags were cleared
-    if (p.fused) {
+    // the status words are read back with the reductions on either path: clear them per solve
+    PIT_CUDA_TRY(cudaMemsetAsync(&b.sblock->status, 0, 2 * sizeof(unsigned), s));
+    if (p.fused)
       PIT_CUDA_TRY(cudaMemsetAsync(b.xflags, 0, (2 * b.xNB + 1) * sizeof(unsigned), s));
-      PIT_CUDA_TRY(cudaMemsetAsync(&b.sblock->status, 0, sizeof(unsigned), s));
-    }
 
     if (eks) {
       // sequential EKS: one chain, local linearisation at the predicted mean, plain model
@@ -876,9 +884,9 @@ struct SolverImpl {
       if (fixed <= 0 || want_obj) {
         PIT_CUDA_TRY(cudaMemcpyAsync(&hb, b.sblock, sizeof(hb), cudaMemcpyDeviceToHost, s));
         PIT_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hb.status & kStatusTimeout) {
+        if (p.fused && (hb.status & kStatusTimeout)) {
           set_error("a cross-block wait of the iteration kernel ran out at iteration " +
-                    std::to_string(k + 1));
+                    std::to_string(k) + wait_report(hb.where));
           return PIT_ETIMEOUT;
         }
         if (hs.flags & 1u) {
@@ -924,7 +932,7 @@ struct SolverImpl {
     PIT_CUDA_TRY(cudaStreamSynchronize(s));
     const SolveScalars& hs2 = hb2.s;
     if (p.fused && (hb2.status & kStatusTimeout)) {
-      set_error("a cross-block wait of the iteration kernel ran out");
+      set_error("a cross-block wait of the iteration kernel ran out" + wait_report(hb2.where));
       return PIT_ETIMEOUT;
     }
     if (fixed > 0 && !want_cov) info.last_delta = hs2.delta_max;
