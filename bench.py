@@ -450,7 +450,7 @@ def run_pit(args):
 
 # ---- batched Lotka-Volterra (segmented scans over 4096 instances) ------------------------------
 def measure_lv_batch(instances: int, steps: int, warmup: int, seed: int, max_iter: int,
-                     single: int, world: int = 1, dev=None):
+                     single: int, world: int = 1, dev=None, scan: int = 0):
     """Batched FP32 Lotka-Volterra solves: steps*iterations/s over all instances and over the
     instances that met the stop rule, converged and diverged fractions, end-to-end rate, and
     the same instances (the first `single`) one at a time through the single-problem FP64
@@ -464,7 +464,7 @@ def measure_lv_batch(instances: int, steps: int, warmup: int, seed: int, max_ite
     probs = W.lotka_volterra_batch(count=instances, seed=seed)
     Ns = np.array([p.N for p in probs])
     opts = pit.make_opts(dtype=torch.float32, max_iter=max_iter, atol_delta=1e-10,
-                         rtol_delta=1e-6, want_cov=False, calibrate=True)
+                         rtol_delta=1e-6, want_cov=False, calibrate=True, scan=scan)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -531,7 +531,10 @@ def measure_lv_batch(instances: int, steps: int, warmup: int, seed: int, max_ite
                     f"(1.5,1,3,1)*U[0.8,1.2], y0~U[0.5,2]^2, t in [0,10], N log-uniform in "
                     f"[256,16384] (sum N = {int(Ns.sum())}), IWP(2), FP32, one batched solve "
                     f"per step, stop per instance at max|dy|<=1e-10+1e-6 max|y| or {max_iter} "
-                    f"iterations, means + sigma^2",
+                    f"iterations, means + sigma^2; "
+                    + ("all means iterations in one cooperative launch (stopping rules and "
+                       "compaction on the device)" if scan == 0 else
+                       "host-driven iterations, one launch per scan phase"),
         "iterations_mean": float(np.mean(r.iterations)),
         "converged_fraction": float(np.mean(r.converged)),
         "diverged_fraction": float(np.mean(r.status == 6)),
@@ -561,7 +564,8 @@ def run_lv_batch(args):
     dev = torch.device("cuda", local_rank)
     pit.load()
     res, prof = measure_lv_batch(args.instances, args.steps, args.warmup, seed=rank,
-                                 max_iter=args.batch_max_iter, single=32, world=world, dev=dev)
+                                 max_iter=args.batch_max_iter, single=32, world=world, dev=dev,
+                                 scan=args.scan)
     shares = {k: v for k, v in prof.items() if v[1] > 0}
     total_ms = sum(v[0] for v in shares.values())
     out = {

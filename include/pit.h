@@ -117,8 +117,11 @@ typedef struct {
   int32_t scan;         /* [0]   0: each IEKS iteration of a single-problem solve is one
                                  cooperative launch (residuals, chain folds, decoupled
                                  cross-block scans, down-sweeps) when the layout is variant 0,
-                                 d <= 3 and the chains fit one resident wave, else as 1;
-                                 1: one launch per scan phase with block-level scan trees     */
+                                 d <= 3 and the chains fit one resident wave, and all means
+                                 iterations of a batched solve are one cooperative launch
+                                 (stopping rules and compaction of the active instances on
+                                 the device); else as 1.  1: one launch per scan phase with
+                                 block-level scan trees, host-driven iteration loop          */
 } pit_opts;
 
 /* Linearisation of the vector field (pit_opts.linearization). */

@@ -178,6 +178,173 @@ k_seg_residuals(const IeksParams<typename C::Tp> p, typename C::Tp* __restrict__
   }
 }
 
+// ---- all means iterations of a batch in one cooperative launch ------------------------------
+// Arguments of k_batch_iterations.
+template <typename T>
+struct BatchRun {
+  InstDesc<T>* desc;     // by instance id (offsets and current trajectories are rewritten)
+  InstAcc* acc;          // per-instance reductions of the pass
+  int* inst_of;          // per global point of the current layout
+  int* ids;              // active instance ids in layout order
+  SegIterState* st;      // per instance id
+  int64_t* ctl;          // [0] points of the current layout, [1] active instances
+  unsigned* bar;         // grid-barrier arrivals (cleared before the launch)
+  T *U, *R, *Yv, *d0, *Es, *gs;
+  int limit, fixed, calibrate, d, chain_len;
+  double atol, rtol, diverged;
+  int64_t cap;           // chains one launch holds
+};
+
+// Block 0 rewrites the layout after the stopping decisions: the active instances keep their
+// order, each gets its new offset (exclusive prefix sum of N + 1 over the instances before it),
+// and ctl receives the new point and instance counts.  Chunks of NT instances, prefix sums in
+// shared memory; within a chunk every read happens before any write.
+template <typename T, int NT>
+__device__ void batch_compact(const BatchRun<T>& r, unsigned char* smem_raw) {
+  int64_t* s_sz = reinterpret_cast<int64_t*>(smem_raw);
+  int* s_ct = reinterpret_cast<int*>(smem_raw + 2 * NT * sizeof(int64_t));
+  const int t = threadIdx.x;
+  const int nact = static_cast<int>(r.ctl[1]);
+  int out = 0;
+  int64_t off = 0;
+  for (int c0 = 0; c0 < nact; c0 += NT) {
+    const int j = c0 + t;
+    const int id = j < nact ? r.ids[j] : -1;
+    const bool keep = id >= 0 && r.st[id].active;
+    const int64_t sz = keep ? r.desc[id].N + 1 : 0;
+    s_sz[t] = sz;
+    s_ct[t] = keep ? 1 : 0;
+    __syncthreads();
+    // inclusive Hillis-Steele scans (ping-pong halves of the buffers)
+    int src = 0;
+    for (int o = 1; o < NT; o <<= 1) {
+      const int64_t a = s_sz[src * NT + t] + (t >= o ? s_sz[src * NT + t - o] : 0);
+      const int b = s_ct[src * NT + t] + (t >= o ? s_ct[src * NT + t - o] : 0);
+      s_sz[(1 - src) * NT + t] = a;
+      s_ct[(1 - src) * NT + t] = b;
+      __syncthreads();
+      src = 1 - src;
+    }
+    if (keep) {
+      r.ids[out + s_ct[src * NT + t] - 1] = id;
+      r.desc[id].off = off + s_sz[src * NT + t] - sz;
+    }
+    out += s_ct[src * NT + NT - 1];
+    off += s_sz[src * NT + NT - 1];
+    __syncthreads();
+  }
+  if (t == 0) {
+    r.ctl[0] = off;
+    r.ctl[1] = out;
+  }
+}
+
+// All means iterations of a batch (Algorithm 2 per instance) in one cooperative launch.  Per
+// iteration: the segmented IEKS pass over the current layout (iteration_body, chain length
+// chosen so that the chains fill the resident blocks), a grid barrier, every active
+// instance's stopping rule (the host loop's rule: non-finite or diverging values, fixed
+// iteration count, max|dy| <= atol + rtol max|y|, iteration cap), a grid barrier, compaction of
+// the active instances by block 0, a grid barrier, the new per-point instance map and cleared
+// reductions, a grid barrier.  Every barrier and every cross-block wait is bounded (see
+// group_wait); after a timeout the launch runs to its end without waiting and the host reports
+// PIT_ETIMEOUT.
+template <class C>
+__global__ void __launch_bounds__(FusedShape<C>::NT, 1)
+k_batch_iterations(const IeksParams<typename C::Tp> p0, const BatchRun<typename C::Tp> r,
+                   const FusedXchg<typename C::Tp> x0) {
+  using T = typename C::Tp;
+  using FS = FusedShape<C>;
+  constexpr int NT = FS::NT, NGB = FS::NGB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typename C::GR g;
+  g.init();
+  const int grp = threadIdx.x / C::G;
+  unsigned gen = 0;
+  auto grid_barrier = [&](unsigned k) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(r.bar, 1u);
+    }
+    ++gen;
+    if (grp == 0) {
+      group_wait(g, r.bar, gen * gridDim.x, x0.status, x0.spin_limit, x0.where,
+                 wait_tag(3u, blockIdx.x, k));
+      __threadfence();
+    }
+    __syncthreads();
+  };
+  for (int k = 1; k <= r.limit; ++k) {
+    const int64_t M = r.ctl[0];
+    const int nact = static_cast<int>(r.ctl[1]);
+    if (nact <= 0 || (ld_acquire_u32(x0.status) & kStatusTimeout)) break;
+    // the iteration's parameters: the layout changes N, L and P (a local copy, whose hot fields
+    // stay in registers; measured faster than a shared-memory copy)
+    IeksParams<T> p = p0;
+    p.N = M - 1;
+    if (r.chain_len > 0) {
+      p.L = r.chain_len;
+    } else {
+      const int64_t L = (M + r.cap - 1) / r.cap;
+      p.L = static_cast<int>(L > 4 ? L : 4);
+    }
+    p.P = p.N / p.L + 1;
+    const int nb = static_cast<int>((p.P + NGB - 1) / NGB);
+    FusedXchg<T> x = x0;
+    x.NB = nb;
+    x.K = 0;
+    while ((1 << x.K) < nb) ++x.K;
+    x.epoch = static_cast<unsigned>(k);
+    if (static_cast<int>(blockIdx.x) < nb)
+      iteration_body<C, false, true>(p, blockIdx.x, nullptr, nullptr, r.U, r.R, r.Yv, r.d0, r.Es,
+                                     r.gs, nullptr, nullptr, nullptr, nullptr, x, smem_raw);
+    grid_barrier(k);
+    // stopping rule of every instance of the pass
+    for (int j = blockIdx.x * NT + threadIdx.x; j < nact; j += gridDim.x * NT) {
+      const int id = r.ids[j];
+      const InstAcc a = r.acc[id];
+      SegIterState& s = r.st[id];
+      const double Ni = static_cast<double>(r.desc[id].N);
+      s.iters = k;
+      s.last_delta = a.delta_max;
+      s.sigma2 = r.calibrate ? a.sigma2_sum / (Ni * r.d) : 1.0;
+      bool stop = false, conv = false, fail = false;
+      if ((a.flags & 1u) || !(a.delta_max <= r.diverged)) {
+        stop = fail = true;
+      } else if (r.fixed > 0) {
+        stop = conv = (k == r.limit);
+      } else if (a.delta_max <= r.atol + r.rtol * a.y_max) {
+        stop = conv = true;
+      } else if (k == r.limit) {
+        stop = true;
+      }
+      if (!stop) {
+        s.cur ^= 1;
+        r.desc[id].cur = s.cur;
+      }
+      s.active = stop ? 0 : 1;
+      s.converged = conv ? 1 : 0;
+      s.failed = fail ? 1 : 0;
+    }
+    grid_barrier(k);
+    if (blockIdx.x == 0) batch_compact<T, NT>(r, smem_raw);
+    grid_barrier(k);
+    // the next layout: per-point instance codes, cleared reductions
+    const int nnext = static_cast<int>(r.ctl[1]);
+    for (int j = blockIdx.x; j < nnext; j += gridDim.x) {
+      const int id = r.ids[j];
+      const int64_t off = r.desc[id].off;
+      const int64_t Ni = r.desc[id].N;
+      for (int64_t n = threadIdx.x; n <= Ni; n += NT) r.inst_of[off + n] = (n == 0) ? ~id : id;
+      if (threadIdx.x == 0) {
+        InstAcc z = {};
+        r.acc[id] = z;
+      }
+    }
+    grid_barrier(k);
+  }
+}
+
 template <typename T, int DD, int Q1, int G, int RL>
 class SegEngineImpl final : public SegEngine {
  public:
@@ -207,7 +374,34 @@ class SegEngineImpl final : public SegEngine {
     InstAcc* acc;
     int* inst_of;
     SegSlot* slots;
+    // device-iterated batches (run_iterations)
+    SegIterState* st;
+    int* ids;
+    int64_t* ctl;
+    unsigned* words;  // [0] status, [1] first timeout, [2] grid-barrier arrivals
+    T *xf, *xs;
+    unsigned* xflags;
+    int xNB, xK;
   };
+
+  // Blocks of k_batch_iterations that are resident at once (0 where it cannot run).
+  static int persistent_blocks() {
+    static std::atomic<int> cached{0};
+    const int c = cached.load(std::memory_order_relaxed);
+    if (c > 0) return c;
+    using FS = FusedShape<C>;
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_batch_iterations<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(FS::smem)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_iterations<C>, FS::NT,
+                                                      FS::smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    const int v = nb * sm_count();
+    cached.store(v, std::memory_order_relaxed);
+    return v;
+  }
 
   size_t carve(void* ws, size_t bytes, int64_t max_points, int max_inst, bool want_cov,
                int chain_len, Bufs& b) const {
@@ -232,6 +426,17 @@ class SegEngineImpl final : public SegEngine {
     b.acc = cv.take<InstAcc>(max_inst);
     b.inst_of = cv.take<int>(M);
     b.slots = cv.take<SegSlot>(max_inst);
+    b.st = cv.take<SegIterState>(max_inst);
+    b.ids = cv.take<int>(max_inst);
+    b.ctl = cv.take<int64_t>(2);
+    b.words = cv.take<unsigned>(4);
+    b.xNB = persistent_blocks();
+    b.xK = 0;
+    while ((1 << b.xK) < b.xNB) ++b.xK;
+    const size_t lv = static_cast<size_t>(b.xK + 1) * b.xNB;
+    b.xf = b.xNB ? cv.take<T>(lv * C::FA) : nullptr;
+    b.xs = b.xNB ? cv.take<T>(lv * C::SA) : nullptr;
+    b.xflags = b.xNB ? cv.take<unsigned>(2 * static_cast<size_t>(b.xNB)) : nullptr;
     return cv.used();
   }
 
@@ -554,6 +759,119 @@ class SegEngineImpl final : public SegEngine {
     int st = pass_begin(slots, n, with_L, calibrate, s);
     if (st != PIT_OK) return st;
     return pass_end(res, s);
+  }
+
+  int run_iterations(int n, const pit_opts& o, double diverged_delta, SegIterState* out,
+                     cudaStream_t s) override {
+    using FS = FusedShape<C>;
+    if (decoupled_ || b_.xNB <= 0 || n < 1 || n > max_inst_) return PIT_EUNSUPPORTED;
+    const int64_t cap = static_cast<int64_t>(b_.xNB) * FS::NGB;
+    std::vector<SegSlot> slots(n);
+    std::vector<int> ids(n);
+    std::vector<SegIterState> st(n);
+    int64_t M = 0;
+    for (int i = 0; i < n; ++i) {
+      slots[i] = SegSlot{i, 0, M};
+      ids[i] = i;
+      st[i] = SegIterState{0, 0, 1, 0, 0, 0, 0.0, 1.0};
+      M += Ns_[i] + 1;
+    }
+    if (M > max_points_ || M < 2) {
+      set_error("layout exceeds the engine's point capacity");
+      return PIT_EINVAL;
+    }
+    if (o.chain_len > 0 && (M - 2) / o.chain_len + 1 > cap) return PIT_EUNSUPPORTED;
+    // the first layout (every instance, trajectories lin[0]) and cleared state
+    int st0 = upload_slots(slots.data(), n, s);
+    if (st0 != PIT_OK) return st0;
+    PIT_LAUNCH(KC_INIT, s,
+               k_seg_layout<T><<<static_cast<unsigned>(n), 256, 0, s>>>(b_.slots, b_.desc,
+                                                                       b_.inst_of););
+    PIT_CUDA_TRY(cudaMemsetAsync(b_.acc, 0, sizeof(InstAcc) * max_inst_, s));
+    PIT_CUDA_TRY(cudaMemsetAsync(b_.words, 0, 4 * sizeof(unsigned), s));
+    PIT_CUDA_TRY(cudaMemsetAsync(b_.xflags, 0, 2 * sizeof(unsigned) * b_.xNB, s));
+    const int64_t ctl[2] = {M, n};
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.ids, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(b_.st, st.data(), sizeof(SegIterState) * n,
+                                 cudaMemcpyHostToDevice, s));
+    IeksParams<T> p = shared_;
+    p.want_cov = 0;
+    p.calibrate = o.calibrate;
+    p.lin_mode = lin_mode_;
+    p.want_sigma = 1;
+    p.sigma_pool = 0;
+    p.seg.desc = b_.desc;
+    p.seg.inst_of = b_.inst_of;
+    p.seg.acc = b_.acc;
+    BatchRun<T> r;
+    r.desc = b_.desc;
+    r.acc = b_.acc;
+    r.inst_of = b_.inst_of;
+    r.ids = b_.ids;
+    r.st = b_.st;
+    r.ctl = b_.ctl;
+    r.bar = b_.words + 2;
+    r.U = b_.U;
+    r.R = b_.R;
+    r.Yv = b_.Yv;
+    r.d0 = b_.d0;
+    r.Es = b_.Es;
+    r.gs = b_.gs;
+    r.limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
+    r.fixed = o.fixed_iters;
+    r.calibrate = o.calibrate;
+    r.d = DD;
+    r.chain_len = o.chain_len;
+    r.atol = o.atol_delta;
+    r.rtol = o.rtol_delta;
+    r.diverged = diverged_delta;
+    r.cap = cap;
+    FusedXchg<T> x;
+    std::memset(&x, 0, sizeof(x));
+    x.fbuf = b_.xf;
+    x.sbuf = b_.xs;
+    x.fflag = b_.xflags;
+    x.sflag = b_.xflags + b_.xNB;
+    x.status = b_.words;
+    x.where = b_.words + 1;
+    x.NB = b_.xNB;
+    x.K = b_.xK;
+    x.spin_limit = Base::kSpinLimit;
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_batch_iterations<C>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(FS::smem)));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(b_.xNB));
+    cfg.blockDim = dim3(FS::NT);
+    cfg.dynamicSmemBytes = FS::smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaSuccess;
+    PIT_LAUNCH(KC_ITERATION, s, e = cudaLaunchKernelEx(&cfg, k_batch_iterations<C>, p, r, x));
+    if (e != cudaSuccess) {
+      set_error(std::string("cooperative launch of the batched iterations: ") +
+                cudaGetErrorString(e));
+      return PIT_ECUDA;
+    }
+    unsigned words[4];
+    PIT_CUDA_TRY(cudaMemcpyAsync(out, b_.st, sizeof(SegIterState) * n, cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaMemcpyAsync(words, b_.words, sizeof(words), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (words[0] & kStatusTimeout) {
+      static const char* phases[] = {"filter scan", "smoothing scan", "calibration barrier",
+                                     "grid barrier"};
+      const unsigned w = words[1];
+      set_error(std::string("a cross-block wait of the batched iterations ran out (") +
+                phases[(w >> 28) & 3u] + ", block position " + std::to_string(w & 0xffffu) +
+                ", iteration/level " + std::to_string((w >> 16) & 0xffu) + ")");
+      return PIT_ETIMEOUT;
+    }
+    return PIT_OK;
   }
 
   static SegEngine* make() { return new SegEngineImpl(); }

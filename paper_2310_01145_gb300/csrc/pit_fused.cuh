@@ -248,29 +248,95 @@ __device__ void residual_steps(const IeksParams<typename C::Tp>& p,
   }
 }
 
-template <class C, bool WITH_L>
-__global__ void __launch_bounds__(FusedShape<C>::NT, 1)
-k_iteration(const IeksParams<typename C::Tp> p,
-            const typename TrajType<typename C::Tp>::type* __restrict__ lin,
-            typename TrajType<typename C::Tp>::type* __restrict__ lin_out,
-            typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
-            typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0,
-            typename C::Tp* __restrict__ Es, typename C::Tp* __restrict__ gs,
-            typename C::Tp* __restrict__ Ls, typename C::Tp* __restrict__ mean_out,
-            typename C::Tp* __restrict__ cov_out, SolveScalars* __restrict__ scal,
-            const FusedXchg<typename C::Tp> x) {
+// Residuals of the increment model for the time steps n in [lo, hi] of a segmented layout (see
+// k_seg_residuals): instance id = the owner of point n, local index m = n - off_id.  Step n reads
+// rows m-1 and m of the instance's own trajectory; at an instance's first point (m = 0) it
+// writes that instance's delta_0 instead of u (the point is a reset element).  Block 0 also
+// writes delta_0 of the instance at global point 0.  One thread per step.
+template <class C, int NT>
+__device__ void residual_steps_seg(const IeksParams<typename C::Tp>& p,
+                                   typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
+                                   typename C::Tp* __restrict__ Yv,
+                                   typename C::Tp* __restrict__ d0, int64_t lo, int64_t hi) {
+  using T = typename C::Tp;
+  using V = typename TrajType<T>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  auto start = [&](int id, const InstDesc<T>& d) {
+    const V* lin = static_cast<const V*>(d.lin[d.cur]);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+      d0[static_cast<int64_t>(id) * D + r] = v_to_T<T>(v_from_double<V>(d.mu0d[r]) - lin[r]);
+  };
+  if (lo == 1 && threadIdx.x == 0) {
+    const int id = seg_id(p.seg.inst_of[0]);
+    start(id, p.seg.desc[id]);
+  }
+  for (int64_t n = lo + threadIdx.x; n <= hi; n += NT) {
+    const int id = seg_id(p.seg.inst_of[n]);
+    const InstDesc<T>& d = p.seg.desc[id];
+    const int64_t m = n - d.off;
+    const V* lin = static_cast<const V*>(d.lin[d.cur]);
+    V x[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) x[r] = lin[m * D + r];
+    if (m == 0) {
+      start(id, d);
+    } else {
+#pragma unroll
+      for (int k = 0; k < DD; ++k) {
+#pragma unroll
+        for (int i = 0; i < Q1; ++i) {
+          V acc = lin[(m - 1) * D + k * Q1 + i];
+#pragma unroll
+          for (int j = i + 1; j < Q1; ++j)
+            acc = acc + lin[(m - 1) * D + k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+          acc = acc - x[k * Q1 + i];
+          U[(n - 1) * D + k * Q1 + i] = v_to_T<T>(acc);
+        }
+      }
+    }
+    OdeConstsV<V> oc;
+    ode_consts_v<V, T, DD>(p.ode, d.pd, oc);
+    const V T0v = v_from_double<V>(d.T0d);
+    const V T1iv = v_from_double<V>(d.T1invd);
+    V y[DD], f[DD];
+#pragma unroll
+    for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
+    ode_f_v<V, DD>(oc, y, f);
+#pragma unroll
+    for (int k = 0; k < DD; ++k) {
+      Yv[n * DD + k] = v_to_T<T>(y[k]);
+      R[n * DD + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
+    }
+  }
+  __syncthreads();
+}
+
+// One IEKS iteration of the chains of block `blk` (phases 0 and A-G above).  SEG: the time axis
+// is a segmented layout of many instances (segment boundaries absorb in the operators, see
+// InstDesc).  Every thread of the block calls it.
+template <class C, bool WITH_L, bool SEG>
+__device__ __forceinline__ void iteration_body(
+    const IeksParams<typename C::Tp>& p, int blk,
+    const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+    typename TrajType<typename C::Tp>::type* __restrict__ lin_out,
+    typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
+    typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0,
+    typename C::Tp* __restrict__ Es, typename C::Tp* __restrict__ gs,
+    typename C::Tp* __restrict__ Ls, typename C::Tp* __restrict__ mean_out,
+    typename C::Tp* __restrict__ cov_out, SolveScalars* __restrict__ scal,
+    const FusedXchg<typename C::Tp>& x, unsigned char* smem_raw) {
   using T = typename C::Tp;
   using GR = typename C::GR;
   using FS = FusedShape<C>;
   using OPF = TreeOps<C, true, false, true>;
   using OPS = TreeOps<C, false, WITH_L>;
   constexpr int NGB = FS::NGB, FA = C::FA, SA = C::SA;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   GR g;
   g.init();
   const int grp = threadIdx.x / C::G;
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * NGB;
+  const int64_t base = static_cast<int64_t>(blk) * NGB;
   const int64_t chain = base + grp;
   const int nv = static_cast<int>(p.P - base < NGB ? p.P - base : NGB);  // chains of this block
   T* scr = smem + grp * C::SCR;
@@ -283,35 +349,36 @@ k_iteration(const IeksParams<typename C::Tp> p,
     const int64_t lo = base * p.L + 1;
     int64_t hi = (base + nv) * p.L;
     hi = hi < p.N ? hi : p.N;
-    residual_steps<C, FS::NT>(p, lin, U, R, Yv, d0, lo, hi, smem_raw);
+    if constexpr (SEG) residual_steps_seg<C, FS::NT>(p, U, R, Yv, d0, lo, hi);
+    else residual_steps<C, FS::NT>(p, lin, U, R, Yv, d0, lo, hi, smem_raw);
   }
-  // (the last __syncthreads of residual_steps orders its global stores before the chains)
+  // (the last __syncthreads of the residual phase orders its global stores before the chains)
 
   // A. filter chain aggregates
-  if (chain < p.P) filter_reduce_chain<C, false>(g, p, U, R, Yv, d0, chain, scr, items + grp * FA);
+  if (chain < p.P) filter_reduce_chain<C, SEG>(g, p, U, R, Yv, d0, chain, scr, items + grp * FA);
   else set_identity_f<C>(g, items + grp * FA);
   __syncthreads();
   // B. block up-sweep; C. cross-block scan; D. down-sweep to chain prefixes
   block_tree<C, OPF, false>(items, NGB, nv, tmp, scr, g, grp, NGB, true, false, nullptr);
   if (grp == 0)
-    cross_block_scan<C, OPF, false>(g, blockIdx.x, items + (NGB - 1) * FA, xpre, tmp, scr,
-                                    x.fbuf, x.fflag, x, 0u);
+    cross_block_scan<C, OPF, false>(g, blk, items + (NGB - 1) * FA, xpre, tmp, scr, x.fbuf,
+                                    x.fflag, x, 0u);
   __syncthreads();
   block_tree<C, OPF, false>(items, NGB, nv, tmp, scr, g, grp, NGB, false, true,
-                            blockIdx.x > 0 ? xpre : nullptr);
+                            blk > 0 ? xpre : nullptr);
   __syncthreads();
   // E. filter down-sweep of every chain; its smoothing aggregate goes to position nv-1-grp
   // (reverse order for the smoothing scan)
   if (chain < p.P)
-    filter_down_chain<C, WITH_L, false, false>(g, p, U, R, Yv, d0, items + grp * FA, Es, gs, Ls,
-                                               tmp, scal, chain, scr);
+    filter_down_chain<C, WITH_L, false, SEG>(g, p, U, R, Yv, d0, items + grp * FA, Es, gs, Ls,
+                                             tmp, scal, chain, scr);
   __syncthreads();
   // the aggregates were written to each group's temporary slot; move them into scan positions
   if (chain < p.P) copy_item<C, SA>(g, tmp, items + (nv - 1 - grp) * SA);
-  else if (grp < NGB) set_identity_s<C>(g, items + grp * SA);
+  else set_identity_s<C>(g, items + grp * SA);
   __syncthreads();
   // F. reverse smoothing scan over the block's aggregates and across blocks
-  const int rpos = x.NB - 1 - static_cast<int>(blockIdx.x);
+  const int rpos = x.NB - 1 - blk;
   block_tree<C, OPS, true>(items, NGB, nv, tmp, scr, g, grp, NGB, true, false, nullptr);
   if (grp == 0)
     cross_block_scan<C, OPS, true>(g, rpos, items + (NGB - 1) * SA, xpre, tmp, scr, x.sbuf,
@@ -323,7 +390,7 @@ k_iteration(const IeksParams<typename C::Tp> p,
   // The covariance pass scales its outputs by the quasi-MLE sigma-hat, a sum over every
   // block's filter steps (phase E): wait until all blocks have added their part.  The reverse
   // scan above only orders this block after the blocks later in time.
-  if constexpr (WITH_L) {
+  if constexpr (WITH_L && !SEG) {
     if (p.calibrate) {
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -332,14 +399,30 @@ k_iteration(const IeksParams<typename C::Tp> p,
       }
       if (grp == 0)
         group_wait(g, x.barrier, x.bar_target, x.status, x.spin_limit, x.where,
-                   wait_tag(2u, blockIdx.x, 0u));
+                   wait_tag(2u, blk, 0u));
       __syncthreads();
     }
   }
   // G. smoothing down-sweep of every chain from its prefix
   if (chain < p.P)
-    smooth_down_chain<C, WITH_L, false>(g, p, Es, gs, Ls, items + (nv - 1 - grp) * SA, lin,
-                                        lin_out, mean_out, cov_out, scal, chain, scr);
+    smooth_down_chain<C, WITH_L, SEG>(g, p, Es, gs, Ls, items + (nv - 1 - grp) * SA, lin,
+                                      lin_out, mean_out, cov_out, scal, chain, scr);
+}
+
+template <class C, bool WITH_L>
+__global__ void __launch_bounds__(FusedShape<C>::NT, 1)
+k_iteration(const IeksParams<typename C::Tp> p,
+            const typename TrajType<typename C::Tp>::type* __restrict__ lin,
+            typename TrajType<typename C::Tp>::type* __restrict__ lin_out,
+            typename C::Tp* __restrict__ U, typename C::Tp* __restrict__ R,
+            typename C::Tp* __restrict__ Yv, typename C::Tp* __restrict__ d0,
+            typename C::Tp* __restrict__ Es, typename C::Tp* __restrict__ gs,
+            typename C::Tp* __restrict__ Ls, typename C::Tp* __restrict__ mean_out,
+            typename C::Tp* __restrict__ cov_out, SolveScalars* __restrict__ scal,
+            const FusedXchg<typename C::Tp> x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  iteration_body<C, WITH_L, false>(p, blockIdx.x, lin, lin_out, U, R, Yv, d0, Es, gs, Ls,
+                                   mean_out, cov_out, scal, x, smem_raw);
 }
 
 }  // namespace pit

@@ -163,6 +163,19 @@ struct SegResult {
   unsigned int flags;
   unsigned int pad;
 };
+// Per-instance state of a batched solve iterated on the device (SegEngine::run_iterations);
+// the same layout on host and device.
+struct SegIterState {
+  int32_t cur;        // lin[cur] is the instance's current linearisation trajectory
+  int32_t iters;      // IEKS iterations it took part in
+  int32_t active;     // still iterating
+  int32_t converged;  // its stopping rule was met (or fixed_iters ran out)
+  int32_t failed;     // non-finite or diverging values
+  int32_t pad;
+  double last_delta;  // max |change of E0 mean| of its last iteration
+  double sigma2;      // quasi-MLE diffusion of its last pass (1 without calibration)
+};
+
 // Engine of one (dtype, d, q): device state of up to max_inst instances and the per-point
 // buffers of passes over up to max_points global points.
 class SegEngine {
@@ -202,6 +215,12 @@ class SegEngine {
   virtual int use_pinned_staging() = 0;
   // mean <- T lin[1 - cur] (the last means pass), for every slot
   virtual int export_means(const SegSlot* slots, int n, cudaStream_t s) = 0;
+  // All means iterations of instances 0..n-1 (trajectories initialised) in one cooperative
+  // launch: per iteration the segmented IEKS pass, every instance's stopping rule and the
+  // compaction of the active instances run on the device.  Fills out[0..n-1].  Returns
+  // PIT_EUNSUPPORTED (nothing launched) when the layout does not fit one resident wave.
+  virtual int run_iterations(int n, const pit_opts& o, double diverged_delta,
+                             SegIterState* out, cudaStream_t s) = 0;
 };
 using SegFactory = SegEngine* (*)();
 struct SegRegistrar {

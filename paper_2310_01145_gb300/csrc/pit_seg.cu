@@ -145,7 +145,29 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
   const int fixed = o.fixed_iters;
   const int limit = fixed > 0 ? fixed : o.max_iter;
   std::vector<SegResult> res(B);
-  for (int k = 1; k <= limit; ++k) {
+  // all means iterations in one cooperative launch (stopping rules and compaction on the
+  // device) where the layout fits one resident wave; otherwise the host-driven loop below
+  bool on_device = false;
+  if (o.scan == 0) {
+    std::vector<SegIterState> ds(B);
+    st = e->run_iterations(B, o, kDivergedDelta, ds.data(), s);
+    if (st == PIT_OK) {
+      on_device = true;
+      for (int i = 0; i < B; ++i) {
+        BatchState& b = bs[i];
+        b.cur = ds[i].cur;
+        b.iters = ds[i].iters;
+        b.active = false;
+        b.converged = ds[i].converged != 0;
+        b.failed = ds[i].failed != 0;
+        b.last_delta = ds[i].last_delta;
+        b.sigma2 = ds[i].sigma2;
+      }
+    } else if (st != PIT_EUNSUPPORTED) {
+      return st;
+    }
+  }
+  for (int k = 1; k <= limit && !on_device; ++k) {
     slots.clear();
     int64_t off = 0;
     for (int i = 0; i < B; ++i) {
