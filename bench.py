@@ -398,6 +398,11 @@ def run_pit(args):
     if rank == 0 and not args.no_extras:
         batched, _ = measure_lv_batch(4096, steps=3, warmup=2, seed=0,
                                       max_iter=args.batch_max_iter, single=32, dev=dev)
+        host_loop, _ = measure_lv_batch(4096, steps=2, warmup=1, seed=0,
+                                        max_iter=args.batch_max_iter, single=0, dev=dev, scan=1)
+        batched["host_loop"] = dict(host_loop, what="the same batch with the host-driven "
+                                                    "iteration loop (one launch per scan phase, "
+                                                    "compaction on the host)")
         serving = measure_serving([100.0, 1000.0], 2.0, 0, 32, dev)
 
     cpu = None
@@ -509,6 +514,10 @@ def measure_lv_batch(instances: int, steps: int, warmup: int, seed: int, max_ite
         work_e2e += float(np.sum(Ns * r.iterations))
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     e2e = reduce_sum(work_e2e, world, dev) / t_e2e
+    if single <= 0:
+        return {"value": value, "converged_only_value": value_conv, "unit": UNIT,
+                "ms_per_batched_solve": ms / steps, "gpu_launches": launches,
+                "converged_fraction": float(np.mean(r.converged))}, prof
     # the same instances one at a time through the single-problem FP64 solver
     sub = probs[:single]
     o64 = pit.make_opts(dtype=torch.float64, max_iter=max_iter, atol_delta=1e-10,

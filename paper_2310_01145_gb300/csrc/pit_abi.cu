@@ -447,6 +447,26 @@ int check_opts(const pit_opts* in, pit_opts& o) {
   return PIT_OK;
 }
 
+int grid_step_data(const double* t, int64_t N, int q, double* out, int* SW) {
+  const int Q1 = q + 1;
+  *SW = 2 * Q1 + 3;
+  double Phib[64], sqb[64], Td[8], Tprev[8];
+  for (int64_t n = 0; n <= N; ++n) {
+    const double h = n == 0 ? t[1] - t[0] : t[n] - t[n - 1];
+    if (prior_blocks(q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
+    double* g = out + n * *SW;
+    for (int i = 0; i < Q1; ++i) {
+      g[i] = Td[i];
+      g[Q1 + i] = n == 0 ? 1.0 : Tprev[i] / Td[i];
+      Tprev[i] = Td[i];
+    }
+    g[2 * Q1] = h / q;
+    g[2 * Q1 + 1] = Td[0];
+    g[2 * Q1 + 2] = 1.0 / Td[1];
+  }
+  return PIT_OK;
+}
+
 // ---- pit_linearize kernel ---------------------------------------------------------------------
 template <typename T, int DD>
 __global__ void k_linearize(OdeParams<T> ode, int64_t N, int Q1, double t0, double h,
@@ -772,7 +792,13 @@ static int32_t solve_grid_common(const pit_ode* ode, const double* t, int64_t N,
   a.pb.N = N;
   st = check_opts(opts, a.opts);
   if (st != PIT_OK) return st;
-  SolveFn fn = find_dense_solver(a.opts.dtype);
+  // small states (d <= 3, layout variants 0 and 1, exact or approximate Jacobian in the dense
+  // d x d form) run on the lane-group kernels with per-point preconditioning; everything else,
+  // and variant 3, on the large-state kernels
+  SolveFn fn = nullptr;
+  if (a.pb.d <= 3 && (a.opts.variant == 0 || a.opts.variant == 1))
+    fn = find_solver(a.opts.dtype, a.pb.d, q, a.opts.variant);
+  if (!fn) fn = find_dense_solver(a.opts.dtype);
   if (!fn) {
     set_error("large-state kernels not compiled for this dtype");
     return PIT_EUNSUPPORTED;

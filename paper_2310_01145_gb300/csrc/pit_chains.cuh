@@ -39,13 +39,16 @@ __device__ __forceinline__ void load_forcing(const typename C::GR& g,
 }
 
 // Raw per-step inputs (loaded one step ahead to hide their latency).  SEG: also the point's
-// instance code (instance id, or ~id at the instance's n = 0).
-template <class C, bool SEG = false>
+// instance code (instance id, or ~id at the instance's n = 0).  GRID: also the transition scale
+// of the step into point n and its h_n / q (non-uniform grids).
+template <class C, bool SEG = false, bool GRID = false>
 struct StepIn {
   using T = typename C::Tp;
   T y[C::DD];  // solution components of lin_n (original coordinates, for the Jacobian)
   T r[C::DD];  // residual r_n
   T u[C::RL];  // forcing u_{n-1}, this lane's rows
+  T sc[C::Q1];  // GRID: T(h_{n-1}) / T(h_n)
+  T hq;         // GRID: h_n / q
   int code;
   __device__ __forceinline__ void load(const typename C::GR& g, const IeksParams<T>& p,
                                        const T* __restrict__ Yv, const T* __restrict__ R,
@@ -57,6 +60,11 @@ struct StepIn {
     }
     load_forcing<C>(g, U, n - 1, u);
     code = SEG ? p.seg.inst_of[n] : 0;
+    if constexpr (GRID) {
+#pragma unroll
+      for (int j = 0; j < C::Q1; ++j) sc[j] = p.gst[n * p.SW + C::Q1 + j];
+      hq = gp_hq(p, n);
+    }
   }
   __device__ __forceinline__ void jacobian(const OdeParams<T>& ode, T hq, int lin_mode,
                                            T (&Ft)[C::DD][C::DD]) const {
@@ -117,7 +125,7 @@ constexpr int kJBatch = PIT_JBATCH;  // leaves whose information rows are folded
 // C = 0), the others from the neutral element.  Output: one filter item per chain, with C and J
 // lower-triangular.
 // ---------------------------------------------------------------------------------------------
-template <class C, bool SEG = false>
+template <class C, bool SEG = false, bool GRID = false>
 __device__ __forceinline__ void filter_reduce_chain(
     const typename C::GR& g, const IeksParams<typename C::Tp>& p,
     const typename C::Tp* __restrict__ U, const typename C::Tp* __restrict__ R,
@@ -128,6 +136,13 @@ __device__ __forceinline__ void filter_reduce_chain(
   constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
   LaneConst<C> lc;
   lc.init(g, p);
+  T phibase[RL][C::Q1];
+  if constexpr (GRID) {
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int j = 0; j < C::Q1; ++j) phibase[l][j] = lc.phirow[l][j];
+  }
 
   T A[RL][D], b[RL], sC[RL][W], eta[RL], sJ[1][RL][D];
   const T* d0c = first_d0<C, SEG>(p, d0);
@@ -154,7 +169,7 @@ __device__ __forceinline__ void filter_reduce_chain(
   int nbuf = 0;
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
-  StepIn<C, SEG> cur, nxt;
+  StepIn<C, SEG, GRID> cur, nxt;
   if (n0 <= n1) cur.load(g, p, Yv, R, U, n0);
   for (int64_t n = n0; n <= n1; ++n) {
     if (n + 1 <= n1) nxt.load(g, p, Yv, R, U, n + 1);
@@ -185,7 +200,8 @@ __device__ __forceinline__ void filter_reduce_chain(
       if (cur.code != mdl.id) mdl.select(p, cur.code);
     }
     T Ft[DD][DD], rr[DD], uf[RL];
-    cur.jacobian(mdl.params(p), mdl.scale(p), p.lin_mode, Ft);
+    if constexpr (GRID) lc.scale_step(phibase, cur.sc);
+    cur.jacobian(mdl.params(p), GRID ? cur.hq : mdl.scale(p), p.lin_mode, Ft);
 #pragma unroll
     for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll
@@ -297,7 +313,7 @@ __device__ __forceinline__ void filter_reduce_chain(
   g.sync();
 }
 
-template <class C, bool SEG = false>
+template <class C, bool SEG = false, bool GRID = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
                 const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
@@ -310,7 +326,8 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
   const int grp = threadIdx.x / C::G;
   const int64_t chain = chain_index<C>(grp);
   if (chain >= p.P) return;
-  filter_reduce_chain<C, SEG>(g, p, U, R, Yv, d0, chain, smem + grp * C::SCR, agg + chain * C::FA);
+  filter_reduce_chain<C, SEG, GRID>(g, p, U, R, Yv, d0, chain, smem + grp * C::SCR,
+                                    agg + chain * C::FA);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -322,7 +339,7 @@ k_filter_reduce(const IeksParams<typename C::Tp> p, const typename C::Tp* __rest
 // Accumulates the calibration sum sum_n ||sqrtS_n^-1 nu_n||^2 in FP64.
 // LOCAL_LIN: the sequential EKS; linearise at the predicted mean (plain model, no increment).
 // ---------------------------------------------------------------------------------------------
-template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false>
+template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false, bool GRID = false>
 __device__ __forceinline__ void filter_down_chain(
     const typename C::GR& g, const IeksParams<typename C::Tp>& p,
     const typename C::Tp* __restrict__ U, const typename C::Tp* __restrict__ R,
@@ -333,8 +350,16 @@ __device__ __forceinline__ void filter_down_chain(
   using T = typename C::Tp;
   using GR = typename C::GR;
   constexpr int D = C::D, DD = C::DD, W = C::W, RL = C::RL, LDM = C::LDM;
+  static_assert(!(GRID && LOCAL_LIN), "the sequential EKS runs on uniform grids");
   LaneConst<C> lc;
   lc.init(g, p);
+  T phibase[RL][C::Q1];
+  if constexpr (GRID) {
+#pragma unroll
+    for (int l = 0; l < RL; ++l)
+#pragma unroll
+      for (int j = 0; j < C::Q1; ++j) phibase[l][j] = lc.phirow[l][j];
+  }
 
   // filter state (m, sqrtP) with sqrtP kept D wide (zero-padded)
   T m[RL], sP[RL][D];
@@ -453,7 +478,7 @@ __device__ __forceinline__ void filter_down_chain(
 
   const int64_t n0 = chain * p.L + 1;
   const int64_t n1 = min(chain * p.L + p.L, p.N);
-  StepIn<C, SEG> cur, nxt;
+  StepIn<C, SEG, GRID> cur, nxt;
   if (!LOCAL_LIN && n0 <= n1) cur.load(g, p, Yv, R, U, n0);
   // One Kalman step n.  NE = number of columns of sqrtP in use: D for a prefix that comes from
   // the tree (a full triangular factor), W = D - d after any update (rank D - d).
@@ -483,8 +508,9 @@ __device__ __forceinline__ void filter_down_chain(
       }
     }
     T Ft[DD][DD], rr[DD], uf[RL];
+    if constexpr (GRID) lc.scale_step(phibase, cur.sc);
     if constexpr (!LOCAL_LIN) {
-      cur.jacobian(mdl.params(p), mdl.scale(p), p.lin_mode, Ft);
+      cur.jacobian(mdl.params(p), GRID ? cur.hq : mdl.scale(p), p.lin_mode, Ft);
 #pragma unroll
       for (int k = 0; k < DD; ++k) rr[k] = cur.r[k];
 #pragma unroll
@@ -601,7 +627,7 @@ __device__ __forceinline__ void filter_down_chain(
   g.sync();
 }
 
-template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false>
+template <class C, bool WITH_L, bool LOCAL_LIN, bool SEG = false, bool GRID = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ U,
               const typename C::Tp* __restrict__ R, const typename C::Tp* __restrict__ Yv,
@@ -617,7 +643,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   const int grp = threadIdx.x / C::G;
   const int64_t chain = chain_index<C>(grp);
   if (chain >= p.P) return;
-  filter_down_chain<C, WITH_L, LOCAL_LIN, SEG>(g, p, U, R, Yv, d0, fprefix + chain * C::FA, Es,
+  filter_down_chain<C, WITH_L, LOCAL_LIN, SEG, GRID>(g, p, U, R, Yv, d0, fprefix + chain * C::FA, Es,
                                                gs, Ls, sagg + chain * C::SA, scal, chain,
                                                smem + grp * C::SCR);
 }
@@ -630,7 +656,7 @@ k_filter_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
 // the covariance pass writes the outputs in original coordinates.  lin == nullptr means a zero
 // trajectory (the sequential EKS).
 // ---------------------------------------------------------------------------------------------
-template <class C, bool WITH_L, bool SEG = false>
+template <class C, bool WITH_L, bool SEG = false, bool GRID = false>
 __device__ __forceinline__ void smooth_down_chain(
     const typename C::GR& g, const IeksParams<typename C::Tp>& p,
     const typename C::Tp* __restrict__ Es, const typename C::Tp* __restrict__ gs,
@@ -781,6 +807,12 @@ __device__ __forceinline__ void smooth_down_chain(
         }
       }
     }
+    if constexpr (GRID) {
+      // per-point preconditioner of a non-uniform grid
+#pragma unroll
+      for (int l = 0; l < RL; ++l) Trow[l] = gp_T(p, n, rr[l] % C::Q1);
+      T0 = gp_T0(p, n);
+    }
     const int64_t on = SEG ? n - soff : n;  // index within the output arrays
     publish_vec(g, m, scr + C::VEC0);
     if constexpr (WITH_L) publish<GR, D, LDM>(g, sPs, scr + C::MAT0);
@@ -844,7 +876,7 @@ __device__ __forceinline__ void smooth_down_chain(
   g.sync();
 }
 
-template <class C, bool WITH_L, bool SEG = false>
+template <class C, bool WITH_L, bool SEG = false, bool GRID = false>
 __global__ void __launch_bounds__(kThreads, ChainOcc<C>::value)
 k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restrict__ Es,
               const typename C::Tp* __restrict__ gs, const typename C::Tp* __restrict__ Ls,
@@ -861,7 +893,7 @@ k_smooth_down(const IeksParams<typename C::Tp> p, const typename C::Tp* __restri
   const int grp = threadIdx.x / C::G;
   const int64_t chain = chain_index<C>(grp);
   if (chain >= p.P) return;
-  smooth_down_chain<C, WITH_L, SEG>(g, p, Es, gs, Ls, sprefix + chain * C::SA, lin, lin_new,
+  smooth_down_chain<C, WITH_L, SEG, GRID>(g, p, Es, gs, Ls, sprefix + chain * C::SA, lin, lin_new,
                                     mean_out, cov_out, scal, chain, smem + grp * C::SCR);
 }
 // ---------------------------------------------------------------------------------------------

@@ -91,6 +91,10 @@ int check_opts(const pit_opts* in, pit_opts& o);
 int prior_blocks(int q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,
                  double* Tdiag);
 int taylor_init(const Problem& pb, double* mu0);
+// Per-point data of a non-uniform grid t[0..N] for IWP(q) with per-step preconditioning: SW =
+// 2 (q+1) + 3 values per point n, [T(h_n) | T(h_{n-1}) / T(h_n) | h_n / q | T_0(h_n) |
+// 1 / T_1(h_n)], h_n = t_n - t_{n-1} (h_0 = h_1).
+int grid_step_data(const double* t, int64_t N, int q, double* out, int* SW);
 
 // Per-configuration entry points (defined in the pit_inst_*.cu files).
 using SolveFn = int (*)(const SolveArgs&, size_t* ws_query, bool eks);

@@ -108,6 +108,15 @@ struct IeksParams {
   int lin_mode;     // Jacobian: 0 exact (EK1), 1 diagonal (DiagonalEK1), 2 zero (EK0)
   int want_sigma;   // accumulate the quasi-MLE diffusion sum in this pass
   int fused;        // host only: iterations run as single cooperative launches
+  // Non-uniform grid (null on a uniform grid): per grid point n = 0..N, SW = 2 Q1 + 3 values
+  // [T(h_n) (Q1) | T(h_{n-1}) / T(h_n) (Q1) | h_n / q | T_0(h_n) | 1 / T_1(h_n)], h_n the step
+  // into t_n (h_0 = h_1); FP64 (gsd) and the arithmetic type (gst).  In coordinates
+  // x_n = T(h_n) xbar_n the step into t_n is xbar_n = Phibar diag(T(h_{n-1}) / T(h_n)) xbar_{n-1}
+  // + w, w ~ N(0, Qbar) (Section 2.4's step-free Phibar, Qbar), and the observation rows of
+  // point n are scaled by 1 / T_1(h_n).
+  const double* gsd;
+  const T* gst;
+  int SW;
   int sigma_pool;   // segmented: > 0 pools the diffusion sums of instances 0..sigma_pool-1
                     // (the components of one decoupled problem) into one sigma-hat
   double sqbd[kMaxQ1 * kMaxQ1];   // sqrt(Qbar) in FP64 (objective value)
@@ -189,6 +198,40 @@ struct Cfg {
   using GR = Grp<T, D, G_, RL_>;
 };
 
+// Per-point grid data (GRID kernels; the constants of IeksParams on a uniform grid).
+template <typename T>
+__device__ __forceinline__ T gp_T(const IeksParams<T>& p, int64_t n, int i) {
+  return p.gst[n * p.SW + i];
+}
+template <typename T>
+__device__ __forceinline__ T gp_scale(const IeksParams<T>& p, int64_t n, int i) {
+  return p.gst[n * p.SW + (p.SW - 3) / 2 + i];
+}
+template <typename T>
+__device__ __forceinline__ T gp_hq(const IeksParams<T>& p, int64_t n) {
+  return p.gst[n * p.SW + p.SW - 3];
+}
+template <typename T>
+__device__ __forceinline__ T gp_T0(const IeksParams<T>& p, int64_t n) {
+  return p.gst[n * p.SW + p.SW - 2];
+}
+template <typename T>
+__device__ __forceinline__ double gp_T0d(const IeksParams<T>& p, int64_t n) {
+  return p.gsd[n * p.SW + p.SW - 2];
+}
+template <typename T>
+__device__ __forceinline__ double gp_T1invd(const IeksParams<T>& p, int64_t n) {
+  return p.gsd[n * p.SW + p.SW - 1];
+}
+template <typename T>
+__device__ __forceinline__ double gp_scaled(const IeksParams<T>& p, int64_t n, int i) {
+  return p.gsd[n * p.SW + (p.SW - 3) / 2 + i];
+}
+template <typename T>
+__device__ __forceinline__ double gp_Td(const IeksParams<T>& p, int64_t n, int i) {
+  return p.gsd[n * p.SW + i];
+}
+
 // Per-lane constant rows of Phibar and sqrt(Qbar) (I_d (x) blocks).
 template <class C>
 struct LaneConst {
@@ -196,6 +239,14 @@ struct LaneConst {
   T phirow[C::RL][C::Q1];  // Phibar1[r % Q1][j], j = 0..Q1-1 (row of the block)
   T sqrow[C::RL][C::D];    // row r of I_d (x) sqrt(Qbar1)
   int blk[C::RL];          // first row of r's block
+  // non-uniform grid: the transition of the step into point n is Phibar diag(scale_n); the
+  // unscaled rows are kept in base
+  __device__ __forceinline__ void scale_step(const T (&base)[C::RL][C::Q1], const T (&sc)[C::Q1]) {
+#pragma unroll
+    for (int l = 0; l < C::RL; ++l)
+#pragma unroll
+      for (int j = 0; j < C::Q1; ++j) phirow[l][j] = base[l][j] * sc[j];
+  }
   __device__ __forceinline__ void init(const typename C::GR& g, const IeksParams<T>& p) {
 #pragma unroll
     for (int l = 0; l < C::RL; ++l) {

@@ -18,7 +18,7 @@ namespace pit {
 // ---- small elementwise kernels ---------------------------------------------------------------
 // Initial linearisation trajectory (preconditioned, trajectory number type V): the constant
 // mu0 of Algorithm 2, or a caller-provided warm start in original coordinates.
-template <class C>
+template <class C, bool GRID = false>
 __global__ void k_init_traj(const IeksParams<typename C::Tp> p,
                             const typename C::Tp* __restrict__ init,
                             typename TrajType<typename C::Tp>::type* __restrict__ lin) {
@@ -27,7 +27,14 @@ __global__ void k_init_traj(const IeksParams<typename C::Tp> p,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % C::D);
-    const double x = init ? static_cast<double>(init[i]) / p.Tdiagd[r % C::Q1] : p.mu0d[r];
+    double x;
+    if constexpr (GRID) {
+      // original coordinates (mu0 was preconditioned with T(h_0)), then the point's T(h_n)
+      const double orig = init ? static_cast<double>(init[i]) : p.mu0d[r] * p.Tdiagd[r % C::Q1];
+      x = orig / gp_Td(p, i / C::D, r % C::Q1);
+    } else {
+      x = init ? static_cast<double>(init[i]) / p.Tdiagd[r % C::Q1] : p.mu0d[r];
+    }
     lin[i] = v_from_double<V>(x);
   }
 }
@@ -52,7 +59,7 @@ struct ResTile {
 };
 
 
-template <class C>
+template <class C, bool GRID = false>
 __global__ void __launch_bounds__(ResTile<C>::size)
 k_residuals(const IeksParams<typename C::Tp> p,
             const typename TrajType<typename C::Tp>::type* __restrict__ lin,
@@ -90,14 +97,19 @@ k_residuals(const IeksParams<typename C::Tp> p,
       V x[D];
 #pragma unroll
       for (int r = 0; r < D; ++r) bits_to(s_lin[t * SV + r], x[r]);
+      double sc[Q1];  // GRID: scale of the step into point n + 1
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) sc[i] = (GRID && t < usteps) ? gp_scaled(p, n0 + t + 1, i) : 1.0;
       if (t < usteps) {
 #pragma unroll
         for (int k = 0; k < DD; ++k) {
 #pragma unroll
           for (int i = 0; i < Q1; ++i) {
-            V acc = x[k * Q1 + i];
+            V acc = GRID ? x[k * Q1 + i] * sc[i] : x[k * Q1 + i];
 #pragma unroll
-            for (int j = i + 1; j < Q1; ++j) acc = acc + x[k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+            for (int j = i + 1; j < Q1; ++j)
+              acc = acc + x[k * Q1 + j] * (GRID ? static_cast<double>(p.phib[i * kMaxQ1 + j]) * sc[j]
+                                                : static_cast<double>(p.phib[i * kMaxQ1 + j]));
             V next;
             bits_to(s_lin[(t + 1) * SV + k * Q1 + i], next);
             acc = acc - next;
@@ -106,13 +118,15 @@ k_residuals(const IeksParams<typename C::Tp> p,
         }
       }
       V y[DD], f[DD];
+      const V t0n = GRID ? v_from_double<V>(gp_T0d(p, n0 + t)) : T0v;
+      const V t1n = GRID ? v_from_double<V>(gp_T1invd(p, n0 + t)) : T1iv;
 #pragma unroll
-      for (int k = 0; k < DD; ++k) y[k] = T0v * x[k * Q1];
+      for (int k = 0; k < DD; ++k) y[k] = t0n * x[k * Q1];
       ode_f_v<V, DD>(oc, y, f);
 #pragma unroll
       for (int k = 0; k < DD; ++k) {
         s_y[t * SR + k] = v_to_T<T>(y[k]);
-        s_r[t * SR + k] = v_to_T<T>(f[k] * T1iv - x[k * Q1 + 1]);
+        s_r[t * SR + k] = v_to_T<T>(f[k] * t1n - x[k * Q1 + 1]);
       }
       if (n0 + t == 0) {
 #pragma unroll
@@ -207,7 +221,7 @@ __global__ void k_coarse_init(const IeksParams<typename C::Tp> p,
   }
 }
 
-template <class C>
+template <class C, bool GRID = false>
 __global__ void k_export_mean(const IeksParams<typename C::Tp> p,
                               const typename TrajType<typename C::Tp>::type* __restrict__ lin,
                               typename C::Tp* __restrict__ mean) {
@@ -215,7 +229,8 @@ __global__ void k_export_mean(const IeksParams<typename C::Tp> p,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int r = static_cast<int>(i % C::D);
-    mean[i] = p.Tdiag[r % C::Q1] * v_to_T<typename C::Tp>(lin[i]);
+    const typename C::Tp tr = GRID ? gp_T(p, i / C::D, r % C::Q1) : p.Tdiag[r % C::Q1];
+    mean[i] = tr * v_to_T<typename C::Tp>(lin[i]);
   }
 }
 
@@ -493,7 +508,7 @@ struct SolverImpl {
     p.N = pb.N;
     p.lin_mode = a.opts.linearization;
     p.want_sigma = 1;
-    const int64_t cap = (allow_fused && a.opts.scan == 0) ? fused_capacity() : 0;
+    const int64_t cap = (allow_fused && a.opts.scan == 0 && !a.grid) ? fused_capacity() : 0;
     if (a.opts.chain_len > 0) {
       p.L = a.opts.chain_len;
     } else if (cap > 0) {
@@ -506,7 +521,9 @@ struct SolverImpl {
     p.fused = (cap > 0 && p.P <= cap) ? 1 : 0;
     p.want_cov = want_cov;
     p.calibrate = a.opts.calibrate;
-    const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
+    // uniform grid: its step; non-uniform: the first step (T at t_0 preconditions mu0), the
+    // per-point data come from grid_step_data
+    const double h = a.grid ? a.grid[1] - a.grid[0] : (pb.t1 - pb.t0) / static_cast<double>(pb.N);
     double Phib[64], sqb[64], Td[8];
     if (prior_blocks(pb.q, h, nullptr, nullptr, Phib, sqb, Td) != PIT_OK) return PIT_EINVAL;
     for (int i = 0; i < Q1; ++i) {
@@ -554,6 +571,9 @@ struct SolverImpl {
     T *Es, *gs, *Ls, *fagg, *fup, *sagg, *sup;
     SolveScalars* scal;
     ScalBlock* sblock;
+    // non-uniform grid: per-point data (FP64 and arithmetic type)
+    double* gsd;
+    T* gst;
     // single-launch iterations: cross-block scan values and flags
     T *xf, *xs;
     unsigned* xflags;  // 2 x NB
@@ -599,6 +619,8 @@ struct SolverImpl {
     b.sup = cv.take<T>(sup_bytes / sizeof(T) + 1);
     b.sblock = cv.take<ScalBlock>(1);
     b.scal = b.sblock ? &b.sblock->s : nullptr;
+    b.gsd = a.grid ? cv.take<double>(N1 * (2 * Q1 + 3)) : nullptr;
+    b.gst = a.grid ? cv.take<T>(N1 * (2 * Q1 + 3)) : nullptr;
     b.xNB = 0;
     b.xK = 0;
     b.xf = b.xs = nullptr;
@@ -631,16 +653,18 @@ struct SolverImpl {
   }
 
   // Residuals of the increment model at trajectory `lin` (once per iteration).
+  template <bool GRID = false>
   static int residuals(const IeksParams<T>& p, const Buffers& b, const V* lin, cudaStream_t s) {
-    PIT_LAUNCH(KC_RESIDUALS, s, 
-               k_residuals<C><<<elem_grid(p.N + 1, ResTile<C>::size), ResTile<C>::size, 0, s>>>(p, lin, b.U, b.R, b.Yv, b.d0););
+    PIT_LAUNCH(KC_RESIDUALS, s,
+               k_residuals<C, GRID><<<elem_grid(p.N + 1, ResTile<C>::size), ResTile<C>::size, 0, s>>>(
+                   p, lin, b.U, b.R, b.Yv, b.d0););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
 
   // One filter pass + smoother pass at trajectory `lin` (Algorithm 1 in the linearised model);
   // needs residuals(lin) to have run.
-  template <bool WITH_L>
+  template <bool WITH_L, bool GRID = false>
   static int pass(const IeksParams<T>& p_in, const Buffers& b, const V* lin, V* lin_out,
                   T* mean_out, T* cov_out, cudaStream_t s) {
     // the diffusion sum is needed by the pass that reports it: the covariance pass, or every
@@ -651,17 +675,18 @@ struct SolverImpl {
     const size_t sm = chain_smem();
     PIT_CUDA_TRY(cudaMemsetAsync(b.scal, 0, sizeof(SolveScalars), s));
     PIT_LAUNCH(KC_FILTER_REDUCE, s, 
-               k_filter_reduce<C><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg););
+               k_filter_reduce<C, false, GRID><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0,
+                                                                          b.fagg););
     int st = Tree<CT, true, false, false, true>::run(b.fagg, p.P, b.fup, false, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_FILTER_DOWN, s, 
-               k_filter_down<C, WITH_L, false><<<grid, kThreads, sm, s>>>(p, b.U, b.R, b.Yv, b.d0, b.fagg,
-                                                               b.Es, b.gs, b.Ls, b.sagg, b.scal););
+               k_filter_down<C, WITH_L, false, false, GRID><<<grid, kThreads, sm, s>>>(
+                   p, b.U, b.R, b.Yv, b.d0, b.fagg, b.Es, b.gs, b.Ls, b.sagg, b.scal););
     st = Tree<CT, false, WITH_L, true>::run(b.sagg, p.P, b.sup, true, s);
     if (st != PIT_OK) return st;
     PIT_LAUNCH(KC_SMOOTH_DOWN, s, 
-               k_smooth_down<C, WITH_L><<<grid, kThreads, sm, s>>>(p, b.Es, b.gs, b.Ls, b.sagg, lin,
-                                                        lin_out, mean_out, cov_out, b.scal););
+               k_smooth_down<C, WITH_L, false, GRID><<<grid, kThreads, sm, s>>>(
+                   p, b.Es, b.gs, b.Ls, b.sagg, lin, lin_out, mean_out, cov_out, b.scal););
     PIT_CUDA_TRY(cudaGetLastError());
     return PIT_OK;
   }
@@ -737,6 +762,22 @@ struct SolverImpl {
     return PIT_OK;
   }
 
+  // kernels of non-uniform grids
+  static int set_smem_attrs_grid() {
+    const int sm = static_cast<int>(chain_smem());
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_reduce<C, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, false, false, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_filter_down<C, true, false, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, false, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    PIT_CUDA_TRY(cudaFuncSetAttribute(k_smooth_down<C, true, false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return PIT_OK;
+  }
+
   // kernels of the segmented (batched) solve
   static int set_smem_attrs_seg() {
     const int sm = static_cast<int>(chain_smem());
@@ -755,6 +796,12 @@ struct SolverImpl {
 
   static int run(const SolveArgs& a, size_t* wsq, bool eks) {
     const bool want_cov = a.opts.want_cov != 0;
+    if (a.grid && (eks || a.opts.init_coarse > 0 || a.opts.objective ||
+                   a.opts.atol_objective > 0 || a.opts.rtol_objective > 0)) {
+      set_error("non-uniform grids support neither the sequential EKS, coarse initialisation nor "
+                "the objective value");
+      return PIT_EUNSUPPORTED;
+    }
     IeksParams<T> p;
     int st = fill_params(a, p, want_cov ? 1 : 0, !eks);
     if (st != PIT_OK) return st;
@@ -791,6 +838,24 @@ struct SolverImpl {
     PIT_CUDA_TRY(cudaMemsetAsync(&b.sblock->status, 0, 2 * sizeof(unsigned), s));
     if (p.fused)
       PIT_CUDA_TRY(cudaMemsetAsync(b.xflags, 0, (2 * b.xNB + 1) * sizeof(unsigned), s));
+    if (a.grid) {
+      // per-point preconditioner and transition scales of the non-uniform grid
+      st = set_smem_attrs_grid();
+      if (st != PIT_OK) return st;
+      int SW = 0;
+      std::vector<double> gs(static_cast<size_t>(p.N + 1) * (2 * Q1 + 3));
+      if (grid_step_data(a.grid, p.N, Q1 - 1, gs.data(), &SW) != PIT_OK) return PIT_EINVAL;
+      std::vector<T> gt(gs.size());
+      for (size_t i = 0; i < gs.size(); ++i) gt[i] = static_cast<T>(gs[i]);
+      PIT_CUDA_TRY(cudaMemcpyAsync(b.gsd, gs.data(), sizeof(double) * gs.size(),
+                                   cudaMemcpyHostToDevice, s));
+      PIT_CUDA_TRY(cudaMemcpyAsync(b.gst, gt.data(), sizeof(T) * gt.size(),
+                                   cudaMemcpyHostToDevice, s));
+      PIT_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+      p.gsd = b.gsd;
+      p.gst = b.gst;
+      p.SW = SW;
+    }
 
     if (eks) {
       // sequential EKS: one chain, local linearisation at the predicted mean, plain model
@@ -845,8 +910,14 @@ struct SolverImpl {
                      p, b.coarse_mean, static_cast<int64_t>(a.opts.init_coarse),
                      a.pb.t1 - a.pb.t0, b.linA););
     } else {
-      PIT_LAUNCH(KC_INIT, s,
-                 k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj), b.linA););
+      if (p.gsd)
+        PIT_LAUNCH(KC_INIT, s,
+                   k_init_traj<C, true><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj),
+                                                          b.linA););
+      else
+        PIT_LAUNCH(KC_INIT, s,
+                   k_init_traj<C><<<eg, 256, 0, s>>>(p, static_cast<const T*>(a.init_traj),
+                                                    b.linA););
     }
     PIT_CUDA_TRY(cudaGetLastError());
     V* cur = b.linA;  // linearisation trajectory of the current iteration
@@ -872,6 +943,10 @@ struct SolverImpl {
     while (k < limit) {
       if (p.fused) {
         st = fused_pass<false>(p, b, cur, nxt, nullptr, nullptr, ++epoch, 0, s);
+      } else if (p.gsd) {
+        st = residuals<true>(p, b, cur, s);
+        if (st != PIT_OK) return st;
+        st = pass<false, true>(p, b, cur, nxt, nullptr, nullptr, s);
       } else {
         st = residuals(p, b, cur, s);
         if (st != PIT_OK) return st;
@@ -920,11 +995,14 @@ struct SolverImpl {
     // reproduces the same means.
     if (want_cov) {
       st = p.fused ? fused_pass<true>(p, b, cur, nullptr, mean, cov, ++epoch, 1, s)
+           : p.gsd ? pass<true, true>(p, b, cur, nullptr, mean, cov, s)
                    : pass<true>(p, b, cur, nullptr, mean, cov, s);
       if (st != PIT_OK) return st;
     } else {
-      PIT_LAUNCH(KC_EXPORT, s, 
-                 k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean););
+      if (p.gsd)
+        PIT_LAUNCH(KC_EXPORT, s, k_export_mean<C, true><<<eg, 256, 0, s>>>(p, nxt, mean););
+      else
+        PIT_LAUNCH(KC_EXPORT, s, k_export_mean<C><<<eg, 256, 0, s>>>(p, nxt, mean););
     }
     PIT_CUDA_TRY(cudaGetLastError());
     ScalBlock hb2;
