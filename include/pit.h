@@ -196,6 +196,13 @@ int32_t pit_init_state(const pit_ode* ode, int32_t q, const double* y0, double* 
  * more than 32 parameters (the affine family beyond d = 5; pit_solve linearises it itself). */
 int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
                       const void* traj, void* H, void* dvec, void* stream);
+/* pit_linearize with an approximate Jacobian (Section 3.2.1, remark on approximate Jacobians):
+ * F_y is replaced by its diagonal (PIT_LIN_DIAGONAL_EK1) or by zero (PIT_LIN_EK0) in both H_n and
+ * d_n; PIT_LIN_EK1 is pit_linearize.  Other arguments, layouts and errors as pit_linearize, plus
+ * PIT_EINVAL for an unknown linearization. */
+int32_t pit_linearize_approx(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
+                             int32_t linearization, const void* traj, void* H, void* dvec,
+                             void* stream);
 
 /* Bytes of device workspace pit_filter_scan needs for N elements of dimension D. */
 int32_t pit_filter_scan_workspace_size(int64_t N, int32_t D, int32_t dtype, size_t* bytes);

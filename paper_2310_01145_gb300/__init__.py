@@ -102,6 +102,8 @@ SIGNATURES = {
     "pit_prior": (_I32, [_I32, _D, _DP, _DP, _DP, _DP, _DP]),
     "pit_init_state": (_I32, [ctypes.POINTER(_Ode), _I32, _DP, _DP]),
     "pit_linearize": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _I32, _P, _P, _P, _P]),
+    "pit_linearize_approx": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _I32, _I32,
+                                    _P, _P, _P, _P]),
     "pit_filter_scan_workspace_size": (_I32, [_I64, _I32, _I32, ctypes.POINTER(_SZ)]),
     "pit_filter_scan": (_I32, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "pit_smooth_scan_workspace_size": (_I32, [_I64, _I32, _I32, _I32, ctypes.POINTER(_SZ)]),
@@ -281,16 +283,26 @@ def pit_init_state(ode: Ode, q: int, y0) -> np.ndarray:
     return mu0
 
 
-def pit_linearize(ode: Ode, t0: float, t1: float, N: int, q: int, traj, stream=None):
-    """H (N, d, D) and dvec (N, d) at the device trajectory traj ((N+1, D))."""
+def pit_linearize(ode: Ode, t0: float, t1: float, N: int, q: int, traj, stream=None,
+                  linearization="ek1"):
+    """H (N, d, D) and dvec (N, d) at the device trajectory traj ((N+1, D)); `linearization`
+    picks the exact Jacobian ("ek1"), its diagonal ("diag") or zero ("ek0")."""
     import torch
     code = _dtype_code(traj.dtype)
     D = ode.d * (q + 1)
     H = torch.empty((N, ode.d, D), dtype=traj.dtype, device=traj.device)
     dv = torch.empty((N, ode.d), dtype=traj.dtype, device=traj.device)
     c, gr = ode.c(), _Grid(t0, t1, N)
-    _check(load().pit_linearize(ctypes.byref(c), ctypes.byref(gr), q, code, _tptr(traj.contiguous()),
-                                _tptr(H), _tptr(dv), _stream_ptr(stream)), "pit_linearize")
+    mode = LINEARIZATIONS[linearization] if isinstance(linearization, str) else int(linearization)
+    lib = load()
+    if mode == 0:
+        st = lib.pit_linearize(ctypes.byref(c), ctypes.byref(gr), q, code,
+                               _tptr(traj.contiguous()), _tptr(H), _tptr(dv), _stream_ptr(stream))
+    else:
+        st = lib.pit_linearize_approx(ctypes.byref(c), ctypes.byref(gr), q, code, mode,
+                                      _tptr(traj.contiguous()), _tptr(H), _tptr(dv),
+                                      _stream_ptr(stream))
+    _check(st, "pit_linearize")
     return H, dv
 
 

@@ -470,13 +470,15 @@ int grid_step_data(const double* t, int64_t N, int q, double* out, int* SW) {
 // ---- pit_linearize kernel ---------------------------------------------------------------------
 template <typename T, int DD>
 __global__ void k_linearize(OdeParams<T> ode, int64_t N, int Q1, double t0, double h,
-                            const T* __restrict__ traj, T* __restrict__ H, T* __restrict__ dv) {
+                            int lin_mode, const T* __restrict__ traj, T* __restrict__ H,
+                            T* __restrict__ dv) {
   const int D = DD * Q1;
   for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= N;
        n += (int64_t)gridDim.x * blockDim.x) {
     T y[DD], f[DD], F[DD][DD];
     for (int k = 0; k < DD; ++k) y[k] = traj[n * D + k * Q1];
     ode_eval<T, DD>(ode, y, f, F);
+    approximate_jacobian<T, DD>(lin_mode, F);
     T* Hn = H + (n - 1) * DD * D;
     for (int k = 0; k < DD; ++k) {
       T acc = f[k];
@@ -492,7 +494,7 @@ __global__ void k_linearize(OdeParams<T> ode, int64_t N, int Q1, double t0, doub
 }
 
 template <typename T, int DD>
-static int launch_linearize(const Problem& pb, const void* traj, void* H, void* dv,
+static int launch_linearize(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
                             cudaStream_t s) {
   OdeParams<T> op;
   std::memset(&op, 0, sizeof(op));
@@ -502,7 +504,7 @@ static int launch_linearize(const Problem& pb, const void* traj, void* H, void* 
   const double h = (pb.t1 - pb.t0) / static_cast<double>(pb.N);
   const unsigned grid = static_cast<unsigned>(std::min<int64_t>((pb.N + 255) / 256, int64_t(sm_count()) * 16));
   PIT_LAUNCH(KC_LINEARIZE, s, 
-             k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h,
+             k_linearize<T, DD><<<grid, 256, 0, s>>>(op, pb.N, pb.q + 1, pb.t0, h, lin_mode,
                                            static_cast<const T*>(traj), static_cast<T*>(H),
                                            static_cast<T*>(dv)););
   PIT_CUDA_TRY(cudaGetLastError());
@@ -608,7 +610,17 @@ int32_t pit_init_state(const pit_ode* ode, int32_t q, const double* y0, double* 
 
 int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
                       const void* traj, void* H, void* dvec, void* stream) {
+  return pit_linearize_approx(ode, grid, q, dtype, PIT_LIN_EK1, traj, H, dvec, stream);
+}
+
+int32_t pit_linearize_approx(const pit_ode* ode, const pit_grid* grid, int32_t q, int32_t dtype,
+                             int32_t linearization, const void* traj, void* H, void* dvec,
+                             void* stream) {
   g_err.clear();
+  if (linearization < PIT_LIN_EK1 || linearization > PIT_LIN_EK0) {
+    set_error("pit_linearize_approx: linearization must be EK1, DiagonalEK1 or EK0");
+    return PIT_EINVAL;
+  }
   Problem pb;
   int st = fill_problem(ode, q, nullptr, pb, false);
   if (st != PIT_OK) return st;
@@ -621,15 +633,15 @@ int32_t pit_linearize(const pit_ode* ode, const pit_grid* grid, int32_t q, int32
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool f64 = dtype == PIT_F64;
   switch (pb.d) {
-    case 1: return f64 ? launch_linearize<double, 1>(pb, traj, H, dvec, s)
-                       : launch_linearize<float, 1>(pb, traj, H, dvec, s);
-    case 2: return f64 ? launch_linearize<double, 2>(pb, traj, H, dvec, s)
-                       : launch_linearize<float, 2>(pb, traj, H, dvec, s);
-    case 3: return f64 ? launch_linearize<double, 3>(pb, traj, H, dvec, s)
-                       : launch_linearize<float, 3>(pb, traj, H, dvec, s);
+    case 1: return f64 ? launch_linearize<double, 1>(pb, linearization, traj, H, dvec, s)
+                       : launch_linearize<float, 1>(pb, linearization, traj, H, dvec, s);
+    case 2: return f64 ? launch_linearize<double, 2>(pb, linearization, traj, H, dvec, s)
+                       : launch_linearize<float, 2>(pb, linearization, traj, H, dvec, s);
+    case 3: return f64 ? launch_linearize<double, 3>(pb, linearization, traj, H, dvec, s)
+                       : launch_linearize<float, 3>(pb, linearization, traj, H, dvec, s);
     default:
-      return f64 ? dense_linearize_f64(pb, traj, H, dvec, s)
-                 : dense_linearize_f32(pb, traj, H, dvec, s);
+      return f64 ? dense_linearize_f64(pb, linearization, traj, H, dvec, s)
+                 : dense_linearize_f32(pb, linearization, traj, H, dvec, s);
   }
 }
 

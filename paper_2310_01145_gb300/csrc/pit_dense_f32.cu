@@ -14,7 +14,8 @@ LargeSessionRegistrar reg_session_f32(PIT_F32, make_session_f32);
 size_t large_session_bytes_f32(const Problem& pb, const pit_opts& o) {
   return dn::DenseSession<float>::bytes(pb, o);
 }
-int dense_linearize_f32(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
-  return dn::dense_linearize<float>(pb, traj, H, dv, s);
+int dense_linearize_f32(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
+                        cudaStream_t s) {
+  return dn::dense_linearize<float>(pb, lin_mode, traj, H, dv, s);
 }
 }  // namespace pit

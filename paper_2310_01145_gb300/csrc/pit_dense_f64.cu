@@ -14,7 +14,8 @@ LargeSessionRegistrar reg_session_f64(PIT_F64, make_session_f64);
 size_t large_session_bytes_f64(const Problem& pb, const pit_opts& o) {
   return dn::DenseSession<double>::bytes(pb, o);
 }
-int dense_linearize_f64(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
-  return dn::dense_linearize<double>(pb, traj, H, dv, s);
+int dense_linearize_f64(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
+                        cudaStream_t s) {
+  return dn::dense_linearize<double>(pb, lin_mode, traj, H, dv, s);
 }
 }  // namespace pit

@@ -1773,9 +1773,10 @@ struct DenseScan {
 
 // ---- linearisation for any d (pit_linearize beyond the lane-group families) -------------------
 // H_n = E1 - F_y(E0 traj_n) E0 and d_n = f - F_y y at every n = 1..N (Section 3.2.1), one thread
-// per (n, component); the family's parameters travel in the kernel argument.
+// per (n, component); the family's parameters travel in the kernel argument.  lin_mode replaces
+// F_y by its diagonal (1) or by zero (2), the approximate Jacobians of Section 3.2.1's remark.
 struct LinArgs {
-  int kind, d, Q1, n_params;
+  int kind, d, Q1, n_params, lin_mode;
   double pd[kMaxParams];
 };
 
@@ -1811,7 +1812,8 @@ k_dlinearize(const LinArgs a, int64_t N, const T* __restrict__ traj, T* __restri
     Hr[k * Q1 + 1] = T(1);
     T acc = dense_f<T, T>(a.kind, pd, d, k, [&](int j) { return y[j]; });
     for (int m = 0; m < d; ++m) {
-      const T F = jac_entry<T>(p, y, k, m);
+      const bool keep = a.lin_mode == 0 || (a.lin_mode == 1 && m == k);
+      const T F = keep ? jac_entry<T>(p, y, k, m) : T(0);
       Hr[m * Q1] -= F;
       acc -= F * y[m];
     }
@@ -1820,7 +1822,8 @@ k_dlinearize(const LinArgs a, int64_t N, const T* __restrict__ traj, T* __restri
 }
 
 template <typename T>
-int dense_linearize(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s) {
+int dense_linearize(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
+                    cudaStream_t s) {
   if (pb.n_params > kMaxParams) {
     set_error("pit_linearize: families with more than " + std::to_string(kMaxParams) +
               " parameters (affine beyond d = 5) are linearised inside pit_solve only");
@@ -1831,6 +1834,7 @@ int dense_linearize(const Problem& pb, const void* traj, void* H, void* dv, cuda
   a.d = pb.d;
   a.Q1 = pb.q + 1;
   a.n_params = pb.n_params;
+  a.lin_mode = lin_mode;
   for (int i = 0; i < pb.n_params; ++i) a.pd[i] = pb.params[i];
   const int64_t total = pb.N * pb.d;
   const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 16)));

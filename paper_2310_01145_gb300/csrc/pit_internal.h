@@ -143,8 +143,10 @@ LargeSessionFactory find_large_session(int dtype);
 size_t large_session_bytes(int dtype, const Problem& pb, const pit_opts& o);
 
 // pit_linearize for any d (families with at most 32 parameters).
-int dense_linearize_f32(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);
-int dense_linearize_f64(const Problem& pb, const void* traj, void* H, void* dv, cudaStream_t s);
+int dense_linearize_f32(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
+                        cudaStream_t s);
+int dense_linearize_f64(const Problem& pb, int lin_mode, const void* traj, void* H, void* dv,
+                        cudaStream_t s);
 // Element scans of the large-state kernels (any D <= 256; ScanArgs::D gives D).
 ScanFn find_dense_scan(int dtype, bool filter);
 struct ScanRegistrar {

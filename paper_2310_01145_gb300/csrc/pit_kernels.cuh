@@ -122,18 +122,6 @@ struct IeksParams {
   double sqbd[kMaxQ1 * kMaxQ1];   // sqrt(Qbar) in FP64 (objective value)
 };
 
-// The Jacobian used by the linearisation (Section 3.2.1, remark on approximate Jacobians):
-// exact, its diagonal, or zero.
-template <typename T, int DD>
-__device__ __forceinline__ void approximate_jacobian(int mode, T (&F)[DD][DD]) {
-  if (mode == 0) return;
-#pragma unroll
-  for (int i = 0; i < DD; ++i)
-#pragma unroll
-    for (int j = 0; j < DD; ++j)
-      if (mode == 2 || i != j) F[i][j] = T(0);
-}
-
 // Number type of the linearisation trajectory: FP64 for both solvers.  At fine grids the
 // residuals r_n = (f(y_n) - y'_n) / T_1(h) of the increment model amplify the trajectory's
 // representation error by 1 / T_1(h) (about 1e12 for IWP(3) at h = 2e-5), and the quasi-MLE

@@ -287,4 +287,16 @@ __device__ __forceinline__ T component_jac_diag(int kind, const double* pd, int 
   return T(0);
 }
 
+// The Jacobian used by the linearisation (Section 3.2.1, remark on approximate Jacobians):
+// exact, its diagonal, or zero.
+template <typename T, int DD>
+__device__ __forceinline__ void approximate_jacobian(int mode, T (&F)[DD][DD]) {
+  if (mode == 0) return;
+#pragma unroll
+  for (int i = 0; i < DD; ++i)
+#pragma unroll
+    for (int j = 0; j < DD; ++j)
+      if (mode == 2 || i != j) F[i][j] = T(0);
+}
+
 }  // namespace pit

@@ -195,3 +195,29 @@ def test_decoupled_rejections(pit):
     with pytest.raises(pit.PitError) as ei:
         pit.solve_problem(W.van_der_pol(N=10), dtype=torch.float64, variant=2)  # EK1 + variant 2
     assert ei.value.status == 1
+
+
+# ---- pit_linearize / pit_linearize_approx at the boundary -----------------------------------------
+@pytest.mark.parametrize("mode", ["ek1", "diag", "ek0"])
+@pytest.mark.parametrize("p", [W.fitzhugh_nagumo(N=333, q=3), W.lorenz96(d=8, N=50, q=2)],
+                         ids=["fhn_d2", "lorenz96_d8"])
+def test_linearize_modes_match_oracle(pit, p, mode):
+    """H_n and d_n (Eq. 13 with F_y exact, diagonal or zero) at a random trajectory: the lane
+    kernel (d <= 3) and the large-state kernel (d = 8) against the oracle's linearisation."""
+    rng = np.random.default_rng(7)
+    traj = rng.standard_normal((p.N + 1, p.D))
+    Hs, ds = ieks.linearize_all(p, traj, mode)
+    H, dv = pit.pit_linearize(pit.ode_from_problem(p), p.t0, p.t1, p.N, p.q,
+                              torch.tensor(traj, dtype=torch.float64, device="cuda:0"),
+                              linearization=mode)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(H.cpu().numpy(), np.stack(Hs[1:]), rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(dv.cpu().numpy(), np.stack(ds[1:]), rtol=1e-13, atol=1e-13)
+
+
+def test_linearize_rejects_unknown_mode(pit):
+    p = W.fitzhugh_nagumo(N=10, q=3)
+    traj = torch.zeros((p.N + 1, p.D), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(pit.PitError) as ei:
+        pit.pit_linearize(pit.ode_from_problem(p), p.t0, p.t1, p.N, p.q, traj, linearization=3)
+    assert ei.value.status == 1
