@@ -122,6 +122,11 @@ typedef struct {
                                  (stopping rules and compaction of the active instances on
                                  the device); else as 1.  1: one launch per scan phase with
                                  block-level scan trees, host-driven iteration loop          */
+  int32_t tensor_cores; /* [1]   FP64 large-state solves (variant 3, d > 3 with EK1): 1 = the
+                                 D x D products run on the tcgen05 tensor cores as exact
+                                 products of 7-bit fixed-point digits (FP64 accuracy) when
+                                 D >= 64; 2 = for any D; 0 = on the FP64 pipes.  No effect on
+                                 FP32 solves or on the small-state kernels                    */
 } pit_opts;
 
 /* Linearisation of the vector field (pit_opts.linearization). */
@@ -290,6 +295,29 @@ int32_t pit_solve_grid(const pit_ode* ode, const double* t, int64_t N, int32_t q
  * the wait gave up and set its timeout bit (a flag that nothing sets), PIT_EINVAL for bad
  * arguments.  words[1..2] are overwritten.  Synchronises `stream`. */
 int32_t pit_check_wait(int64_t poll_limit, uint32_t target, void* words, void* stream);
+
+/* Check of the FP64-accurate tensor-core product that the large-state solver uses for its dense
+ * D x D products (Section 3.1.2's operators; the method itself is not in the paper).  One thread
+ * block computes C = alpha op(A) op(B) + beta C in FP64 from 7-bit fixed-point digits of the
+ * operands multiplied on the tcgen05 tensor cores (bf16 digits, exact FP32 accumulation, integer
+ * recombination); the error of an output is below about 2^-52 k max|row of op(A)| max|column of
+ * op(B)|.  op(A) = A (m x k, row-major, row stride lda) or, trans_a = 1, A^T with A k x m;
+ * op(B) = B (k x n, stride ldb) or, trans_b = 1, B^T with B n x k; C m x n, stride ldc.  All
+ * matrices are FP64 device memory owned by the caller; C must not alias A or B; beta == 0 does
+ * not read C.  status: 2 x uint32 device words (overwritten: timeout bit 4, the product whose
+ * wait gave up).  Returns PIT_OK, PIT_ETIMEOUT when a wait for the tensor cores gave up (after 4
+ * s; the outputs are then NaN), PIT_EINVAL for sizes outside 0..4096, trans flags other than 0/1,
+ * leading dimensions below the row lengths or null pointers.  Synchronises `stream`. */
+int32_t pit_check_dgemm_tc(int32_t m, int32_t n, int32_t k, int32_t trans_a, int32_t trans_b,
+                           double alpha, const void* A, int32_t lda, const void* B, int32_t ldb,
+                           double beta, void* C, int32_t ldc, void* status, void* stream);
+
+/* Check of the bounded wait of the tensor-core product (no counterpart in the paper): one block
+ * allocates its tensor memory, waits on an mbarrier that nothing arrives on and frees the tensor
+ * memory.  The wait must give up after wait_ns nanoseconds (0 .. 4e9) and set the timeout bit.
+ * status: 2 x uint32 device words (overwritten).  Returns PIT_ETIMEOUT when it did so,
+ * PIT_EINTERNAL otherwise, PIT_EINVAL for bad arguments.  Synchronises `stream`. */
+int32_t pit_check_tc_wait(int64_t wait_ns, void* status, void* stream);
 
 /* pit_solve for callers that cannot allocate device memory (no counterpart in the paper: this
  * is a deployment convenience).  Serving loops whose device memory budget is fixed at start-up,

@@ -46,7 +46,7 @@ class _Opts(ctypes.Structure):
                 ("variant", ctypes.c_int32), ("linearization", ctypes.c_int32),
                 ("objective", ctypes.c_int32), ("atol_objective", ctypes.c_double),
                 ("rtol_objective", ctypes.c_double), ("init_coarse", ctypes.c_int32),
-                ("scan", ctypes.c_int32)]
+                ("scan", ctypes.c_int32), ("tensor_cores", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -59,7 +59,7 @@ class _Info(ctypes.Structure):
 LINEARIZATIONS = {"ek1": 0, "diag": 1, "diagonal_ek1": 1, "ek0": 2}
 _OPT_KEYS = ("dtype", "max_iter", "fixed_iters", "atol_delta", "rtol_delta", "calibrate",
              "want_cov", "chain_len", "variant", "linearization", "objective", "atol_objective",
-             "rtol_objective", "init_coarse", "scan")
+             "rtol_objective", "init_coarse", "scan", "tensor_cores")
 
 
 class _BatchInfo(ctypes.Structure):
@@ -119,6 +119,9 @@ SIGNATURES = {
     "pit_solve_noalloc": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
                                  ctypes.POINTER(_Opts), _P, _P, _P, ctypes.POINTER(_Info), _P]),
     "pit_check_wait": (_I32, [_I64, ctypes.c_uint32, _P, _P]),
+    "pit_check_dgemm_tc": (_I32, [_I32, _I32, _I32, _I32, _I32, ctypes.c_double, _P, _I32, _P,
+                                  _I32, ctypes.c_double, _P, _I32, _P, _P]),
+    "pit_check_tc_wait": (_I32, [_I64, _P, _P]),
     "pit_eks_workspace_size": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32,
                                       ctypes.POINTER(_Opts), ctypes.POINTER(_SZ)]),
     "pit_eks_sequential": (_I32, [ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
@@ -218,7 +221,7 @@ def pit_opts_default() -> _Opts:
 def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_delta=0.0,
               calibrate=True, want_cov=True, chain_len=0, variant=0, linearization="ek1",
               objective=False, atol_objective=0.0, rtol_objective=0.0,
-              init_coarse=0, scan=0) -> _Opts:
+              init_coarse=0, scan=0, tensor_cores=1) -> _Opts:
     o = pit_opts_default()
     o.max_iter, o.fixed_iters = int(max_iter), int(fixed_iters)
     o.atol_delta, o.rtol_delta = float(atol_delta), float(rtol_delta)
@@ -231,6 +234,7 @@ def make_opts(dtype=PIT_F64, max_iter=20, fixed_iters=0, atol_delta=1e-10, rtol_
     o.atol_objective, o.rtol_objective = float(atol_objective), float(rtol_objective)
     o.init_coarse = int(init_coarse)
     o.scan = int(scan)
+    o.tensor_cores = int(tensor_cores)
     return o
 
 
@@ -398,6 +402,32 @@ def pit_solve(ode: Ode, y0, t0: float, t1: float, N: int, q: int, opts: Optional
     return _solve_like(lib.pit_solve_workspace_size, lib.pit_solve, ode, y0, t0, t1, N, q,
                        opts or make_opts(), init_traj, device, stream, workspace, out,
                        allow_noconv)
+
+
+def pit_check_dgemm_tc(A, B, C, alpha=1.0, beta=0.0, trans_a=False, trans_b=False, stream=None):
+    """C = alpha op(A) op(B) + beta C through the tensor-core digit product (FP64 torch tensors on
+    the device, row-major and contiguous); returns C.  Raises PitError (status PIT_ETIMEOUT when a
+    wait for the tensor cores gave up)."""
+    import torch
+    m, n = C.shape
+    k = A.shape[0] if trans_a else A.shape[1]
+    for t in (A, B, C):
+        assert t.dtype == torch.float64 and t.is_contiguous()
+    status = torch.zeros(2, dtype=torch.int32, device=C.device)
+    _check(load().pit_check_dgemm_tc(m, n, k, int(trans_a), int(trans_b), float(alpha), _tptr(A),
+                                     max(1, A.shape[1]), _tptr(B), max(1, B.shape[1]),
+                                     float(beta), _tptr(C), max(1, C.shape[1]), _tptr(status),
+                                     _stream_ptr(stream)),
+           "pit_check_dgemm_tc")
+    return C
+
+
+def pit_check_tc_wait(wait_ns: int, device="cuda:0", stream=None) -> int:
+    """Bounded wait of the tensor-core product on an mbarrier nothing arrives on; returns the
+    status (PIT_ETIMEOUT: it gave up and set the timeout bit)."""
+    import torch
+    status = torch.zeros(2, dtype=torch.int32, device=device)
+    return int(load().pit_check_tc_wait(int(wait_ns), _tptr(status), _stream_ptr(stream)))
 
 
 def pit_check_wait(poll_limit: int, target: int, words, stream=None) -> int:

@@ -440,7 +440,8 @@ int check_opts(const pit_opts* in, pit_opts& o) {
   if (o.max_iter < 1 || o.fixed_iters < 0 || !(o.atol_delta >= 0) || !(o.rtol_delta >= 0) ||
       (o.dtype != PIT_F32 && o.dtype != PIT_F64) || o.chain_len < 0 || o.chain_len > (1 << 20) ||
       o.variant < 0 || o.variant > 9 || o.linearization < 0 || o.linearization > 2 ||
-      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0) || o.init_coarse < 0 || o.scan < 0 || o.scan > 1) {
+      !(o.atol_objective >= 0) || !(o.rtol_objective >= 0) || o.init_coarse < 0 || o.scan < 0 || o.scan > 1 ||
+      o.tensor_cores < 0 || o.tensor_cores > 2) {
     set_error("invalid pit_opts");
     return PIT_EINVAL;
   }
@@ -586,6 +587,7 @@ void pit_opts_default(pit_opts* o) {
   o->rtol_objective = 0.0;
   o->init_coarse = 0;
   o->scan = 0;
+  o->tensor_cores = 1;
 }
 
 int32_t pit_prior(int32_t q, double h, double* Phi, double* Q, double* Phibar, double* sqrtQbar,

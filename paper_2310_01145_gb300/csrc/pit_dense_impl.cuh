@@ -30,9 +30,12 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "pit_dense.cuh"
 #include "pit_kernels.cuh"
 #include "pit_internal.h"
+#include "pit_tc.cuh"
 
 namespace pit {
 
@@ -82,6 +85,10 @@ struct DenseParams {
   const double* gsd;     // FP64
   const T* gst;          // arithmetic type
   int SW;
+  // FP64 solves: 1 = the D x D products run on the tensor cores as exact digit products
+  // (pit_tc.cuh); tc_status receives the timeout bit of their bounded waits
+  int tc;
+  unsigned* tc_status;
 };
 
 // ---- per-step quantities (uniform grid: the constants) ------------------------------------------
@@ -183,6 +190,49 @@ __device__ __forceinline__ void cta_jacobian(const DenseParams<T>& p, const T* y
   __syncthreads();
 }
 
+// ---- tensor-core products of the FP64 kernels ---------------------------------------------------
+// Products with all three dimensions at least kTcMinDim run as FP64-accurate digit products on
+// the tensor cores when p.tc is set (FP64 solves); the others, and every FP32 product, on the
+// FP64/FP32 pipes (cta_gemm).  Every kernel that reaches dgemm opens a TcScope first.
+constexpr int kTcMinDim = 32;
+
+template <typename T, bool TA, bool TB>
+__device__ __forceinline__ void dgemm(const DenseParams<T>& p, int m, int n, int k, T alpha,
+                                      const T* A, int lda, const T* B, int ldb, T beta, T* C,
+                                      int ldc, T* sm) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (p.tc && m >= kTcMinDim && n >= kTcMinDim && k >= kTcMinDim) {
+      const tc::TcCtx c{reinterpret_cast<unsigned char*>(sm), p.tc_status, tc::kTcWaitNs};
+      tc::cta_dgemm<TA, TB>(c, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+      return;
+    }
+  }
+  cta_gemm<T, TA, TB>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+}
+
+// The tensor-core products for a solve: FP64 only; pit_opts.tensor_cores 1 = when D >= 64,
+// 2 = for any D, 0 = never.
+constexpr int kTcMinD = 64;
+template <typename T>
+inline int use_tensor_cores(int opt, int D) {
+  if (!std::is_same<T, double>::value) return 0;
+  return (opt == 2 || (opt == 1 && D >= kTcMinD)) ? 1 : 0;
+}
+
+// Holds the block's tensor memory for the lifetime of a kernel (FP64 solves with p.tc only).
+// Open it after the kernel's block-uniform early returns; every thread leaves through its end.
+template <typename T>
+struct TcScope {
+  bool on;
+  __device__ explicit TcScope(const DenseParams<T>& p)
+      : on(std::is_same<T, double>::value && p.tc != 0) {
+    if (on) tc::tc_setup();
+  }
+  __device__ ~TcScope() {
+    if (on) tc::tc_teardown();
+  }
+};
+
 // OUT (d x ncol) = Ht X = E1 X - Ft E0 X for X with D rows (row stride ldx).
 template <typename T>
 __device__ __forceinline__ void cta_hx(const DenseParams<T>& p, const T* Ft, const T* X, int ldx,
@@ -194,7 +244,7 @@ __device__ __forceinline__ void cta_hx(const DenseParams<T>& p, const T* Ft, con
   }
   __syncthreads();
   // E0 X = rows 0, Q1, 2 Q1, ... of X: a matrix with row stride Q1 ldx
-  cta_gemm<T, false, false>(d, ncol, d, T(-1), Ft, d, X, Q1 * ldx, T(1), OUT, ldo, sm);
+  dgemm<T, false, false>(p, d, ncol, d, T(-1), Ft, d, X, Q1 * ldx, T(1), OUT, ldo, sm);
 }
 
 // nu = r - Ht x for a state vector x (d values)
@@ -423,6 +473,7 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t chain = blockIdx.x;
   if (chain >= p.P) return;
+  TcScope<T> tc_scope(p);
   const int d = p.d, D = p.D, W = p.W;
   const ChainLayout lay(d, D, p.kJ);
   const int ldw = lay.ldw, ldj = lay.ldj;
@@ -475,7 +526,7 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
     cta_gemv<T, false>(D, d, T(1), K, d, nu, T(1), b);
     // A = A' - K Ht A';  G = sqrtS^-1 Ht A'
     cta_hx<T>(p, Ft, A, D, D, HA, D, sm);
-    cta_gemm<T, false, false>(D, D, d, T(-1), K, d, HA, D, T(1), A, D, sm);
+    dgemm<T, false, false>(p, D, D, d, T(-1), K, d, HA, D, T(1), A, D, sm);
     cta_trsm_left<T>(d, D, Wk, ldw, HA, D, sm);
     cta_solve_small<T>(d, Wk, ldw, nu, znu);
     cta_gemv<T, true>(D, d, T(1), HA, D, znu, T(1), eta);
@@ -553,7 +604,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   cta_set<T>(D, D, X, l2, T(1));
   cta_set<T>(D, D, X + static_cast<size_t>(D) * l2, l2, T(0));
   cta_copy<T>(D, D, Jj, D, X + static_cast<size_t>(D) * l2 + D, l2);
-  cta_gemm<T, true, false>(D, D, D, T(1), Ci, D, Jj, D, T(0), X + D, l2, sm);
+  dgemm<T, true, false>(p, D, D, D, T(1), Ci, D, Jj, D, T(0), X + D, l2, sm);
   cta_lq<T>(X, l2, 2 * D, D, D, 2 * D, sm, p.wsmax);
   const T* X11 = X;
   const T* X21 = X + static_cast<size_t>(D) * l2;
@@ -563,7 +614,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   cta_copy<T>(D, D, Ci, D, M, D);
   cta_trsm_right<T, true>(D, D, X11, l2, M, D, sm);
   cta_set<T>(D, D, Y, D, T(1));
-  cta_gemm<T, false, true>(D, D, D, T(-1), M, D, X21, l2, T(1), Y, D, sm);
+  dgemm<T, false, true>(p, D, D, D, T(-1), M, D, X21, l2, T(1), Y, D, sm);
   // 3. vectors: t = Ci^T eta_j, v = b_i + Ci t, w = Y v, b_new = b_j + Aj w
   cta_gemv<T, true>(D, D, T(1), Ci, D, ej, T(0), tv);
   for (int i = threadIdx.x; i < D; i += NT) vv[i] = bi[i];
@@ -576,13 +627,13 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   cta_gemv<T, false>(D, D, T(1), Aj, D, wv, T(1), ob);
   // 4. C_new = tria([Cj | Aj M])
   cta_copy<T>(D, D, Cj, D, CW, l2);
-  cta_gemm<T, false, false>(D, D, D, T(1), Aj, D, M, D, T(0), CW + D, l2, sm);
+  dgemm<T, false, false>(p, D, D, D, T(1), Aj, D, M, D, T(0), CW + D, l2, sm);
   cta_lq<T>(CW, l2, D, D, D, 2 * D, sm, p.wsmax);
   cta_copy<T>(D, D, CW, l2, out + DD + D, D);
   if (VALUES) return;
   // 5. U = Y Ai, A_new = Aj U; s = Jj^T b_i, u = eta_j - Jj s, eta_new = U^T u + eta_i
-  cta_gemm<T, false, false>(D, D, D, T(1), Y, D, Ai, D, T(0), Um, D, sm);
-  cta_gemm<T, false, false>(D, D, D, T(1), Aj, D, Um, D, T(0), out, D, sm);
+  dgemm<T, false, false>(p, D, D, D, T(1), Y, D, Ai, D, T(0), Um, D, sm);
+  dgemm<T, false, false>(p, D, D, D, T(1), Aj, D, Um, D, T(0), out, D, sm);
   cta_gemv<T, true>(D, D, T(1), Jj, D, bi, T(0), sv);
   for (int i = threadIdx.x; i < D; i += NT) uu[i] = ej[i];
   __syncthreads();
@@ -593,7 +644,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   cta_gemv<T, true>(D, D, T(1), Um, D, uu, T(1), oe);
   // 6. J_new = tria([Ji | Ai^T Xi22])
   cta_copy<T>(D, D, Ji, D, JW, l2);
-  cta_gemm<T, true, false>(D, D, D, T(1), Ai, D, X22, l2, T(0), JW + D, l2, sm);
+  dgemm<T, true, false>(p, D, D, D, T(1), Ai, D, X22, l2, T(0), JW + D, l2, sm);
   cta_lq<T>(JW, l2, D, D, D, 2 * D, sm, p.wsmax);
   cta_copy<T>(D, D, JW, l2, out + 2 * DD + 2 * D, D);
 }
@@ -605,14 +656,14 @@ __device__ void dcombine_s(const DenseParams<T>& p, const T* bl, const T* br, T*
   const int D = p.D;
   const int64_t DD = static_cast<int64_t>(D) * D;
   const TreeLayout tl(D);
-  cta_gemm<T, false, false>(D, D, D, T(1), bl, D, br, D, T(0), out, D, sm);
+  dgemm<T, false, false>(p, D, D, D, T(1), bl, D, br, D, T(0), out, D, sm);
   for (int i = threadIdx.x; i < D; i += NT) out[DD + i] = bl[DD + i];
   __syncthreads();
   cta_gemv<T, false>(D, D, T(1), bl, D, br + DD, T(1), out + DD);
   if (WITH_L) {
     T* LW = scr + tl.CW;
     cta_copy<T>(D, D, bl + DD + D, D, LW, 2 * D);
-    cta_gemm<T, false, false>(D, D, D, T(1), bl, D, br + DD + D, D, T(0), LW + D, 2 * D, sm);
+    dgemm<T, false, false>(p, D, D, D, T(1), bl, D, br + DD + D, D, T(0), LW + D, 2 * D, sm);
     cta_lq<T>(LW, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
     cta_copy<T>(D, D, LW, 2 * D, out + DD + D, D);
   } else {
@@ -659,6 +710,7 @@ k_dtree_level(const DenseParams<T> p, T* __restrict__ items, int64_t s, T* __res
   const int64_t k = blockIdx.x;
   const int64_t i = (k + 1) * 2 * s - 1, j = i - s;
   if (j - s + 1 >= P) return;  // both subtrees are padding
+  TcScope<T> tc_scope(p);
   T* scr = scratch + k * p.chain_elems;
   const TreeLayout tl(D);
   T* res = scr + tl.out;
@@ -703,6 +755,7 @@ k_dtree_seq(const DenseParams<T> p, T* __restrict__ items, int64_t G, int64_t ng
             T* __restrict__ pre, T* __restrict__ tot, T* __restrict__ scratch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  TcScope<T> tc_scope(p);
   const int D = p.D;
   const int64_t P = p.P;
   const int64_t sz = FILTER ? fitem(D) : sitem(D);
@@ -755,6 +808,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t chain = blockIdx.x;
   if (chain >= p.P) return;
+  TcScope<T> tc_scope(p);
   const int d = p.d, D = p.D, W = p.W;
   const int64_t DD = static_cast<int64_t>(D) * D;
   const ChainLayout lay(d, D, p.kJ);
@@ -804,10 +858,10 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
   auto fold = [&](const T* Enew, const T* gnew, const T* Lnew) {
     cta_gemv<T, false>(D, D, T(1), Ea, D, gnew, T(1), xa);
     if (WITH_L) {
-      cta_gemm<T, false, false>(D, D, D, T(1), Ea, D, Lnew, D, T(0), LaW + D, 2 * D, sm);
+      dgemm<T, false, false>(p, D, D, D, T(1), Ea, D, Lnew, D, T(0), LaW + D, 2 * D, sm);
       cta_lq<T>(LaW, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
     }
-    cta_gemm<T, false, false>(D, D, D, T(1), Ea, D, Enew, D, T(0), Eb, D, sm);
+    dgemm<T, false, false>(p, D, D, D, T(1), Ea, D, Enew, D, T(0), Eb, D, sm);
     T* t = Ea;
     Ea = Eb;
     Eb = t;
@@ -923,6 +977,7 @@ k_dsmooth(const DenseParams<T> p, const T* __restrict__ Es, const T* __restrict_
   __shared__ int redbad;
   const int64_t chain = blockIdx.x;
   if (chain >= p.P) return;
+  TcScope<T> tc_scope(p);
   const int d = p.d, D = p.D, Q1 = p.Q1;
   const int64_t DD = static_cast<int64_t>(D) * D;
   const ChainLayout lay(d, D, p.kJ);
@@ -954,7 +1009,7 @@ k_dsmooth(const DenseParams<T> p, const T* __restrict__ Es, const T* __restrict_
     __syncthreads();
     cta_gemv<T, false>(D, D, T(1), En, D, m, T(1), mn);
     if (WITH_L) {
-      cta_gemm<T, false, false>(D, D, D, T(1), En, D, Pw, 2 * D, T(0), Pw + D, 2 * D, sm);
+      dgemm<T, false, false>(p, D, D, D, T(1), En, D, Pw, 2 * D, T(0), Pw + D, 2 * D, sm);
       cta_copy<T>(D, D, Ls + n * DD, D, Pw, 2 * D);
       cta_lq<T>(Pw, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
     }
@@ -1052,6 +1107,7 @@ struct DenseSolver {
     T *Es, *gs, *Ls;
     T *fagg, *sagg, *scratch, *seq;
     SolveScalars* scal;
+    unsigned* tcs;   // tensor-core status word (timeout bit), cleared once per solve
     double* pd;
     T* pt;
     double* mu0d;
@@ -1117,6 +1173,7 @@ struct DenseSolver {
     p.P = pb.N / p.L + 1;
     p.n_params = pb.n_params;
     p.wsmax = NB + std::max(p.D, p.kJ * p.d);
+    p.tc = use_tensor_cores<T>(a.opts.tensor_cores, p.D);
     if (p.D > kMaxDenseD || p.wsmax > MAXWS) {
       set_error("large-state solver: D = d (q+1) must be <= " + std::to_string(kMaxDenseD));
       return PIT_EUNSUPPORTED;
@@ -1169,6 +1226,7 @@ struct DenseSolver {
     b.scratch = cv.take<T>(std::max<int64_t>(p.P, P2 / 2) * p.chain_elems);
     b.seq = cv.take<T>(2 * fitem(p.D));
     b.scal = cv.take<SolveScalars>(1);
+    b.tcs = cv.take<unsigned>(4);
     b.pd = cv.take<double>(std::max(1, a.pb.n_params));
     b.pt = cv.take<T>(std::max(1, a.pb.n_params));
     b.mu0d = cv.take<double>(D);
@@ -1185,7 +1243,20 @@ struct DenseSolver {
   }
 
   static size_t smem_bytes(const DenseParams<T>& p) {
-    return lq_smem_elems<T>(p.wsmax) * sizeof(T);
+    return std::max(lq_smem_elems<T>(p.wsmax) * sizeof(T), p.tc ? tc::stage_bytes() : size_t(0));
+  }
+
+  // Reads the tensor-core status word (one small copy; synchronises the stream).
+  static int tc_check(const DenseParams<T>& p, const Buffers& b, cudaStream_t s) {
+    if (!p.tc) return PIT_OK;
+    unsigned w = 0;
+    PIT_CUDA_TRY(cudaMemcpyAsync(&w, b.tcs, sizeof(w), cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (w & tc::kTcTimeoutBit) {
+      set_error("large-state solver: a wait for the tensor cores gave up after 4 s");
+      return PIT_ETIMEOUT;
+    }
+    return PIT_OK;
   }
 
   // The attribute is a per-kernel cap shared by every solve, session and scan in the process,
@@ -1336,6 +1407,8 @@ struct DenseSolver {
     st = set_attrs(sm);
     if (st != PIT_OK) return st;
     cudaStream_t s = a.stream;
+    p.tc_status = b.tcs;
+    PIT_CUDA_TRY(cudaMemsetAsync(b.tcs, 0, 4 * sizeof(unsigned), s));
     // ODE parameters and the exact initial state to the device
     std::vector<T> pt(std::max(1, a.pb.n_params));
     for (int i = 0; i < a.pb.n_params; ++i) pt[i] = static_cast<T>(a.pb.params[i]);
@@ -1387,6 +1460,8 @@ struct DenseSolver {
       PIT_CUDA_TRY(cudaGetLastError());
       PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
       PIT_CUDA_TRY(cudaStreamSynchronize(s));
+      st = tc_check(p, b, s);
+      if (st != PIT_OK) return st;
       info.iterations = 1;
       info.converged = 1;
       info.sigma2 = a.opts.calibrate ? hs.sigma2_sum / (static_cast<double>(p.N) * p.d) : 1.0;
@@ -1422,6 +1497,8 @@ struct DenseSolver {
       if (fixed <= 0) {
         PIT_CUDA_TRY(cudaMemcpyAsync(&hs, b.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
         PIT_CUDA_TRY(cudaStreamSynchronize(s));
+        st = tc_check(p, b, s);
+        if (st != PIT_OK) return st;
         if (hs.flags & 1u) {
           set_error("non-finite value in the smoothing means at iteration " + std::to_string(k));
           return PIT_ENONFINITE;
@@ -1446,6 +1523,8 @@ struct DenseSolver {
     SolveScalars hs2;
     PIT_CUDA_TRY(cudaMemcpyAsync(&hs2, b.scal, sizeof(hs2), cudaMemcpyDeviceToHost, s));
     PIT_CUDA_TRY(cudaStreamSynchronize(s));
+    st = tc_check(p, b, s);
+    if (st != PIT_OK) return st;
     if (fixed > 0 && !want_cov) info.last_delta = hs2.delta_max;
     info.iterations = k;
     info.converged = converged ? 1 : 0;
@@ -1509,6 +1588,7 @@ class DenseSession final : public LargeSession {
     p_.pt = b_.pt;
     p_.mu0d = b_.mu0d;
     p_.mu0o = b_.mu0o;
+    p_.tc_status = &b_.scal->flags;
     const int64_t total = (p_.N + 1) * p_.D;
     PIT_LAUNCH(KC_INIT, s, (k_dinit_traj<T><<<S::elem_grid(total, 256), 256, 0, s>>>(p_, nullptr, b_.linA)));
     PIT_CUDA_TRY(cudaGetLastError());
@@ -1574,6 +1654,7 @@ k_dgen_filter(const DenseParams<T> p, int64_t N, T* __restrict__ A, T* __restric
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t chain = blockIdx.x;
   if (chain >= p.P) return;
+  TcScope<T> tc_scope(p);
   const int D = p.D;
   const int64_t DD = static_cast<int64_t>(D) * D, sz = fitem(D);
   const TreeLayout tl(D);
@@ -1618,6 +1699,7 @@ k_dgen_smooth(const DenseParams<T> p, int64_t N, T* __restrict__ E, T* __restric
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t chain = blockIdx.x;
   if (chain >= p.P) return;
+  TcScope<T> tc_scope(p);
   const int D = p.D;
   const int64_t DD = static_cast<int64_t>(D) * D, sz = sitem(D);
   const TreeLayout tl(D);
