@@ -18,6 +18,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "pit_tc.cuh"
+
 namespace pit {
 namespace dn {
 
@@ -47,6 +51,12 @@ __host__ __device__ constexpr size_t lq_smem_elems(int wsmax) {
          + static_cast<size_t>(NB) * (LqTile<T>::RT + 4)         // (W T)^T
          + static_cast<size_t>(LqTile<T>::RT) * (NB + 1)         // W
          + NB;                                                   // tau
+}
+// Shared memory (bytes) of the LQ with its trailing rows updated on the tensor cores (FP64): the
+// panel's reflections, T, Gram and tau, then the digit staging area at a 128-byte boundary.
+__host__ __device__ constexpr size_t lq_tc_smem_bytes(int wsmax) {
+  return (static_cast<size_t>(NB) * lq_ldv<double>(wsmax) + 2 * NB * (NB + 1) + NB) * 8 + 128 +
+         tc::stage_bytes();   // + 128: the staging area starts at the next 128-byte boundary
 }
 template <typename T>
 __host__ __device__ constexpr size_t gemm_smem_elems() {
@@ -385,17 +395,23 @@ __device__ __forceinline__ T make_reflection(T (&x)[MAXCH], int j, int ws, int l
 // rows < ctri lower-triangular in columns [0, ctri).  The compact panel width
 // kb + (ncols - max(k0 + kb, ctri)) must not exceed MAXWS.
 // sm: lq_smem_elems<T>(wsmax) elements with wsmax >= every panel width of this call.
+// FP64 with tcx: the trailing rows' two products run as exact digit products on the tensor
+// cores (pit_tc.cuh); sm then needs lq_tc_smem_bytes(wsmax) bytes and wbuf (global memory of
+// the block) 2 (rows - 1) NB values.
 template <typename T>
-__device__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* sm, int wsmax) {
+__device__ __noinline__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* sm,
+                                   int wsmax, const tc::TcCtx* tcx = nullptr, T* wbuf = nullptr) {
   constexpr int RT = LqTile<T>::RT;
+  constexpr bool kF64 = std::is_same<T, double>::value;
+  const bool use_tc = kF64 && tcx != nullptr;
   const int ldvmax = lq_ldv<T>(wsmax);
-  T* Vs = sm;                                   // [NB][ldv]
-  T* Xs = Vs + NB * ldvmax;                     // [RT][ldv]
-  T* Tm = Xs + RT * ldvmax;                     // [NB][NB + 1]
-  T* Gm = Tm + NB * (NB + 1);                   // [NB][NB + 1] Gram v_i . v_j (i < j)
-  T* W2t = Gm + NB * (NB + 1);                  // [NB][RT + 4]
-  T* Ws = W2t + NB * (RT + 4);                  // [RT][NB + 1]
-  T* tau = Ws + RT * (NB + 1);                  // [NB]
+  T* Vs = sm;                                           // [NB][ldv]
+  T* Xs = Vs + NB * ldvmax;                             // [RT][ldv] (FP64 pipes only)
+  T* Tm = use_tc ? Xs : Xs + RT * ldvmax;               // [NB][NB + 1]
+  T* Gm = Tm + NB * (NB + 1);                           // [NB][NB + 1] Gram v_i . v_j (i < j)
+  T* W2t = Gm + NB * (NB + 1);                          // [NB][RT + 4] (FP64 pipes only)
+  T* Ws = W2t + NB * (RT + 4);                          // [RT][NB + 1] (FP64 pipes only)
+  T* tau = use_tc ? W2t : Ws + RT * (NB + 1);           // [NB]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tid = threadIdx.x;
 
@@ -513,6 +529,40 @@ __device__ void cta_lq(T* M, int ld, int rows, int rf, int ctri, int ncols, T* s
       }
     }
     __syncthreads();
+
+    if constexpr (kF64) {
+      if (use_tc) {
+        // ---- trailing rows on the tensor cores: W = X V^T, W2 = W T, X <- X - W2 V
+        const int r0 = k0 + kb, R = rows - r0;
+        unsigned char* stage = reinterpret_cast<unsigned char*>(
+            (reinterpret_cast<uintptr_t>(tau + NB) + 127) & ~static_cast<uintptr_t>(127));
+        const tc::TcCtx c{stage, tcx->gstatus, tcx->wait_ns};
+        double* W = wbuf;                                   // [R][NB]
+        double* W2 = wbuf + static_cast<size_t>(R) * NB;   // [R][NB]
+        tc::cta_dgemm_f(
+            c, R, NB, ws,
+            [=](int i, int l) { return M[static_cast<size_t>(r0 + i) * ld + pc.col(l)]; },
+            [=](int l, int j) { return Vs[j * ldv + l]; },
+            [=](int i, int j, double v, bool first) {
+              double* w = W + static_cast<size_t>(i) * NB + j;
+              *w = first ? v : *w + v;
+            });
+        tc::cta_dgemm_f(
+            c, R, NB, NB, [=](int i, int l) { return W[static_cast<size_t>(i) * NB + l]; },
+            [=](int l, int j) { return l <= j ? Tm[l * (NB + 1) + j] : 0.0; },
+            [=](int i, int j, double v, bool first) {
+              double* w = W2 + static_cast<size_t>(i) * NB + j;
+              *w = first ? v : *w + v;
+            });
+        tc::cta_dgemm_f(
+            c, R, ws, NB, [=](int i, int l) { return W2[static_cast<size_t>(i) * NB + l]; },
+            [=](int l, int j) { return Vs[l * ldv + j]; },
+            [=](int i, int j, double v, bool) {
+              M[static_cast<size_t>(r0 + i) * ld + pc.col(j)] -= v;
+            });
+        continue;
+      }
+    }
 
     // ---- trailing rows: X <- X - ((X V) T) V^T on the panel's columns, RT rows at a time
     for (int r0 = k0 + kb; r0 < rows; r0 += RT) {

@@ -89,6 +89,7 @@ struct DenseParams {
   // (pit_tc.cuh); tc_status receives the timeout bit of their bounded waits
   int tc;
   unsigned* tc_status;
+  int64_t wbuf_off;      // tc: offset of the tria's product buffer in a block's scratch
 };
 
 // ---- per-step quantities (uniform grid: the constants) ------------------------------------------
@@ -217,6 +218,21 @@ template <typename T>
 inline int use_tensor_cores(int opt, int D) {
   if (!std::is_same<T, double>::value) return 0;
   return (opt == 2 || (opt == 1 && D >= kTcMinD)) ? 1 : 0;
+}
+
+// tria of Section 3.1.2 (cta_lq) with, for FP64 solves with p.tc, the trailing-row products on
+// the tensor cores (their buffer in the block's scratch area scr).
+template <typename T>
+__device__ __forceinline__ void dlq(const DenseParams<T>& p, T* scr, T* M, int ld, int rows,
+                                    int rf, int ctri, int ncols, T* sm) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (p.tc) {
+      const tc::TcCtx c{nullptr, p.tc_status, tc::kTcWaitNs};
+      cta_lq<T>(M, ld, rows, rf, ctri, ncols, sm, p.wsmax, &c, scr + p.wbuf_off);
+      return;
+    }
+  }
+  cta_lq<T>(M, ld, rows, rf, ctri, ncols, sm, p.wsmax);
 }
 
 // Holds the block's tensor memory for the lifetime of a kernel (FP64 solves with p.tc only).
@@ -513,10 +529,10 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
     T* Pr = Wk + static_cast<size_t>(d) * ldw;  // rows d .. d+D-1
     cta_phi_mat<T>(p, Csq, ldw, W, Pr + D, ldw, sc);
     cta_sqrtq<T>(p, Pr, ldw);
-    cta_lq<T>(Pr, ldw, D, D, D, D + W, sm, p.wsmax);
+    dlq<T>(p, scr, Pr, ldw, D, D, D, D + W, sm);
     // update: Psi = tria([[Ht sqrtC-], [sqrtC-]]), d reflections
     cta_hx<T>(p, Ft, Pr, ldw, D, Wk, ldw, sm);
-    cta_lq<T>(Wk, ldw, d + D, d, 0, D, sm, p.wsmax);
+    dlq<T>(p, scr, Wk, ldw, d + D, d, 0, D, sm);
     // sqrtS = Wk[0:d, 0:d], Psi21 = Pr[:, 0:d], sqrtC = Psi22 = Pr[:, d:D] (= Csq)
     cta_innovation<T>(p, Ft, bp, vec + V_R * D, nu);
     cta_copy<T>(D, d, Pr, ldw, K, d);
@@ -534,7 +550,7 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
     cta_copy_t<T>(d, D, HA, D, Jw + D + slot * d, ldj);
     ++slot;
     if (slot == p.kJ || n == n1) {
-      cta_lq<T>(Jw, ldj, D, D, D, D + slot * d, sm, p.wsmax);
+      dlq<T>(p, scr, Jw, ldj, D, D, D, D + slot * d, sm);
       slot = 0;
     }
   }
@@ -549,7 +565,7 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
     item[2LL * D * D + D + i] = eta[i];
   }
   __syncthreads();
-  if (W > 0) cta_lq<T>(Ci, D, D, W, 0, W, sm, p.wsmax);
+  if (W > 0) dlq<T>(p, scr, Ci, D, D, W, 0, W, sm);
   cta_copy<T>(D, D, Jw, ldj, item + 2LL * D * D + 2 * D, D);
 }
 
@@ -605,11 +621,11 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   cta_set<T>(D, D, X + static_cast<size_t>(D) * l2, l2, T(0));
   cta_copy<T>(D, D, Jj, D, X + static_cast<size_t>(D) * l2 + D, l2);
   dgemm<T, true, false>(p, D, D, D, T(1), Ci, D, Jj, D, T(0), X + D, l2, sm);
-  cta_lq<T>(X, l2, 2 * D, D, D, 2 * D, sm, p.wsmax);
+  dlq<T>(p, scr, X, l2, 2 * D, D, D, 2 * D, sm);
   const T* X11 = X;
   const T* X21 = X + static_cast<size_t>(D) * l2;
   T* X22 = X + static_cast<size_t>(D) * l2 + D;
-  if (!VALUES) cta_lq<T>(X22, l2, D, D, 0, D, sm, p.wsmax);
+  if (!VALUES) dlq<T>(p, scr, X22, l2, D, D, 0, D, sm);
   // 2. M = Ci Xi11^-T; Y = I - M Xi21^T
   cta_copy<T>(D, D, Ci, D, M, D);
   cta_trsm_right<T, true>(D, D, X11, l2, M, D, sm);
@@ -628,7 +644,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   // 4. C_new = tria([Cj | Aj M])
   cta_copy<T>(D, D, Cj, D, CW, l2);
   dgemm<T, false, false>(p, D, D, D, T(1), Aj, D, M, D, T(0), CW + D, l2, sm);
-  cta_lq<T>(CW, l2, D, D, D, 2 * D, sm, p.wsmax);
+  dlq<T>(p, scr, CW, l2, D, D, D, 2 * D, sm);
   cta_copy<T>(D, D, CW, l2, out + DD + D, D);
   if (VALUES) return;
   // 5. U = Y Ai, A_new = Aj U; s = Jj^T b_i, u = eta_j - Jj s, eta_new = U^T u + eta_i
@@ -645,7 +661,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   // 6. J_new = tria([Ji | Ai^T Xi22])
   cta_copy<T>(D, D, Ji, D, JW, l2);
   dgemm<T, true, false>(p, D, D, D, T(1), Ai, D, X22, l2, T(0), JW + D, l2, sm);
-  cta_lq<T>(JW, l2, D, D, D, 2 * D, sm, p.wsmax);
+  dlq<T>(p, scr, JW, l2, D, D, D, 2 * D, sm);
   cta_copy<T>(D, D, JW, l2, out + 2 * DD + 2 * D, D);
 }
 
@@ -664,7 +680,7 @@ __device__ void dcombine_s(const DenseParams<T>& p, const T* bl, const T* br, T*
     T* LW = scr + tl.CW;
     cta_copy<T>(D, D, bl + DD + D, D, LW, 2 * D);
     dgemm<T, false, false>(p, D, D, D, T(1), bl, D, br + DD + D, D, T(0), LW + D, 2 * D, sm);
-    cta_lq<T>(LW, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
+    dlq<T>(p, scr, LW, 2 * D, D, D, D, 2 * D, sm);
     cta_copy<T>(D, D, LW, 2 * D, out + DD + D, D);
   } else {
     for (int e = threadIdx.x; e < D * D; e += NT) out[DD + D + e] = T(0);
@@ -859,7 +875,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
     cta_gemv<T, false>(D, D, T(1), Ea, D, gnew, T(1), xa);
     if (WITH_L) {
       dgemm<T, false, false>(p, D, D, D, T(1), Ea, D, Lnew, D, T(0), LaW + D, 2 * D, sm);
-      cta_lq<T>(LaW, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
+      dlq<T>(p, scr, LaW, 2 * D, D, D, D, 2 * D, sm);
     }
     dgemm<T, false, false>(p, D, D, D, T(1), Ea, D, Enew, D, T(0), Eb, D, sm);
     T* t = Ea;
@@ -878,7 +894,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
     cta_sqrtq<T>(p, Top, ldw);
     cta_set<T>(D, D, Bot, ldw, T(0));
     cta_phi_vec<T>(p, m, LOCAL_LIN ? nullptr : vec + V_U * D, mp, sc);
-    cta_lq<T>(Top, ldw, 2 * D, D, D, D + ne, sm, p.wsmax);
+    dlq<T>(p, scr, Top, ldw, 2 * D, D, D, D + ne, sm);
     // smoothing element n-1: E = Pi21 Pi11^-1, g = m^f - E m-, sqrtL = tria(remainder)
     T* En = Es + (n - 1) * DD;
     T* gn = gs + (n - 1) * D;
@@ -895,7 +911,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
         Ln[e] = c < ne ? Bot[static_cast<size_t>(r) * ldw + D + c] : T(0);
       }
       __syncthreads();
-      cta_lq<T>(Ln, D, D, min(D, ne), 0, ne, sm, p.wsmax);
+      dlq<T>(p, scr, Ln, D, D, min(D, ne), 0, ne, sm);
     }
     fold(En, gn, Ln);
     if (LOCAL_LIN) {
@@ -915,7 +931,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
     }
     // Kalman update of step n with Psi = tria([[Ht Pi11], [Pi11]])
     cta_hx<T>(p, Ft, Top, ldw, D, Wk, ldw, sm);
-    cta_lq<T>(Wk, ldw, d + D, d, 0, D, sm, p.wsmax);
+    dlq<T>(p, scr, Wk, ldw, d + D, d, 0, D, sm);
     cta_innovation<T>(p, Ft, mp, vec + V_R * D, nu);
     cta_copy<T>(D, d, Top, ldw, K, d);
     cta_trsm_right<T, false>(D, d, Wk, ldw, K, d, sm);
@@ -946,7 +962,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
         Ln[e] = c < ne ? psrc[static_cast<size_t>(r) * psld + c] : T(0);
       }
       __syncthreads();
-      cta_lq<T>(Ln, D, D, min(D, ne), 0, ne, sm, p.wsmax);
+      dlq<T>(p, scr, Ln, D, D, min(D, ne), 0, ne, sm);
     }
     fold(En, gn, Ln);
   }
@@ -1011,7 +1027,7 @@ k_dsmooth(const DenseParams<T> p, const T* __restrict__ Es, const T* __restrict_
     if (WITH_L) {
       dgemm<T, false, false>(p, D, D, D, T(1), En, D, Pw, 2 * D, T(0), Pw + D, 2 * D, sm);
       cta_copy<T>(D, D, Ls + n * DD, D, Pw, 2 * D);
-      cta_lq<T>(Pw, 2 * D, D, D, D, 2 * D, sm, p.wsmax);
+      dlq<T>(p, scr, Pw, 2 * D, D, D, D, 2 * D, sm);
     }
     for (int r = threadIdx.x; r < D; r += NT) {
       const V lnew = v_add_small(lin ? lin[n * D + r] : v_from_zero<V>(), mn[r]);
@@ -1204,6 +1220,10 @@ struct DenseSolver {
     const ChainLayout lay(p.d, p.D, p.kJ);
     const TreeLayout tl(p.D);
     p.chain_elems = std::max(lay.total, tl.total);
+    if (p.tc) {   // the tria's W and W T (2 x (2 D) x NB values, the tallest tria has 2 D rows)
+      p.wbuf_off = (p.chain_elems + 31) / 32 * 32;
+      p.chain_elems = p.wbuf_off + 4LL * p.D * NB;
+    }
     return PIT_OK;
   }
 
@@ -1243,7 +1263,7 @@ struct DenseSolver {
   }
 
   static size_t smem_bytes(const DenseParams<T>& p) {
-    return std::max(lq_smem_elems<T>(p.wsmax) * sizeof(T), p.tc ? tc::stage_bytes() : size_t(0));
+    return std::max(lq_smem_elems<T>(p.wsmax) * sizeof(T), p.tc ? lq_tc_smem_bytes(p.wsmax) : size_t(0));
   }
 
   // Reads the tensor-core status word (one small copy; synchronises the stream).
@@ -1262,7 +1282,10 @@ struct DenseSolver {
   // The attribute is a per-kernel cap shared by every solve, session and scan in the process,
   // so it is always raised to the largest panel width the engine accepts: a call with a smaller
   // D must not lower it under another (e.g. a serving class with larger D) still launching.
-  static size_t max_smem_bytes() { return lq_smem_elems<T>(MAXWS) * sizeof(T); }
+  static size_t max_smem_bytes() {
+    return std::max(lq_smem_elems<T>(MAXWS) * sizeof(T),
+                    std::is_same<T, double>::value ? lq_tc_smem_bytes(MAXWS) : size_t(0));
+  }
   static int set_attrs(size_t) {
     const int s = static_cast<int>(max_smem_bytes());
     PIT_CUDA_TRY(cudaFuncSetAttribute(k_dreduce<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, s));

@@ -335,7 +335,7 @@ __device__ __forceinline__ void tc_issue_groups(uint64_t ad0, uint64_t bd0, uint
     tc_issue_groups<G + 1>(ad0, bd0, tm, first);
   }
 }
-__device__ __forceinline__ void tc_issue_chunk(const TcCtx& c, bool first) {
+static __device__ __noinline__ void tc_issue_chunk(const TcCtx c, bool first) {
   const uint32_t sa = smem_u32(c.stage), sb = sa + NDIG * A_SLICE;
   tc_issue_groups<0>(smem_desc(sa, LBO, SBO), smem_desc(sb, LBO, SBO), tc_state().tmem, first);
   mma_commit(&tc_state().bar);
@@ -400,27 +400,21 @@ __device__ __forceinline__ int lane_max_exp(int k, int lane, Get get) {
 __device__ __forceinline__ double tc_nan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
 // ---- block GEMM ------------------------------------------------------------------------------------
-// C[m x n] = alpha op(A)[m x k] op(B)[k x n] + beta C in FP64 accuracy on the tensor cores.
-// op(A)[i][l] = TA ? A[l][i] : A[i][l]; op(B)[l][j] = TB ? B[j][l] : B[l][j].  beta == 0 does
-// not read C; C must not alias A or B.  All NT = 512 threads of the block; inputs visible on
-// entry, outputs visible to the block on return.  A block whose wait gave up writes NaN.
-template <bool TA, bool TB>
-__device__ void cta_dgemm(const TcCtx& c, int m, int n, int k, double alpha, const double* A, int lda,
-                          const double* B, int ldb, double beta, double* C, int ldc) {
+// The product op(A)[m x k] op(B)[k x n] in FP64 accuracy on the tensor cores, with the operands
+// read through getA(i, l) = op(A)[i][l] and getB(l, j) = op(B)[l][j] and the result delivered
+// through put(i, j, v, first): once per output and window of KACC terms, v the window's part of
+// (op(A) op(B))[i][j] and first true for the first window (NaN for every window after a wait
+// gave up; v = 0 once when k == 0).  The getters may read any memory the block can see; put must
+// only write memory the getters do not read.  All NT = 512 threads of the block; inputs
+// visible on entry, everything put wrote visible to the block on return.
+template <class GA, class GB, class PUT>
+__device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA opA, GB opB, PUT put) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NW = 16;
   TcShared& ts = tc_state();
   int* ea = ts.ea;
   int* eb = ts.eb;
-  auto opA = [&](int i, int l) -> double {
-    return TA ? A[static_cast<size_t>(l) * lda + i] : A[static_cast<size_t>(i) * lda + l];
-  };
-  auto opB = [&](int l, int j) -> double {
-    return TB ? B[static_cast<size_t>(j) * ldb + l] : B[static_cast<size_t>(l) * ldb + j];
-  };
   const int nchunks = (k + KC - 1) / KC;
-  const bool alpha_m1 = alpha == -1.0, alpha_1 = alpha == 1.0;
-  const bool beta_0 = beta == 0.0, beta_1 = beta == 1.0;
   // staging roles, in quarter rows of a chunk (4 consecutive K values): A quarters tid and
   // tid + 512 (rows tid / 8 and 64 + tid / 8), B quarter tid (row tid / 8)
   static_assert(TM * KC / 4 == 2 * 512 && TN * KC / 4 == 512, "staging roles assume 512 threads");
@@ -490,33 +484,54 @@ __device__ void cta_dgemm(const TcCtx& c, int m, int n, int k, double alpha, con
             const int jj = ocol + 8 * h + e, j = j0 + jj;
             if (j >= n) continue;
             const int s2 = ea[orow] + eb[jj];
-            double val = (ea[orow] == 2047 || eb[jj] == 2047) ? tc_nan() : tc_scaled(v[e], s2 - 2114 + vx[e]);
-            if (alpha_m1) val = -val;
-            else if (!alpha_1) val *= alpha;
-            double* cp = C + static_cast<size_t>(i) * ldc + j;
-            if (!first_window || beta_1) *cp += val;
-            else if (beta_0) *cp = val;
-            else *cp = fma(beta, *cp, val);
+            const double val = (ea[orow] == 2047 || eb[jj] == 2047) ? tc_nan()
+                                                                    : tc_scaled(v[e], s2 - 2114 + vx[e]);
+            put(i, j, val, first_window);
           }
         }
         tc_fence_before();
       }
       __syncthreads();
-      if (ts.fail != 0 || nchunks == 0) {   // a wait gave up (NaN), or k == 0 (C = beta C)
-        const bool nan = ts.fail != 0;
+      if (ts.fail != 0 || nchunks == 0) {   // a wait gave up (NaN), or k == 0 (a zero product)
+        const double v = ts.fail != 0 ? tc_nan() : 0.0;
         const int i = i0 + orow;
         if (i < m) {
           for (int jj = ocol; jj < ocol + 16; ++jj) {
             const int j = j0 + jj;
-            if (j >= n) continue;
-            double* cp = C + static_cast<size_t>(i) * ldc + j;
-            *cp = nan ? tc_nan() : (beta_0 ? 0.0 : beta * *cp);
+            if (j < n) put(i, j, v, true);
           }
         }
       }
       __syncthreads();   // eb and the staging area are reused by the next column tile
     }
   }
+}
+
+// C[m x n] = alpha op(A)[m x k] op(B)[k x n] + beta C in FP64 accuracy on the tensor cores.
+// op(A)[i][l] = TA ? A[l][i] : A[i][l]; op(B)[l][j] = TB ? B[j][l] : B[l][j].  beta == 0 does
+// not read C; C must not alias A or B.  All NT = 512 threads of the block; inputs visible on
+// entry, outputs visible to the block on return.  A block whose wait gave up writes NaN.
+template <bool TA, bool TB>
+__device__ void cta_dgemm(const TcCtx& c, int m, int n, int k, double alpha, const double* A, int lda,
+                          const double* B, int ldb, double beta, double* C, int ldc) {
+  const bool alpha_m1 = alpha == -1.0, alpha_1 = alpha == 1.0;
+  const bool beta_0 = beta == 0.0, beta_1 = beta == 1.0;
+  cta_dgemm_f(
+      c, m, n, k,
+      [=](int i, int l) -> double {
+        return TA ? A[static_cast<size_t>(l) * lda + i] : A[static_cast<size_t>(i) * lda + l];
+      },
+      [=](int l, int j) -> double {
+        return TB ? B[static_cast<size_t>(j) * ldb + l] : B[static_cast<size_t>(l) * ldb + j];
+      },
+      [=](int i, int j, double v, bool first) {
+        if (alpha_m1) v = -v;
+        else if (!alpha_1) v *= alpha;
+        double* cp = C + static_cast<size_t>(i) * ldc + j;
+        if (!first || beta_1) *cp += v;
+        else if (beta_0) *cp = v;
+        else *cp = fma(beta, *cp, v);
+      });
 }
 
 }  // namespace tc
