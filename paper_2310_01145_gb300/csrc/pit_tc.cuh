@@ -236,6 +236,13 @@ __device__ __forceinline__ void tc_wait(const TcCtx& c) {
 }
 
 // ---- FP64 -> digits ------------------------------------------------------------------------------
+// a * b + c on bf16 pairs (one rounding).
+__device__ __forceinline__ uint32_t bf16x2_fma(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // Biased exponent field of x (0 for zero and subnormals, 2047 for non-finite values).
 __device__ __forceinline__ int bexp(double x) {
   return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7FFu);
@@ -264,25 +271,33 @@ __device__ __forceinline__ void split_store(const double (&x)[NV], int emax, uns
 #pragma unroll
   for (int sl = 0; sl < NDIG; ++sl) {
     const int shift = 7 * (NDIG - 1 - sl);
+    // bf16 pairs 2^(-7 sl) and -128 2^(-7 sl) (exact powers of two)
+    const uint32_t sc = static_cast<uint32_t>(127 - 7 * sl) << 7;
+    const uint32_t nb = 0x8000u | (static_cast<uint32_t>(134 - 7 * sl) << 7);
     uint32_t w[NV / 2];
 #pragma unroll
     for (int q = 0; q < NV / 2; ++q) {
-      uint32_t h[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t dg = static_cast<uint32_t>(mag[2 * q + u] >> shift) & 127u;
-        // dg exactly as an FP32 (2^23 + dg - 2^23), its upper half exactly as a bf16; the bf16
-        // exponent field lowered by 7 sl scales it by 2^(-7 sl)
-        const float f = __uint_as_float(0x4B000000u | dg) - 8388608.0f;
-        const uint32_t hb = dg ? (__float_as_uint(f) >> 16) - static_cast<uint32_t>((7 * sl) << 7) : 0u;
-        h[u] = hb | sgn[2 * q + u];
-      }
-      w[q] = h[0] | (h[1] << 16);
+      const uint32_t d0 = static_cast<uint32_t>(mag[2 * q] >> shift) & 127u;
+      const uint32_t d1 = static_cast<uint32_t>(mag[2 * q + 1] >> shift) & 127u;
+      // 0x4300 | d is the bf16 128 + d exactly; (128 + d) 2^(-7 sl) - 128 2^(-7 sl) is the bf16
+      // d 2^(-7 sl) exactly: two digits per packed fma
+      w[q] = bf16x2_fma(0x43004300u | d0 | (d1 << 16), sc | (sc << 16), nb | (nb << 16)) |
+             sgn[2 * q] | (sgn[2 * q + 1] << 16);
     }
     if constexpr (NV == 8)
       *reinterpret_cast<uint4*>(slice0 + sl * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
     else
       *reinterpret_cast<uint2*>(slice0 + sl * slice_bytes) = make_uint2(w[0], w[1]);
+  }
+}
+
+// Writes zero digits (NDIG slices of 2 NV bytes) for a quarter row outside the operand.
+template <int NV>
+__device__ __forceinline__ void zero_store(unsigned char* slice0, int slice_bytes) {
+#pragma unroll
+  for (int sl = 0; sl < NDIG; ++sl) {
+    if constexpr (NV == 8) *reinterpret_cast<uint4*>(slice0 + sl * slice_bytes) = make_uint4(0, 0, 0, 0);
+    else *reinterpret_cast<uint2*>(slice0 + sl * slice_bytes) = make_uint2(0, 0);
   }
 }
 
@@ -382,21 +397,6 @@ __device__ __forceinline__ double tc_scaled(long long S, int x) {
   return ldexp(v, x);
 }
 
-// Largest biased exponent of a warp's values (all lanes hold the result).
-__device__ __forceinline__ int warp_max_exp(int e) { return __reduce_max_sync(0xffffffffu, e); }
-
-// Largest biased exponent of the k values get(l), l = lane, lane + 32, ... (four loads in flight).
-template <class Get>
-__device__ __forceinline__ int lane_max_exp(int k, int lane, Get get) {
-  int e = 0, l = lane;
-  for (; l + 96 < k; l += 128) {
-    const double v0 = get(l), v1 = get(l + 32), v2 = get(l + 64), v3 = get(l + 96);
-    e = max(max(e, max(bexp(v0), bexp(v1))), max(bexp(v2), bexp(v3)));
-  }
-  for (; l < k; l += 32) e = max(e, bexp(get(l)));
-  return e;
-}
-
 __device__ __forceinline__ double tc_nan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
 // ---- block GEMM ------------------------------------------------------------------------------------
@@ -410,7 +410,6 @@ __device__ __forceinline__ double tc_nan() { return __longlong_as_double(0x7FF80
 template <class GA, class GB, class PUT>
 __device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA opA, GB opB, PUT put) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int NW = 16;
   TcShared& ts = tc_state();
   int* ea = ts.ea;
   int* eb = ts.eb;
@@ -425,19 +424,44 @@ __device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA 
   const int orow = 32 * (warp & 3) + lane, ocol = 16 * (warp >> 2);
   for (int i0 = 0; i0 < m; i0 += TM) {
     __syncthreads();   // ea of the previous row tile no longer read
-    for (int r = warp; r < TM; r += NW) {
-      const int i = i0 + r;
-      int e = i < m ? lane_max_exp(k, lane, [&](int l) { return opA(i, l); }) : 0;
-      e = warp_max_exp(e);
-      if (lane == 0) ea[r] = e;
+    {  // row tid / 4, every fourth K value from tid % 4, eight loads in flight
+      const int r = tid >> 2, part = tid & 3, i = i0 + r;
+      int e = 0;
+      if (i < m) {
+        int l = part;
+        for (; l + 28 < k; l += 32) {
+          double v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = opA(i, l + 4 * u);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) e = max(e, bexp(v[u]));
+        }
+        for (; l < k; l += 4) e = max(e, bexp(opA(i, l)));
+      }
+      e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+      e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+      if (part == 0) ea[r] = e;
     }
     const int ia0 = i0 + ra0, ia1 = i0 + ra1;
     for (int j0 = 0; j0 < n; j0 += TN) {
-      for (int r = warp; r < TN; r += NW) {
-        const int j = j0 + r;
-        int e = j < n ? lane_max_exp(k, lane, [&](int l) { return opB(l, j); }) : 0;
-        e = warp_max_exp(e);
-        if (lane == 0) eb[r] = e;
+      {  // column tid / 8, every eighth K value from tid % 8, eight loads in flight
+        const int r = tid >> 3, part = tid & 7, j = j0 + r;
+        int e = 0;
+        if (j < n) {
+          int l = part;
+          for (; l + 56 < k; l += 64) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = opB(l + 8 * u, j);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e = max(e, bexp(v[u]));
+          }
+          for (; l < k; l += 8) e = max(e, bexp(opB(l, j)));
+        }
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, 4));
+        if (part == 0) eb[r] = e;
       }
       __syncthreads();
       const int jb = j0 + rb;
@@ -454,9 +478,13 @@ __device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA 
       if (nchunks > 0) load(0);
       for (int ch = 0; ch < nchunks; ++ch) {
         const int kc0 = ch * KC;
-        split_store<4>(xa0, ea[ra0], c.stage + core_off(ra0, oq) + qoff, A_SLICE);
-        split_store<4>(xa1, ea[ra1], c.stage + core_off(ra1, oq) + qoff, A_SLICE);
-        split_store<4>(xb, eb[rb], c.stage + NDIG * A_SLICE + core_off(rb, oq) + qoff, B_SLICE);
+        const bool kin = kc0 + 8 * oq + 4 * uq < k;
+        if (ia0 < m && kin) split_store<4>(xa0, ea[ra0], c.stage + core_off(ra0, oq) + qoff, A_SLICE);
+        else zero_store<4>(c.stage + core_off(ra0, oq) + qoff, A_SLICE);
+        if (ia1 < m && kin) split_store<4>(xa1, ea[ra1], c.stage + core_off(ra1, oq) + qoff, A_SLICE);
+        else zero_store<4>(c.stage + core_off(ra1, oq) + qoff, A_SLICE);
+        if (jb < n && kin) split_store<4>(xb, eb[rb], c.stage + NDIG * A_SLICE + core_off(rb, oq) + qoff, B_SLICE);
+        else zero_store<4>(c.stage + NDIG * A_SLICE + core_off(rb, oq) + qoff, B_SLICE);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
