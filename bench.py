@@ -364,11 +364,7 @@ def run_pit(args):
                 "traffic_source": "ncu dram bytes read+written per launch, scaled from N=2^19 "
                                   "by time steps (profiles/); null if the kernels changed",
                 "peak_source": f"nominal: {sms} SMs x 128 FP32 lanes x 2 x {mhz:g} MHz",
-                "algorithmic_flops_per_step": fl,
-            "note": ("FP64 tensor_cores=%d: with 1 or 2 the dense D x D products of these kernels "
-                     "run on the bf16 tensor cores as exact digit products, so the achieved "
-                     "figure counts FP64-equivalent algorithmic flops, part of them executed "
-                     "outside the FP64 pipe" % args.tensor_cores) if f64 else None}
+                "algorithmic_flops_per_step": fl}
     else:
         by = roofline.bytes_per_step("smooth_down", D, prob.d, esz, traj_elem)
         achieved = by * steps_per_launch / (avg_ms / 1e3) / 1e9

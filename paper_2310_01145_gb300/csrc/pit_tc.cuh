@@ -465,13 +465,17 @@ __device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA 
       }
       __syncthreads();
       const int jb = j0 + rb;
+      // a single K chunk: the A digits staged for the first column tile serve every column tile
+      const bool a_resident = nchunks == 1 && j0 > 0;
       double xa0[4], xa1[4], xb[4];
       auto load = [&](int kc0) {
         const int l0 = kc0 + 8 * oq + 4 * uq;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          xa0[e] = (ia0 < m && l0 + e < k) ? opA(ia0, l0 + e) : 0.0;
-          xa1[e] = (ia1 < m && l0 + e < k) ? opA(ia1, l0 + e) : 0.0;
+          if (!a_resident) {
+            xa0[e] = (ia0 < m && l0 + e < k) ? opA(ia0, l0 + e) : 0.0;
+            xa1[e] = (ia1 < m && l0 + e < k) ? opA(ia1, l0 + e) : 0.0;
+          }
           xb[e] = (jb < n && l0 + e < k) ? opB(l0 + e, jb) : 0.0;
         }
       };
@@ -479,10 +483,12 @@ __device__ __noinline__ void cta_dgemm_f(const TcCtx c, int m, int n, int k, GA 
       for (int ch = 0; ch < nchunks; ++ch) {
         const int kc0 = ch * KC;
         const bool kin = kc0 + 8 * oq + 4 * uq < k;
-        if (ia0 < m && kin) split_store<4>(xa0, ea[ra0], c.stage + core_off(ra0, oq) + qoff, A_SLICE);
-        else zero_store<4>(c.stage + core_off(ra0, oq) + qoff, A_SLICE);
-        if (ia1 < m && kin) split_store<4>(xa1, ea[ra1], c.stage + core_off(ra1, oq) + qoff, A_SLICE);
-        else zero_store<4>(c.stage + core_off(ra1, oq) + qoff, A_SLICE);
+        if (!a_resident) {
+          if (ia0 < m && kin) split_store<4>(xa0, ea[ra0], c.stage + core_off(ra0, oq) + qoff, A_SLICE);
+          else zero_store<4>(c.stage + core_off(ra0, oq) + qoff, A_SLICE);
+          if (ia1 < m && kin) split_store<4>(xa1, ea[ra1], c.stage + core_off(ra1, oq) + qoff, A_SLICE);
+          else zero_store<4>(c.stage + core_off(ra1, oq) + qoff, A_SLICE);
+        }
         if (jb < n && kin) split_store<4>(xb, eb[rb], c.stage + NDIG * A_SLICE + core_off(rb, oq) + qoff, B_SLICE);
         else zero_store<4>(c.stage + NDIG * A_SLICE + core_off(rb, oq) + qoff, B_SLICE);
         fence_proxy_async_smem();
