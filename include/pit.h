@@ -328,8 +328,7 @@ int32_t pit_check_tc_wait(int64_t wait_ns, void* status, void* stream);
  * (held by every GPU that loads the library until the process exits).  It allocates nothing
  * itself.  Arguments and outputs are those of pit_solve without workspace/ws_bytes.  The first
  * call on a device looks up the array's address on that device (with that device current) and
- * keeps it for the life of the process; make that first call before any stream capture, and do
- * not reset the device (cudaDeviceReset) after it.  Every call shares the array (the solver
+ * keeps it for the life of the process; do not reset the device (cudaDeviceReset) after it.  Every call shares the array (the solver
  * initialises all scratch it reads, so the previous call's contents are harmless); calls whose
  * device work overlaps race on it and must be serialised by the caller.  Errors: as pit_solve,
  * plus PIT_ENOMEM (with a message giving both sizes) when the problem needs more scratch than
@@ -413,7 +412,8 @@ int32_t pit_solve_batched(int32_t B, const pit_ode* odes, const pit_grid* grids,
  * in the budget and takes one iteration per step on its class's stream.  A request's
  * trajectory stays in device memory from admission to retirement; the host reads back only
  * the per-request change statistics once per step.  Retired requests deliver their smoothing
- * means (original coordinates) and diffusion estimate; covariances are not served.
+ * means (original coordinates) and diffusion estimate, and on request (pit_server_submit_cov)
+ * their square-root covariances.
  * The server allocates its whole device memory budget once, at creation, and never more.
  * Calls on one server must not overlap (they are serialised by a mutex). */
 typedef struct pit_server pit_server;
@@ -461,6 +461,20 @@ int32_t pit_server_create(const pit_server_config* cfg, pit_server** out);
 int32_t pit_server_submit(pit_server* server, const pit_ode* ode, const pit_grid* grid,
                           int32_t q, const double* y0, void* mean_out, uint64_t tag,
                           int64_t* request_id);
+/* pit_server_submit that also delivers square-root covariances.  sqrtcov_out: device,
+ * (N+1) x D x D values of the server's dtype (row-major per grid point, original coordinates,
+ * as pit_solve's sqrtcov), owned by the caller until the request retires.  When the request
+ * retires with PIT_OK or PIT_ENOCONV, the server runs the covariance pass on the class's stream
+ * before delivering the result: one IEKS iteration of Algorithm 1 linearised at the delivered
+ * means, with the covariance recursions and, with calibrate, that pass's quasi-MLE diffusion
+ * (Section 2.4).  This is the pass pit_solve ends with, taken at the final iterate.  The pass's
+ * workspace and scratch means are reserved from the budget at admission, with the request's
+ * trajectory.  Errors: as pit_server_submit, plus PIT_EINVAL for a NULL sqrtcov_out and
+ * PIT_ENOMEM when the pass needs more than the whole budget.  A failing pass (e.g.
+ * PIT_ENONFINITE) becomes the result's status. */
+int32_t pit_server_submit_cov(pit_server* server, const pit_ode* ode, const pit_grid* grid,
+                              int32_t q, const double* y0, void* mean_out, void* sqrtcov_out,
+                              uint64_t tag, int64_t* request_id);
 /* Admit, iterate once, retire (see above); waits for the iteration.  in_flight and queued
  * (host, may be NULL) receive the counts after the step. */
 int32_t pit_server_step(pit_server* server, int32_t* in_flight, int32_t* queued);

@@ -138,6 +138,8 @@ SIGNATURES = {
     "pit_server_create": (_I32, [ctypes.POINTER(_ServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "pit_server_submit": (_I32, [_P, ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP, _P,
                                  ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
+    "pit_server_submit_cov": (_I32, [_P, ctypes.POINTER(_Ode), ctypes.POINTER(_Grid), _I32, _DP,
+                                     _P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
     "pit_server_step": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "pit_server_poll": (_I32, [_P, ctypes.POINTER(_ServerResult), _I32, ctypes.POINTER(_I32)]),
     "pit_server_stats": (_I32, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_I32)]),
@@ -587,24 +589,36 @@ class Server:
         self._h = ctypes.c_void_p()
         _check(lib.pit_server_create(ctypes.byref(cfg), ctypes.byref(self._h)), "pit_server_create")
         self._outs = {}
+        self._covs = {}
 
     @staticmethod
     def clock() -> float:
         return float(load().pit_server_clock())
 
-    def submit(self, problem, tag: int = 0, out=None) -> int:
+    def submit(self, problem, tag: int = 0, out=None, cov: bool = False) -> int:
+        """Queue a request; cov=True also delivers its square-root covariances
+        (pit_server_submit_cov), returned by poll() as "sqrtcov"."""
         import torch
         ode = ode_from_problem(problem)
         c = ode.c()
         gr = _Grid(float(problem.t0), float(problem.t1), int(problem.N))
         y = np.ascontiguousarray(problem.y0, dtype=np.float64)
+        dt = _torch_dtype(self.cfg.dtype)
         if out is None:
-            out = torch.empty((problem.N + 1, problem.D), dtype=_torch_dtype(self.cfg.dtype),
-                              device=self.device)
+            out = torch.empty((problem.N + 1, problem.D), dtype=dt, device=self.device)
         rid = ctypes.c_int64(0)
-        _check(load().pit_server_submit(self._h, ctypes.byref(c), ctypes.byref(gr), int(problem.q),
-                                        _dptr(y), _tptr(out), int(tag), ctypes.byref(rid)),
-               "pit_server_submit")
+        if cov:
+            S = torch.empty((problem.N + 1, problem.D, problem.D), dtype=dt, device=self.device)
+            _check(load().pit_server_submit_cov(self._h, ctypes.byref(c), ctypes.byref(gr),
+                                                int(problem.q), _dptr(y), _tptr(out), _tptr(S),
+                                                int(tag), ctypes.byref(rid)),
+                   "pit_server_submit_cov")
+            self._covs[rid.value] = S
+        else:
+            _check(load().pit_server_submit(self._h, ctypes.byref(c), ctypes.byref(gr),
+                                            int(problem.q), _dptr(y), _tptr(out), int(tag),
+                                            ctypes.byref(rid)),
+                   "pit_server_submit")
         self._outs[rid.value] = out
         return rid.value
 
@@ -624,7 +638,8 @@ class Server:
             out.append({"request_id": r.request_id, "tag": r.tag, "status": r.status,
                         "iterations": r.iterations, "last_delta": r.last_delta,
                         "sigma2": r.sigma2, "t_submit": r.t_submit, "t_admit": r.t_admit,
-                        "t_done": r.t_done, "mean": self._outs.pop(r.request_id)})
+                        "t_done": r.t_done, "mean": self._outs.pop(r.request_id),
+                        "sqrtcov": self._covs.pop(r.request_id, None)})
         return out
 
     def stats(self):
@@ -638,6 +653,7 @@ class Server:
             load().pit_server_destroy(self._h)
             self._h = ctypes.c_void_p()
             self._outs.clear()
+            self._covs.clear()
 
     def __del__(self):
         try:

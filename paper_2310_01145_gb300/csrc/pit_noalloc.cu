@@ -10,8 +10,8 @@
 // The array is kStaticScratchBytes (64 MiB) and, like any __device__ variable, every GPU that
 // loads the library holds it until the process exits.  Its device address is obtained once per
 // device (cudaGetSymbolAddress with that device current) on the first call made on that device
-// and kept for the life of the process: make that first call before any stream capture, and do
-// not reset the device after it (a new context could place the array elsewhere).  All calls
+// and kept for the life of the process; do not reset the device after it (a new context could
+// place the array elsewhere).  All calls
 // share the one array and it keeps the previous call's contents; the solver initialises every
 // scratch region it reads (the trajectory, residuals, aggregates and its scalar accumulators),
 // so nothing has to start at zero.  Calls whose device work overlaps -- on different streams,

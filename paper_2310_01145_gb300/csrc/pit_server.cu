@@ -94,6 +94,11 @@ struct Request {
   double last_delta = 0, sigma2 = 1;
   // large-state request (d > 3): its own session and workspace in the pool
   std::unique_ptr<LargeSession> sess;
+  // square-root covariances on request: the covariance pass's workspace and scratch means,
+  // reserved from the pool at admission
+  void* cov_out = nullptr;
+  size_t cov_ws = 0, cov_bytes = 0, cov_off = 0;
+  bool cov_held = false;
 };
 
 struct ClassState {
@@ -208,6 +213,65 @@ pit_opts session_opts(const pit_server* sv) {
   return o;
 }
 
+// The covariance pass of a retiring request: the request's problem as the C ABI describes it,
+// and options for one IEKS iteration linearised at the delivered means with the covariance
+// recursions (host-driven scan trees: no cooperative launch beside the other classes' kernels).
+pit_ode ode_of(const Problem& pb) {
+  pit_ode o;
+  o.kind = pb.kind;
+  o.d = pb.d;
+  o.params = pb.params;
+  o.n_params = pb.n_params;
+  return o;
+}
+pit_grid grid_of(const Problem& pb) {
+  pit_grid g;
+  g.t0 = pb.t0;
+  g.t1 = pb.t1;
+  g.N = pb.N;
+  return g;
+}
+pit_opts cov_opts(const pit_server* sv) {
+  pit_opts o = session_opts(sv);
+  o.fixed_iters = 1;
+  o.want_cov = 1;
+  o.scan = 1;
+  return o;
+}
+// Workspace of the covariance pass and the bytes reserved for it (+ its scratch means).
+int cov_sizes(const pit_server* sv, const Problem& pb, size_t* ws, size_t* total) {
+  const pit_ode o = ode_of(pb);
+  const pit_grid g = grid_of(pb);
+  const pit_opts op = cov_opts(sv);
+  size_t w = 0;
+  const int st = pit_solve_workspace_size(&o, &g, pb.q, &op, &w);
+  if (st != PIT_OK) return st;
+  const size_t esz = sv->cfg.dtype == PIT_F64 ? 8 : 4;
+  *ws = round256(w);
+  *total = *ws + round256(static_cast<size_t>(pb.N + 1) * pb.d * (pb.q + 1) * esz);
+  return PIT_OK;
+}
+// Runs the covariance pass of a retiring request on `s` (synchronises it) and frees its
+// reservation.  Returns the pass's status.
+int cov_pass(pit_server* sv, Request& r, cudaStream_t s) {
+  const pit_ode o = ode_of(r.pb);
+  const pit_grid g = grid_of(r.pb);
+  const pit_opts op = cov_opts(sv);
+  char* base = static_cast<char*>(sv->pool) + r.cov_off;
+  const int st = pit_solve(&o, &g, r.pb.q, r.pb.y0, &op, r.mean_out, base + r.cov_ws, r.cov_out,
+                           nullptr, base, r.cov_ws, s);
+  sv->alloc.release(r.cov_off, r.cov_bytes);
+  r.cov_held = false;
+  return st;
+}
+// Reserves the covariance pass's memory at admission (false: the pool cannot hold it now).
+bool cov_reserve(pit_server* sv, Request& r) {
+  if (!r.cov_out) return true;
+  if (!sv->alloc.alloc(r.cov_bytes, &r.cov_off)) return false;
+  r.cov_held = true;
+  return true;
+}
+
 // Large-state class: admit (FIFO, by slots, points and pool memory), then enqueue one IEKS
 // iteration of every request in flight on the class stream.
 int begin_large(pit_server* sv, ClassState& cs) {
@@ -220,10 +284,16 @@ int begin_large(pit_server* sv, ClassState& cs) {
     if (bytes == 0) return PIT_EINVAL;
     size_t off = 0;
     if (!sv->alloc.alloc(bytes, &off)) break;
+    if (!cov_reserve(sv, r)) {
+      sv->alloc.release(off, bytes);
+      break;
+    }
     std::unique_ptr<LargeSession> ss(find_large_session(sv->cfg.dtype)());
     const int st = ss->start(r.pb, o, static_cast<char*>(sv->pool) + off, round256(bytes), cs.stream);
     if (st != PIT_OK) {
       sv->alloc.release(off, bytes);
+      if (r.cov_held) sv->alloc.release(r.cov_off, r.cov_bytes);
+      r.cov_held = false;
       return st;
     }
     r.sess = std::move(ss);
@@ -257,6 +327,10 @@ int begin_class(pit_server* sv, ClassState& cs) {
     const size_t tb = round256(cs.eng->traj_bytes(r.pb.N));
     size_t off = 0;
     if (!sv->alloc.alloc(2 * tb, &off)) break;
+    if (!cov_reserve(sv, r)) {
+      sv->alloc.release(off, 2 * tb);
+      break;
+    }
     r.lin_off = off;
     r.lin_bytes = 2 * tb;
     r.slot = cs.free_slots.back();
@@ -316,6 +390,15 @@ int end_large(pit_server* sv, ClassState& cs) {
     const int st = r.sess->export_means(r.mean_out, status == PIT_ENONFINITE, cs.stream);
     if (st != PIT_OK) return st;
     PIT_CUDA_TRY(cudaStreamSynchronize(cs.stream));
+    if (r.cov_held) {
+      if (status != PIT_ENONFINITE) {
+        const int cst = cov_pass(sv, r, cs.stream);
+        if (cst != PIT_OK) status = cst;
+      } else {
+        sv->alloc.release(r.cov_off, r.cov_bytes);
+        r.cov_held = false;
+      }
+    }
     pit_server_result out;
     std::memset(&out, 0, sizeof(out));
     out.request_id = r.id;
@@ -376,6 +459,17 @@ int end_class(pit_server* sv, ClassState& cs) {
     st = cs.eng->export_means(fin.data(), static_cast<int>(fin.size()), cs.stream);
     if (st != PIT_OK) return st;
     PIT_CUDA_TRY(cudaStreamSynchronize(cs.stream));
+    for (size_t k = 0; k < fin_ids.size(); ++k) {
+      Request& r = sv->reqs[fin_ids[k]];
+      if (!r.cov_held) continue;
+      if (fin_status[k] != PIT_ENONFINITE) {
+        const int cst = cov_pass(sv, r, cs.stream);
+        if (cst != PIT_OK) fin_status[k] = cst;
+      } else {
+        sv->alloc.release(r.cov_off, r.cov_bytes);
+        r.cov_held = false;
+      }
+    }
     const double t = now_s();
     for (size_t k = 0; k < fin_ids.size(); ++k) {
       Request& r = sv->reqs[fin_ids[k]];
@@ -401,6 +495,57 @@ int end_class(pit_server* sv, ClassState& cs) {
   return PIT_OK;
 }
 
+}  // namespace
+}  // namespace pit
+
+namespace pit {
+namespace {
+int submit_common(pit_server* sv, const pit_ode* ode, const pit_grid* grid, int32_t q,
+                  const double* y0, void* mean_out, void* cov_out, uint64_t tag,
+                  int64_t* request_id) {
+  std::lock_guard<std::mutex> lk(sv->mu);
+  Request r;
+  int st = fill_problem(ode, q, y0, r.pb, true);
+  if (st == PIT_OK) st = fill_grid(grid, r.pb);
+  if (st != PIT_OK) return st;
+  if (r.pb.N + 1 > sv->cfg.max_points) {
+    set_error("request longer than the server's per-class point capacity");
+    return PIT_EINVAL;
+  }
+  ClassState* cs = nullptr;
+  st = ensure_class(sv, r.pb, &cs);
+  if (st != PIT_OK) return st;
+  if (cs->large) {
+    // a request whose workspace can never fit the budget would block its queue for good
+    const size_t bytes = large_session_bytes(sv->cfg.dtype, r.pb, session_opts(sv));
+    if (bytes == 0) return PIT_EINVAL;
+    if (bytes > sv->cfg.hbm_budget_bytes) {
+      set_error("request needs " + std::to_string(bytes) + " bytes of device memory, more than the "
+                "server's budget of " + std::to_string(sv->cfg.hbm_budget_bytes));
+      return PIT_ENOMEM;
+    }
+  }
+  if (cov_out) {
+    st = cov_sizes(sv, r.pb, &r.cov_ws, &r.cov_bytes);
+    if (st != PIT_OK) return st;
+    if (r.cov_bytes > sv->cfg.hbm_budget_bytes) {
+      set_error("the request's covariance pass needs " + std::to_string(r.cov_bytes) +
+                " bytes of device memory, more than the server's budget");
+      return PIT_ENOMEM;
+    }
+    r.cov_out = cov_out;
+  }
+  r.id = sv->next_id++;
+  r.tag = tag;
+  r.mean_out = mean_out;
+  r.key = class_key(r.pb.kind, r.pb.d, r.pb.q);
+  r.t_submit = now_s();
+  const int64_t rid = r.id;
+  cs->queue.push_back(rid);
+  sv->reqs.emplace(rid, std::move(r));
+  if (request_id) *request_id = rid;
+  return PIT_OK;
+}
 }  // namespace
 }  // namespace pit
 
@@ -452,6 +597,7 @@ int32_t pit_server_create(const pit_server_config* cfg, pit_server** out) {
   return PIT_OK;
 }
 
+
 int32_t pit_server_submit(pit_server* sv, const pit_ode* ode, const pit_grid* grid, int32_t q,
                           const double* y0, void* mean_out, uint64_t tag, int64_t* request_id) {
   set_error("");
@@ -459,38 +605,18 @@ int32_t pit_server_submit(pit_server* sv, const pit_ode* ode, const pit_grid* gr
     set_error("server or mean_out is NULL");
     return PIT_EINVAL;
   }
-  std::lock_guard<std::mutex> lk(sv->mu);
-  Request r;
-  int st = fill_problem(ode, q, y0, r.pb, true);
-  if (st == PIT_OK) st = fill_grid(grid, r.pb);
-  if (st != PIT_OK) return st;
-  if (r.pb.N + 1 > sv->cfg.max_points) {
-    set_error("request longer than the server's per-class point capacity");
+  return submit_common(sv, ode, grid, q, y0, mean_out, nullptr, tag, request_id);
+}
+
+int32_t pit_server_submit_cov(pit_server* sv, const pit_ode* ode, const pit_grid* grid, int32_t q,
+                              const double* y0, void* mean_out, void* sqrtcov_out, uint64_t tag,
+                              int64_t* request_id) {
+  set_error("");
+  if (!sv || !mean_out || !sqrtcov_out) {
+    set_error("server, mean_out or sqrtcov_out is NULL");
     return PIT_EINVAL;
   }
-  ClassState* cs = nullptr;
-  st = ensure_class(sv, r.pb, &cs);
-  if (st != PIT_OK) return st;
-  if (cs->large) {
-    // a request whose workspace can never fit the budget would block its queue for good
-    const size_t bytes = large_session_bytes(sv->cfg.dtype, r.pb, session_opts(sv));
-    if (bytes == 0) return PIT_EINVAL;
-    if (bytes > sv->cfg.hbm_budget_bytes) {
-      set_error("request needs " + std::to_string(bytes) + " bytes of device memory, more than the "
-                "server's budget of " + std::to_string(sv->cfg.hbm_budget_bytes));
-      return PIT_ENOMEM;
-    }
-  }
-  r.id = sv->next_id++;
-  r.tag = tag;
-  r.mean_out = mean_out;
-  r.key = class_key(r.pb.kind, r.pb.d, r.pb.q);
-  r.t_submit = now_s();
-  const int64_t rid = r.id;
-  cs->queue.push_back(rid);
-  sv->reqs.emplace(rid, std::move(r));
-  if (request_id) *request_id = rid;
-  return PIT_OK;
+  return submit_common(sv, ode, grid, q, y0, mean_out, sqrtcov_out, tag, request_id);
 }
 
 int32_t pit_server_step(pit_server* sv, int32_t* in_flight, int32_t* queued) {

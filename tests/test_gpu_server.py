@@ -178,3 +178,54 @@ def test_server_rejects_large_request_beyond_budget(pit):
         sv.submit(W.lorenz96(d=64, N=4096, q=2))
     assert ei.value.status == 2
     sv.close()
+
+
+def _cov(S):
+    return np.einsum("nij,nkj->nik", S, S)
+
+
+def test_server_covariances_fp64(pit):
+    """Requests with square-root covariances (pit_server_submit_cov) next to requests without:
+    the covariance pass at the delivered means gives the covariances of the problem solved alone
+    (pit_solve's last pass linearises one iterate earlier, within the 1e-10 stopping rule), and
+    the oracle's; small-state and large-state classes."""
+    reqs = [W.logistic_paper(N=200, q=2), W.van_der_pol(N=150, q=2), W.lorenz96(d=8, N=40, q=2),
+            W.logistic(N=300, q=1, rate=1.0), W.fitzhugh_nagumo(N=257, q=3)]
+    sv = pit.Server(dtype="f64", max_iter=80, atol_delta=1e-10, rtol_delta=0.0,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16, max_requests=16)
+    ids = [sv.submit(p, tag=i, cov=(i != 3)) for i, p in enumerate(reqs[:3])]
+    sv.step()
+    ids += [sv.submit(p, tag=i + 3, cov=(i + 3 != 3)) for i, p in enumerate(reqs[3:])]
+    done = _drain(sv)
+    assert set(done) == set(ids)
+    for rid in ids:
+        r = done[rid]
+        p = reqs[r["tag"]]
+        assert r["status"] == 0, r
+        if r["tag"] == 3:
+            assert r["sqrtcov"] is None
+            continue
+        single = pit.solve_problem(p, dtype=torch.float64, max_iter=80, atol_delta=1e-10,
+                                   want_cov=True)
+        torch.cuda.synchronize()
+        c_sv = _cov(r["sqrtcov"].cpu().numpy())
+        c_one = _cov(single.sqrtcov.cpu().numpy())
+        assert rel(c_sv, c_one) < 1e-7, r["tag"]
+        assert rel(r["mean"].cpu().numpy(), single.mean.cpu().numpy()) < 1e-10, r["tag"]
+        if r["tag"] in (0, 1):
+            orc = ieks.ieks(p, atol=1e-10, max_iter=80, want_cov=True, calibrate=True)
+            assert rel(c_sv, _cov(orc.sqrtcovs)) < 1e-7, r["tag"]
+    sv.close()
+
+
+def test_server_covariances_fp32_vs_oracle(pit):
+    p = W.fitzhugh_nagumo(N=400, q=3)
+    sv = pit.Server(dtype="f32", max_iter=40, atol_delta=1e-10, rtol_delta=1e-6,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16, max_requests=16)
+    rid = sv.submit(p, cov=True)
+    done = _drain(sv)
+    r = done[rid]
+    assert r["status"] in (0, 4), r       # converged, or max_iter at the FP32 change floor
+    orc = ieks.ieks(p, atol=1e-10, max_iter=60, want_cov=True, calibrate=True)
+    assert rel(_cov(r["sqrtcov"].double().cpu().numpy()), _cov(orc.sqrtcovs)) < 1e-3
+    sv.close()
