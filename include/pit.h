@@ -359,6 +359,8 @@ typedef struct {
   int32_t pad;
   double last_delta;    /* max |change of E0 mean| of its last iteration                    */
   double sigma2;        /* its quasi-MLE diffusion sigma^2 (1 when calibrate == 0)          */
+  double objective;     /* V of its last iterate (Eq. objective-value) when pit_opts.objective
+                           or the objective stopping rule asks for it, else 0               */
 } pit_batch_info;
 
 /* ParaIEKS (Algorithm 2) on B independent initial value problems of one ODE family, dimension
@@ -370,8 +372,10 @@ typedef struct {
  * E = 0 (the boundary elements of Section 3.1.3, Eqs. filtering-elements and
  * smoothing-elements), so no value of one instance depends on another's and every instance gets
  * the result a single solve would give, up to the rounding of a different chain partition.
- * Each instance stops on its own rule (as pit_solve) and then leaves the active set; later
- * iterations run on the remaining instances only.
+ * Each instance stops on its own rule (as pit_solve, including the objective rule of Section
+ * 3.2.2 on its own V when atol_objective or rtol_objective is set) and then leaves the active
+ * set; later iterations run on the remaining instances only.  Evaluating V (objective, or the
+ * objective rule) runs the host-driven iteration loop whatever pit_opts.scan says.
  *   B                  number of instances (>= 1)
  *   odes               host, B entries; all of the same kind and d (parameters may differ)
  *   grids              host, B entries (t0 < t1, N >= 1 each)

@@ -65,7 +65,8 @@ _OPT_KEYS = ("dtype", "max_iter", "fixed_iters", "atol_delta", "rtol_delta", "ca
 class _BatchInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double)]
+                ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("objective", ctypes.c_double)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -508,6 +509,7 @@ class BatchResult:
     last_delta: np.ndarray
     sigma2: np.ndarray
     call_status: int
+    objective: Optional[np.ndarray] = None   # V of each instance's last iterate, when evaluated
 
     def instance(self, i: int):
         """(mean, sqrtcov) views of instance i."""
@@ -554,7 +556,8 @@ def pit_solve_batched(odes: Sequence[Ode], y0s, grids: Sequence[tuple], q: int,
                        np.array([bool(info[i].converged) for i in range(B)]),
                        np.array([info[i].status for i in range(B)]),
                        np.array([info[i].last_delta for i in range(B)]),
-                       np.array([info[i].sigma2 for i in range(B)]), int(st))
+                       np.array([info[i].sigma2 for i in range(B)]), int(st),
+                       np.array([info[i].objective for i in range(B)]))
 
 
 def solve_problems_batched(problems, **kw) -> BatchResult:

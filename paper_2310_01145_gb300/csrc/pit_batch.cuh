@@ -65,6 +65,48 @@ __global__ void k_seg_export(const SegSlot* __restrict__ slots,
   }
 }
 
+// Objective value (Eq. objective-value) of trajectory lin[cur] of every slot (blockIdx.y):
+// out[slot] += 1/2 sum_{n=1..N} || sqrt(Qbar)^-1 (xbar_n - Phibar xbar_{n-1}) ||^2 per dimension
+// block, as k_objective for a single solve (Phibar, Qbar are step-free, shared by the instances).
+template <class C>
+__global__ void __launch_bounds__(256)
+k_seg_objective(const SegSlot* __restrict__ slots, const InstDesc<typename C::Tp>* __restrict__ desc,
+                const IeksParams<typename C::Tp> p, double* __restrict__ out) {
+  using V = typename TrajType<typename C::Tp>::type;
+  constexpr int D = C::D, DD = C::DD, Q1 = C::Q1;
+  const SegSlot sl = slots[blockIdx.y];
+  const InstDesc<typename C::Tp>& d = desc[sl.id];
+  const V* lin = static_cast<const V*>(d.lin[sl.cur]);
+  double acc = 0.0;
+  for (int64_t n = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= d.N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < DD; ++k) {
+      double w[Q1];
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        V a = lin[n * D + k * Q1 + i] - lin[(n - 1) * D + k * Q1 + i];
+#pragma unroll
+        for (int j = i + 1; j < Q1; ++j)
+          a = a - lin[(n - 1) * D + k * Q1 + j] * static_cast<float>(p.phib[i * kMaxQ1 + j]);
+        w[i] = v_to_double(a);
+      }
+#pragma unroll
+      for (int i = 0; i < Q1; ++i) {
+        double z = w[i];
+        // forward substitution with the lower-triangular sqrt(Qbar); z_i kept in w[i]
+#pragma unroll
+        for (int j = 0; j < i; ++j) z -= p.sqbd[i * kMaxQ1 + j] * w[j];
+        w[i] = z / p.sqbd[i * kMaxQ1 + i];
+        acc += w[i] * w[i];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(out + blockIdx.y, 0.5 * acc);
+}
+
 // Decoupled residuals: every instance is component k = id of one d-dimensional problem solved
 // with an approximate (diagonal or zero) Jacobian, laid out at offset k (N + 1); component k's
 // residual reads the whole state y_j(n) = T_0 lin_j(n) of that problem.  Writes U, R as
@@ -379,6 +421,7 @@ class SegEngineImpl final : public SegEngine {
     int* ids;
     int64_t* ctl;
     unsigned* words;  // [0] status, [1] first timeout, [2] grid-barrier arrivals
+    double* obj;      // objective values of the slots of one evaluation
     T *xf, *xs;
     unsigned* xflags;
     int xNB, xK;
@@ -430,6 +473,7 @@ class SegEngineImpl final : public SegEngine {
     b.ids = cv.take<int>(max_inst);
     b.ctl = cv.take<int64_t>(2);
     b.words = cv.take<unsigned>(4);
+    b.obj = cv.take<double>(max_inst);
     b.xNB = persistent_blocks();
     b.xK = 0;
     while ((1 << b.xK) < b.xNB) ++b.xK;
@@ -646,6 +690,18 @@ class SegEngineImpl final : public SegEngine {
     dim3 grid(per_slot_grid(slots, n), static_cast<unsigned>(n));
     PIT_LAUNCH(KC_INIT, s, k_seg_init<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc););
     PIT_CUDA_TRY(cudaGetLastError());
+    return PIT_OK;
+  }
+
+  int objective(const SegSlot* slots, int n, double* out, cudaStream_t s) override {
+    int st = upload_slots(slots, n, s);
+    if (st != PIT_OK) return st;
+    PIT_CUDA_TRY(cudaMemsetAsync(b_.obj, 0, sizeof(double) * n, s));
+    dim3 grid(per_slot_grid(slots, n), static_cast<unsigned>(n));
+    PIT_LAUNCH(KC_EXPORT, s, k_seg_objective<C><<<grid, 256, 0, s>>>(b_.slots, b_.desc, shared_, b_.obj););
+    PIT_CUDA_TRY(cudaGetLastError());
+    PIT_CUDA_TRY(cudaMemcpyAsync(out, b_.obj, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    PIT_CUDA_TRY(cudaStreamSynchronize(s));
     return PIT_OK;
   }
 

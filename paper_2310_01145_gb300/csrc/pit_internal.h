@@ -221,6 +221,9 @@ class SegEngine {
   virtual int use_pinned_staging() = 0;
   // mean <- T lin[1 - cur] (the last means pass), for every slot
   virtual int export_means(const SegSlot* slots, int n, cudaStream_t s) = 0;
+  // Objective value (Eq. objective-value) of trajectory lin[slot.cur] of each slot, into out
+  // (host, n values).  Synchronises s.
+  virtual int objective(const SegSlot* slots, int n, double* out, cudaStream_t s) = 0;
   // All means iterations of instances 0..n-1 (trajectories initialised) in one cooperative
   // launch: per iteration the segmented IEKS pass, every instance's stopping rule and the
   // compaction of the active instances run on the device.  Fills out[0..n-1].  Returns

@@ -53,6 +53,7 @@ struct BatchState {
   bool failed = false;
   double last_delta = 0.0;
   double sigma2 = 1.0;
+  double objective = 0.0;   // V of the last iterate (Eq. objective-value), when evaluated
 };
 
 int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, const double* y0,
@@ -145,10 +146,20 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
   const int fixed = o.fixed_iters;
   const int limit = fixed > 0 ? fixed : o.max_iter;
   std::vector<SegResult> res(B);
+  // objective value V (Eq. objective-value) per instance: evaluated when requested or used by
+  // the second stopping rule of Section 3.2.2 (host-driven loop only)
+  const bool obj_rule = o.atol_objective > 0 || o.rtol_objective > 0;
+  const bool want_obj = obj_rule || o.objective != 0;
+  std::vector<double> vals(B);
+  if (want_obj) {
+    st = e->objective(slots.data(), B, vals.data(), s);
+    if (st != PIT_OK) return st;
+    for (int i = 0; i < B; ++i) bs[i].objective = vals[i];
+  }
   // all means iterations in one cooperative launch (stopping rules and compaction on the
   // device) where the layout fits one resident wave; otherwise the host-driven loop below
   bool on_device = false;
-  if (o.scan == 0) {
+  if (o.scan == 0 && !want_obj) {
     std::vector<SegIterState> ds(B);
     st = e->run_iterations(B, o, kDivergedDelta, ds.data(), s);
     if (st == PIT_OK) {
@@ -179,10 +190,22 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
     const int n = static_cast<int>(slots.size());
     st = e->pass(slots.data(), n, false, o.calibrate, res.data(), s);
     if (st != PIT_OK) return st;
+    if (want_obj) {   // V of the new iterates lin[1 - cur]
+      std::vector<SegSlot> nxt(slots);
+      for (SegSlot& x : nxt) x.cur ^= 1;
+      st = e->objective(nxt.data(), n, vals.data(), s);
+      if (st != PIT_OK) return st;
+    }
     for (int j = 0; j < n; ++j) {
       const int i = slots[j].id;
       BatchState& b = bs[i];
       const SegResult& r = res[j];
+      bool obj_stop = false;
+      if (want_obj) {
+        obj_stop = obj_rule && std::fabs(vals[j] - b.objective) <=
+                                   o.atol_objective + o.rtol_objective * std::fabs(vals[j]);
+        b.objective = vals[j];
+      }
       b.iters = k;
       b.last_delta = r.delta_max;
       b.sigma2 = o.calibrate ? r.sigma2_sum / (static_cast<double>(pbs[i].N) * pbs[i].d) : 1.0;
@@ -196,7 +219,7 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
         } else {
           b.cur ^= 1;
         }
-      } else if (r.delta_max <= o.atol_delta + o.rtol_delta * r.y_max) {
+      } else if (r.delta_max <= o.atol_delta + o.rtol_delta * r.y_max || obj_stop) {
         b.active = false;
         b.converged = true;
       } else if (k == limit) {
@@ -244,6 +267,7 @@ int batched(int32_t B, const pit_ode* odes, const pit_grid* grids, int32_t q, co
       info[i].pad = 0;
       info[i].last_delta = b.last_delta;
       info[i].sigma2 = b.sigma2;
+      info[i].objective = want_obj ? b.objective : 0.0;
     }
   }
   if (anyfail) {

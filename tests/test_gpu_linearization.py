@@ -221,3 +221,32 @@ def test_linearize_rejects_unknown_mode(pit):
     with pytest.raises(pit.PitError) as ei:
         pit.pit_linearize(pit.ode_from_problem(p), p.t0, p.t1, p.N, p.q, traj, linearization=3)
     assert ei.value.status == 1
+
+
+# ---- objective value and its stopping rule in batched solves ----------------------------------------
+def test_batched_objective_values_and_rule_match_oracle(pit):
+    """Each instance of a batched solve evaluates its own V (Eq. objective-value) and stops on its
+    own objective rule (change rule off): iteration counts, V of the last iterate and the means
+    agree with the oracle solving each instance alone."""
+    probs = [W.logistic_paper(N=100, q=2), W.logistic(N=150, q=2, rate=1.0),
+             W.logistic(N=60, q=2, y0=0.3, rate=2.0), W.logistic(N=220, q=2, y0=0.05)]
+    res = pit.solve_problems_batched(probs, dtype=torch.float64, max_iter=40, atol_delta=0.0,
+                                     atol_objective=1e-9, rtol_objective=1e-6, want_cov=False,
+                                     allow_noconv=False)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, atol=0.0, max_iter=40, obj_atol=1e-9, obj_rtol=1e-6, want_cov=False,
+                        calibrate=True)
+        assert res.iterations[i] == orc.iterations < 40, i
+        assert res.objective[i] == pytest.approx(orc.objectives[-1], rel=1e-9), i
+        assert rel(res.instance(i)[0].cpu().numpy(), orc.means) < 1e-10, i
+
+
+def test_batched_objective_recorded_fixed_iterations(pit):
+    probs = [W.lotka_volterra(alpha=a, N=n, q=2, t1=2.0) for a, n in ((1.5, 120), (1.3, 77))]
+    res = pit.solve_problems_batched(probs, dtype=torch.float64, fixed_iters=3, want_cov=False,
+                                     objective=True)
+    torch.cuda.synchronize()
+    for i, p in enumerate(probs):
+        orc = ieks.ieks(p, fixed_iters=3, want_cov=False, calibrate=True, record_objective=True)
+        assert res.objective[i] == pytest.approx(orc.objectives[-1], rel=1e-9), i
