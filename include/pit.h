@@ -435,6 +435,9 @@ typedef struct {
   size_t hbm_budget_bytes;  /* [8 GiB] device memory the server allocates at creation: the
                                classes' workspaces and the requests' trajectories (2 (N+1) D
                                values each, 8 bytes per value in FP32, 16 in FP64 rounded)     */
+  double atol_objective;    /* [0]     objective rule of Sec. 3.2.2 per request (classes with
+                               d <= 3): also stop when |V(k) - V(k-1)| <= atol_objective +  */
+  double rtol_objective;    /* [0]     rtol_objective |V(k)|; enabled when either is > 0     */
 } pit_server_config;
 
 typedef struct {
@@ -447,6 +450,8 @@ typedef struct {
   double t_submit;          /* pit_server_clock() at submission, admission and retirement   */
   double t_admit;
   double t_done;            /* the request's means are complete in its buffer at this time   */
+  double objective;         /* V of its last iterate (Eq. objective-value) when the objective
+                               rule is enabled and its class has d <= 3, else 0             */
 } pit_server_result;
 
 /* Fill `cfg` with the defaults in brackets above. */

@@ -74,7 +74,8 @@ class _ServerConfig(ctypes.Structure):
                 ("atol_delta", ctypes.c_double), ("rtol_delta", ctypes.c_double),
                 ("calibrate", ctypes.c_int32), ("chain_len", ctypes.c_int32),
                 ("max_points", ctypes.c_int64), ("max_requests", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("pad", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("atol_objective", ctypes.c_double), ("rtol_objective", ctypes.c_double)]
 
 
 class _ServerResult(ctypes.Structure):
@@ -82,7 +83,7 @@ class _ServerResult(ctypes.Structure):
                 ("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
                 ("last_delta", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double)]
+                ("t_done", ctypes.c_double), ("objective", ctypes.c_double)]
 
 
 _lib = None
@@ -577,7 +578,8 @@ class Server:
 
     def __init__(self, dtype="f32", max_iter=20, atol_delta=1e-10, rtol_delta=1e-6,
                  calibrate=True, chain_len=0, max_points=1 << 22, max_requests=1024,
-                 hbm_budget_bytes=8 << 30, device=None):
+                 hbm_budget_bytes=8 << 30, device=None, atol_objective=0.0,
+                 rtol_objective=0.0):
         import torch
         lib = load()
         cfg = _ServerConfig()
@@ -587,6 +589,7 @@ class Server:
         cfg.calibrate, cfg.chain_len = int(bool(calibrate)), int(chain_len)
         cfg.max_points, cfg.max_requests = int(max_points), int(max_requests)
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.atol_objective, cfg.rtol_objective = float(atol_objective), float(rtol_objective)
         self.cfg = cfg
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self._h = ctypes.c_void_p()
@@ -641,7 +644,8 @@ class Server:
             out.append({"request_id": r.request_id, "tag": r.tag, "status": r.status,
                         "iterations": r.iterations, "last_delta": r.last_delta,
                         "sigma2": r.sigma2, "t_submit": r.t_submit, "t_admit": r.t_admit,
-                        "t_done": r.t_done, "mean": self._outs.pop(r.request_id),
+                        "t_done": r.t_done, "objective": r.objective,
+                        "mean": self._outs.pop(r.request_id),
                         "sqrtcov": self._covs.pop(r.request_id, None)})
         return out
 

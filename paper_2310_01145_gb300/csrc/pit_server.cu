@@ -7,6 +7,7 @@
 // requests whose stopping rule holds.  A request's trajectory stays in device memory between
 // iterations; only the per-request change statistics come back to the host each step.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -92,6 +93,7 @@ struct Request {
   int cur = 0;
   int iters = 0;
   double last_delta = 0, sigma2 = 1;
+  double objective = 0;   // V of the current trajectory (objective rule, d <= 3 classes)
   // large-state request (d > 3): its own session and workspace in the pool
   std::unique_ptr<LargeSession> sess;
   // square-root covariances on request: the covariance pass's workspace and scratch means,
@@ -272,6 +274,10 @@ bool cov_reserve(pit_server* sv, Request& r) {
   return true;
 }
 
+bool obj_rule(const pit_server* sv) {
+  return sv->cfg.atol_objective > 0 || sv->cfg.rtol_objective > 0;
+}
+
 // Large-state class: admit (FIFO, by slots, points and pool memory), then enqueue one IEKS
 // iteration of every request in flight on the class stream.
 int begin_large(pit_server* sv, ClassState& cs) {
@@ -348,6 +354,14 @@ int begin_class(pit_server* sv, ClassState& cs) {
   if (!fresh.empty()) {
     int st = cs.eng->init_traj(fresh.data(), static_cast<int>(fresh.size()), cs.stream);
     if (st != PIT_OK) return st;
+    if (obj_rule(sv)) {
+      std::vector<double> v(fresh.size());
+      st = cs.eng->objective(fresh.data(), static_cast<int>(fresh.size()), v.data(), cs.stream);
+      if (st != PIT_OK) return st;
+      for (size_t j = 0; j < fresh.size(); ++j)
+        for (int64_t id : cs.active)
+          if (sv->reqs[id].slot == fresh[j].id) sv->reqs[id].objective = v[j];
+    }
   }
   if (cs.active.empty()) return PIT_OK;
   cs.slots.clear();
@@ -428,6 +442,14 @@ int end_class(pit_server* sv, ClassState& cs) {
   cs.res.resize(cs.slots.size());
   int st = cs.eng->pass_end(cs.res.data(), cs.stream);
   if (st != PIT_OK) return st;
+  std::vector<double> vnew;
+  if (obj_rule(sv)) {   // V of the new iterates lin[1 - cur] (Eq. objective-value)
+    std::vector<SegSlot> nxt(cs.slots);
+    for (SegSlot& x : nxt) x.cur ^= 1;
+    vnew.resize(nxt.size());
+    st = cs.eng->objective(nxt.data(), static_cast<int>(nxt.size()), vnew.data(), cs.stream);
+    if (st != PIT_OK) return st;
+  }
   std::vector<SegSlot> fin;
   std::vector<int64_t> fin_ids, keep;
   std::vector<int> fin_status;
@@ -437,10 +459,16 @@ int end_class(pit_server* sv, ClassState& cs) {
     r.iters += 1;
     r.last_delta = a.delta_max;
     r.sigma2 = sv->cfg.calibrate ? a.sigma2_sum / (static_cast<double>(r.pb.N) * r.pb.d) : 1.0;
+    bool obj_stop = false;
+    if (!vnew.empty()) {
+      obj_stop = std::fabs(vnew[j] - r.objective) <=
+                 sv->cfg.atol_objective + sv->cfg.rtol_objective * std::fabs(vnew[j]);
+      r.objective = vnew[j];
+    }
     int status = -1;
     if ((a.flags & 1u) || !(a.delta_max <= kDiverged)) {
       status = PIT_ENONFINITE;
-    } else if (a.delta_max <= sv->cfg.atol_delta + sv->cfg.rtol_delta * a.y_max) {
+    } else if (a.delta_max <= sv->cfg.atol_delta + sv->cfg.rtol_delta * a.y_max || obj_stop) {
       status = PIT_OK;
     } else if (r.iters >= sv->cfg.max_iter) {
       status = PIT_ENOCONV;
@@ -484,6 +512,7 @@ int end_class(pit_server* sv, ClassState& cs) {
       out.t_submit = r.t_submit;
       out.t_admit = r.t_admit;
       out.t_done = t;
+      out.objective = obj_rule(sv) ? r.objective : 0.0;
       sv->done.push_back(out);
       sv->alloc.release(r.lin_off, r.lin_bytes);
       cs.free_slots.push_back(r.slot);
@@ -581,7 +610,8 @@ int32_t pit_server_create(const pit_server_config* cfg, pit_server** out) {
   if (cfg) c = *cfg;
   if ((c.dtype != PIT_F32 && c.dtype != PIT_F64) || c.max_iter < 1 || !(c.atol_delta >= 0) ||
       !(c.rtol_delta >= 0) || c.chain_len < 0 || c.max_points < 2 || c.max_requests < 1 ||
-      c.hbm_budget_bytes < (size_t(1) << 20)) {
+      c.hbm_budget_bytes < (size_t(1) << 20) || !(c.atol_objective >= 0) ||
+      !(c.rtol_objective >= 0)) {
     set_error("invalid pit_server_config");
     return PIT_EINVAL;
   }

@@ -229,3 +229,29 @@ def test_server_covariances_fp32_vs_oracle(pit):
     orc = ieks.ieks(p, atol=1e-10, max_iter=60, want_cov=True, calibrate=True)
     assert rel(_cov(r["sqrtcov"].double().cpu().numpy()), _cov(orc.sqrtcovs)) < 1e-3
     sv.close()
+
+
+def test_server_objective_rule_matches_oracle(pit):
+    """Served requests stop on their own objective rule of Section 3.2.2 (change rule off):
+    iteration counts, V of the last iterate and the means agree with the oracle solving each
+    request alone, FP64; requests admitted while others are in flight."""
+    reqs = [W.logistic_paper(N=100, q=2), W.logistic(N=150, q=2, rate=1.0),
+            W.logistic(N=60, q=2, y0=0.3, rate=2.0), W.van_der_pol(N=150, q=2)]
+    sv = pit.Server(dtype="f64", max_iter=40, atol_delta=0.0, rtol_delta=0.0,
+                    hbm_budget_bytes=1 << 30, max_points=1 << 16, max_requests=16,
+                    atol_objective=1e-9, rtol_objective=1e-6)
+    ids = [sv.submit(p, tag=i) for i, p in enumerate(reqs[:2])]
+    sv.step()
+    ids += [sv.submit(p, tag=i + 2) for i, p in enumerate(reqs[2:])]
+    done = _drain(sv)
+    assert set(done) == set(ids)
+    for rid in ids:
+        r = done[rid]
+        p = reqs[r["tag"]]
+        orc = ieks.ieks(p, atol=0.0, max_iter=40, obj_atol=1e-9, obj_rtol=1e-6, want_cov=False,
+                        calibrate=True)
+        assert r["status"] == 0, r
+        assert r["iterations"] == orc.iterations < 40, (r["tag"], r["iterations"], orc.iterations)
+        assert r["objective"] == pytest.approx(orc.objectives[-1], rel=1e-9), r["tag"]
+        assert rel(r["mean"].cpu().numpy(), orc.means) < 1e-10, r["tag"]
+    sv.close()
