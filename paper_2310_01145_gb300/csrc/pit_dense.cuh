@@ -227,9 +227,13 @@ __device__ void cta_gemm(int m, int n, int k, T alpha, const T* A, int lda, cons
 //   TRANS = false:  X L = B;   TRANS = true: X L^T = B.
 // Blocks of NB columns: the coupling to solved blocks is one GEMM, the diagonal block is solved
 // row by row (one thread per row of X, the block of L in shared memory).
+// FP64 with tcx: the coupling products run as exact digit products on the tensor cores (their
+// staging area at sm, which then needs tc::stage_bytes() bytes).
 template <typename T, bool TRANS>
-__device__ void cta_trsm_right(int m, int n, const T* L, int ldl, T* X, int ldx, T* sm) {
-  T* Lb = sm + gemm_smem_elems<T>();  // [NB][NB + 1] diagonal block
+__device__ void cta_trsm_right(int m, int n, const T* L, int ldl, T* X, int ldx, T* sm,
+                               const tc::TcCtx* tcx = nullptr) {
+  T* Lb = sm + gemm_smem_elems<T>();  // [NB][NB + 1] diagonal block (after the coupling)
+
   const int nblk = (n + NB - 1) / NB;
   for (int bi = 0; bi < nblk; ++bi) {
     // X L: columns are resolved from the right;  X L^T: from the left
@@ -237,13 +241,33 @@ __device__ void cta_trsm_right(int m, int n, const T* L, int ldl, T* X, int ldx,
     const int j0 = blk * NB, j1 = min(n, j0 + NB), bj = j1 - j0;
     if (!TRANS && j1 < n) {
       // X[:, J] -= X[:, j1:n] L[j1:n, J]
-      cta_gemm<T, false, false>(m, bj, n - j1, T(-1), X + j1, ldx, L + static_cast<size_t>(j1) * ldl + j0,
-                                ldl, T(1), X + j0, ldx, sm);
+      bool done = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (tcx) {
+          const tc::TcCtx c{reinterpret_cast<unsigned char*>(sm), tcx->gstatus, tcx->wait_ns};
+          tc::cta_dgemm<false, false>(c, m, bj, n - j1, -1.0, X + j1, ldx,
+                                      L + static_cast<size_t>(j1) * ldl + j0, ldl, 1.0, X + j0, ldx);
+          done = true;
+        }
+      }
+      if (!done)
+        cta_gemm<T, false, false>(m, bj, n - j1, T(-1), X + j1, ldx, L + static_cast<size_t>(j1) * ldl + j0,
+                                  ldl, T(1), X + j0, ldx, sm);
     }
     if (TRANS && j0 > 0) {
       // X[:, J] -= X[:, 0:j0] L[J, 0:j0]^T
-      cta_gemm<T, false, true>(m, bj, j0, T(-1), X, ldx, L + static_cast<size_t>(j0) * ldl, ldl,
-                               T(1), X + j0, ldx, sm);
+      bool done = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (tcx) {
+          const tc::TcCtx c{reinterpret_cast<unsigned char*>(sm), tcx->gstatus, tcx->wait_ns};
+          tc::cta_dgemm<false, true>(c, m, bj, j0, -1.0, X, ldx, L + static_cast<size_t>(j0) * ldl,
+                                     ldl, 1.0, X + j0, ldx);
+          done = true;
+        }
+      }
+      if (!done)
+        cta_gemm<T, false, true>(m, bj, j0, T(-1), X, ldx, L + static_cast<size_t>(j0) * ldl, ldl,
+                                 T(1), X + j0, ldx, sm);
     }
     for (int i = threadIdx.x; i < NB * NB; i += NT) {
       const int r = i / NB, c = i % NB;

@@ -235,6 +235,21 @@ __device__ __forceinline__ void dlq(const DenseParams<T>& p, T* scr, T* M, int l
   cta_lq<T>(M, ld, rows, rf, ctri, ncols, sm, p.wsmax);
 }
 
+// X op(L) = B (cta_trsm_right) with, for FP64 solves with p.tc, the coupling products on the
+// tensor cores.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void dtrsm_right(const DenseParams<T>& p, int m, int n, const T* L,
+                                            int ldl, T* X, int ldx, T* sm) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (p.tc) {
+      const tc::TcCtx c{nullptr, p.tc_status, tc::kTcWaitNs};
+      cta_trsm_right<T, TRANS>(m, n, L, ldl, X, ldx, sm, &c);
+      return;
+    }
+  }
+  cta_trsm_right<T, TRANS>(m, n, L, ldl, X, ldx, sm);
+}
+
 // Holds the block's tensor memory for the lifetime of a kernel (FP64 solves with p.tc only).
 // Open it after the kernel's block-uniform early returns; every thread leaves through its end.
 template <typename T>
@@ -536,7 +551,7 @@ k_dreduce(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__
     // sqrtS = Wk[0:d, 0:d], Psi21 = Pr[:, 0:d], sqrtC = Psi22 = Pr[:, d:D] (= Csq)
     cta_innovation<T>(p, Ft, bp, vec + V_R * D, nu);
     cta_copy<T>(D, d, Pr, ldw, K, d);
-    cta_trsm_right<T, false>(D, d, Wk, ldw, K, d, sm);
+    dtrsm_right<T, false>(p, D, d, Wk, ldw, K, d, sm);
     for (int i = threadIdx.x; i < D; i += NT) b[i] = bp[i];
     __syncthreads();
     cta_gemv<T, false>(D, d, T(1), K, d, nu, T(1), b);
@@ -628,7 +643,7 @@ __device__ void dcombine_f(const DenseParams<T>& p, const T* al, const T* ar, T*
   if (!VALUES) dlq<T>(p, scr, X22, l2, D, D, 0, D, sm);
   // 2. M = Ci Xi11^-T; Y = I - M Xi21^T
   cta_copy<T>(D, D, Ci, D, M, D);
-  cta_trsm_right<T, true>(D, D, X11, l2, M, D, sm);
+  dtrsm_right<T, true>(p, D, D, X11, l2, M, D, sm);
   cta_set<T>(D, D, Y, D, T(1));
   dgemm<T, false, true>(p, D, D, D, T(-1), M, D, X21, l2, T(1), Y, D, sm);
   // 3. vectors: t = Ci^T eta_j, v = b_i + Ci t, w = Y v, b_new = b_j + Aj w
@@ -899,7 +914,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
     T* En = Es + (n - 1) * DD;
     T* gn = gs + (n - 1) * D;
     cta_copy<T>(D, D, Bot, ldw, En, D);
-    cta_trsm_right<T, false>(D, D, Top, ldw, En, D, sm);
+    dtrsm_right<T, false>(p, D, D, Top, ldw, En, D, sm);
     for (int i = threadIdx.x; i < D; i += NT) gn[i] = m[i];
     __syncthreads();
     cta_gemv<T, false>(D, D, T(-1), En, D, mp, T(1), gn);
@@ -934,7 +949,7 @@ k_ddown(const DenseParams<T> p, const T* __restrict__ U, const T* __restrict__ R
     dlq<T>(p, scr, Wk, ldw, d + D, d, 0, D, sm);
     cta_innovation<T>(p, Ft, mp, vec + V_R * D, nu);
     cta_copy<T>(D, d, Top, ldw, K, d);
-    cta_trsm_right<T, false>(D, d, Wk, ldw, K, d, sm);
+    dtrsm_right<T, false>(p, D, d, Wk, ldw, K, d, sm);
     for (int i = threadIdx.x; i < D; i += NT) m[i] = mp[i];
     __syncthreads();
     cta_gemv<T, false>(D, d, T(1), K, d, nu, T(1), m);
