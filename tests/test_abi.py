@@ -168,7 +168,8 @@ def test_server_config_validation_on_host(pit):
     assert cfg.dtype == 0 and cfg.max_iter == 20 and cfg.max_requests == 1024
     h = ctypes.c_void_p()
     for field, bad in (("dtype", 7), ("max_iter", 0), ("max_points", 1), ("max_requests", 0),
-                       ("hbm_budget_bytes", 1000)):
+                       ("hbm_budget_bytes", 1000), ("atol_objective", -1.0),
+                       ("rtol_objective", float("nan"))):
         c = P._ServerConfig()
         lib.pit_server_config_default(ctypes.byref(c))
         setattr(c, field, bad)
@@ -210,3 +211,36 @@ def test_binding_fails_loudly_without_the_library():
             "    print('raised', e)\n") % ROOT
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert "raised" in out.stdout, out.stdout + out.stderr
+
+
+def test_tensor_core_options_and_checks_on_host(pit):
+    """pit_opts.tensor_cores is validated and sizes the FP64 large-state workspace (the trias'
+    product buffer); the tensor-core checks and pit_linearize_approx reject bad arguments on the
+    host, before any device work."""
+    import ctypes
+    lib = pit.load()
+    p = W.lorenz96(d=64, N=100, q=2)
+    c = pit.ode_from_problem(p).c()
+    g = pit._Grid(p.t0, p.t1, p.N)
+    sizes = {}
+    for dt in ("f64", "f32"):
+        for tcores in (0, 1):
+            o = pit.make_opts(dtype=pit.PIT_F64 if dt == "f64" else pit.PIT_F32,
+                              tensor_cores=tcores)
+            sz = ctypes.c_size_t(0)
+            assert lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(g), p.q,
+                                                ctypes.byref(o), ctypes.byref(sz)) == 0
+            sizes[dt, tcores] = sz.value
+    assert sizes["f64", 1] > sizes["f64", 0]          # W and W T of the trias, per block
+    assert sizes["f32", 1] == sizes["f32", 0]          # FP32 solves never use them
+    bad = pit.make_opts(tensor_cores=3)
+    sz = ctypes.c_size_t(0)
+    assert lib.pit_solve_workspace_size(ctypes.byref(c), ctypes.byref(g), p.q, ctypes.byref(bad),
+                                        ctypes.byref(sz)) == 1
+    assert lib.pit_check_dgemm_tc(-1, 1, 1, 0, 0, 1.0, None, 1, None, 1, 0.0, None, 1, None,
+                                  None) == 1
+    assert lib.pit_check_dgemm_tc(4, 4, 4, 2, 0, 1.0, None, 4, None, 4, 0.0, None, 4, None,
+                                  None) == 1
+    assert lib.pit_check_tc_wait(-1, None, None) == 1
+    assert lib.pit_linearize_approx(ctypes.byref(c), ctypes.byref(g), p.q, 0, 3, None, None,
+                                    None, None) == 1
